@@ -1,0 +1,178 @@
+"""FP64 CPU oracle for the Modal Gamma' projection (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  It wraps ``modal_oracle.c`` (plain C, built by
+``oracle/build.py`` with gcc) through ctypes and shares no code with the CUDA
+library.  Each wrapper names the passage of arXiv 1503.08809 it follows; the
+C file has the derivations.
+
+Parity status: all functions pinned by ``tests/test_oracle_pins.py`` except
+``direct(..., weight_mode=SMOOTH)`` on sparse grids (an approximation of the
+dense sum): parity unpinned there.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_LIB = None
+
+EXACT, SMOOTH = 0, 1
+TRAPEZOID, HERMITE = 0, 1
+
+_d = ctypes.POINTER(ctypes.c_double)
+_i = ctypes.POINTER(ctypes.c_int)
+
+
+def lib_path() -> Path:
+    return _HERE / "_build" / "liboracle.so"
+
+
+def _load():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = lib_path()
+    if not p.exists():
+        from . import build as _b
+        _b.build()
+    lib = ctypes.CDLL(str(p))
+    lib.oracle_threej000_sq.restype = ctypes.c_double
+    lib.oracle_threej000_sq.argtypes = [ctypes.c_int] * 3
+    lib.oracle_gosper_threej000_sq.restype = ctypes.c_double
+    lib.oracle_gosper_threej000_sq.argtypes = [ctypes.c_int] * 3
+    lib.oracle_gl_nodes.argtypes = [ctypes.c_int, _d, _d]
+    lib.oracle_legendre_row.argtypes = [ctypes.c_int, ctypes.c_double, _d]
+    lib.oracle_x_weights.argtypes = [ctypes.c_int, ctypes.c_int, _d, _d]
+    lib.oracle_num_threads.restype = ctypes.c_int
+    common = [ctypes.c_int] * 5 + [_d, _d, _d, _d]
+    lib.oracle_separable.argtypes = common + [ctypes.c_int, _d, _d, ctypes.c_int, _i,
+                                              ctypes.c_int, _i, _d]
+    lib.oracle_direct.argtypes = common + [ctypes.c_int, _i, _d, ctypes.c_int,
+                                           ctypes.c_int, _i, ctypes.c_int, _i, _d]
+    lib.oracle_backward.argtypes = common + [ctypes.c_int, _d, _d, ctypes.c_int, _i,
+                                             ctypes.c_int, _i, _d, _d, _d]
+    _LIB = lib
+    return lib
+
+
+def _pd(a: np.ndarray):
+    return a.ctypes.data_as(_d)
+
+
+def _pi(a: np.ndarray):
+    return a.ctypes.data_as(_i)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def threej000_sq(l1: int, l2: int, l3: int) -> float:
+    """(l1 l2 l3; 0 0 0)^2 by the closed form (Section 2.1)."""
+    return float(_load().oracle_threej000_sq(int(l1), int(l2), int(l3)))
+
+
+def gosper_threej000_sq(l1: int, l2: int, l3: int) -> float:
+    """Gosper approximation of (l1 l2 l3; 0 0 0)^2 (Section 2.1)."""
+    return float(_load().oracle_gosper_threej000_sq(int(l1), int(l2), int(l3)))
+
+
+def gl_nodes(n: int):
+    """Gauss-Legendre nodes (ascending) and weights, long-double Newton (Section 2.2)."""
+    mu = np.zeros(n)
+    om = np.zeros(n)
+    _load().oracle_gl_nodes(int(n), _pd(mu), _pd(om))
+    return mu, om
+
+
+def legendre_row(lmax: int, mu: float) -> np.ndarray:
+    """P_0..P_lmax at mu by the three-term recurrence."""
+    P = np.zeros(lmax + 1)
+    _load().oracle_legendre_row(int(lmax), float(mu), _pd(P))
+    return P
+
+
+def x_weights(x, kind: int = TRAPEZOID) -> np.ndarray:
+    """Radial weights including x^2 (Section 3.2.4: trapezium or Hermite)."""
+    x = _f64(x)
+    w = np.zeros_like(x)
+    _load().oracle_x_weights(int(kind), int(x.size), _pd(x), _pd(w))
+    return w
+
+
+def _common(P, xw):
+    return (int(P.l_min), int(P.l_max), int(P.nb_late), int(P.nb_prim), int(P.n_x),
+            _f64(P.q), _f64(P.qt), _f64(P.w_l), _f64(xw))
+
+
+def separable(P, n_mu: int | None = None, xw=None, mu=None, om=None,
+              late=None, prim=None) -> np.ndarray:
+    """Gamma' by Eq. 2D (Section 2.2) with GL mu and trapezium x weights.
+    ``late``/``prim`` restrict the mode lists (rows/columns)."""
+    n_mu = P.n_mu if n_mu is None else int(n_mu)
+    if mu is None:
+        mu, om = gl_nodes(n_mu)
+    if xw is None:
+        xw = x_weights(P.x)
+    late = _i32(P.late_modes if late is None else late)
+    prim = _i32(P.prim_modes if prim is None else prim)
+    l0, l1, nbl, nbp, nx, q, qt, wl, xw = _common(P, xw)
+    mu, om = _f64(mu), _f64(om)
+    g = np.zeros((late.shape[0], prim.shape[0]))
+    _load().oracle_separable(l0, l1, nbl, nbp, nx, _pd(q), _pd(qt), _pd(wl), _pd(xw),
+                             int(mu.size), _pd(mu), _pd(om), int(late.shape[0]), _pi(late),
+                             int(prim.shape[0]), _pi(prim), _pd(g))
+    return g
+
+
+def direct(P, l_grid=None, l_dw=None, weight_mode: int = EXACT, xw=None,
+           late=None, prim=None) -> np.ndarray:
+    """Gamma' by the tetrahedral sum of Eq. 3D (Section 2.1) on a multipole grid."""
+    if l_grid is None:
+        l_grid = np.arange(P.l_min, P.l_max + 1)
+        l_dw = np.ones(l_grid.size)
+    if xw is None:
+        xw = x_weights(P.x)
+    late = _i32(P.late_modes if late is None else late)
+    prim = _i32(P.prim_modes if prim is None else prim)
+    lg = _i32(l_grid)
+    dw = _f64(l_dw)
+    l0, l1, nbl, nbp, nx, q, qt, wl, xw = _common(P, xw)
+    g = np.zeros((late.shape[0], prim.shape[0]))
+    _load().oracle_direct(l0, l1, nbl, nbp, nx, _pd(q), _pd(qt), _pd(wl), _pd(xw),
+                          int(lg.size), _pi(lg), _pd(dw), int(weight_mode),
+                          int(late.shape[0]), _pi(late), int(prim.shape[0]), _pi(prim),
+                          _pd(g))
+    return g
+
+
+def backward(P, gbar, n_mu: int | None = None, xw=None, want_dq: bool = True):
+    """Adjoint of ``separable``: (dL/dq~ [n_x][nb_prim][L], dL/dq [nb_late][L])."""
+    n_mu = P.n_mu if n_mu is None else int(n_mu)
+    mu, om = gl_nodes(n_mu)
+    if xw is None:
+        xw = x_weights(P.x)
+    late = _i32(P.late_modes)
+    prim = _i32(P.prim_modes)
+    l0, l1, nbl, nbp, nx, q, qt, wl, xw = _common(P, xw)
+    gb = _f64(gbar)
+    dqt = np.zeros((nx, nbp, P.L))
+    dq = np.zeros((nbl, P.L)) if want_dq else None
+    _load().oracle_backward(l0, l1, nbl, nbp, nx, _pd(q), _pd(qt), _pd(wl), _pd(xw),
+                            int(mu.size), _pd(mu), _pd(om), int(late.shape[0]), _pi(late),
+                            int(prim.shape[0]), _pi(prim), _pd(gb), _pd(dqt),
+                            _pd(dq) if dq is not None else None)
+    return dqt, dq
