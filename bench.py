@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the Modal Gamma' projection on one or more GB300s.
+
+One step = one full separable projection (Gauss-Legendre nodes, weighted
+Legendre table, l contraction, triple product with the slice reduction,
+symmetrise/gather) of the Planck-scale workload: l_max = 2000, 20 basis
+functions (1540 modes each side), 500 radial points, N_mu = 3001, i.e.
+1,500,500 (x, mu) slices.  The metric is slices per second of the whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Under torchrun (N > 1) every rank projects its own independent problem (a
+different seed): weak scaling with no collective on the data path; the time
+is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "Γ_nm (x,μ)-slices/s and % tensor peak vs plain FP64 GPU at stated error"
+PREC = {"fp64": 0, "fp32": 1, "ozaki": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "ozaki": "bf16x(ozaki)+f64"}
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (CUDA cores), nominal figure
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", *PREC])
+    ap.add_argument("--n-x", type=int, default=500, help="radial points (workload: 500)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(backend_gpu: bool):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if backend_gpu else "gloo")
+    return ws, rank, local
+
+
+def max_over_ranks(v: float, ws: int, device=None) -> float:
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in Path(self.f.name).read_text().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        load = [r for r in rows if r[0] > 0.5 * r[1]] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            return json.loads(p.read_text()), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(P, seconds: float):
+    """The FP64 oracle as it stands, on a bounded sample of the workload: one
+    radial point (the one nearest the last-scattering peak) and the first K
+    Gauss-Legendre nodes, all 1540 x 1540 modes; K is sized for ~`seconds` of
+    work.  Returns slices/s (slices = K here) and a description."""
+    import oracle
+    import synthetic as syn
+    mu, om = oracle.gl_nodes(P.n_mu)
+    xi = int(np.argmin(np.abs(P.x - syn.X_PEAK)))
+    Ps = syn.Problem(**{**P.__dict__, "qt": P.qt[xi:xi + 1].copy(), "x": P.x[xi:xi + 1],
+                        "n_x": 1})
+    xw = np.ones(1)
+
+    def run(k):
+        t0 = time.perf_counter()
+        oracle.separable(Ps, xw=xw, mu=mu[:k], om=om[:k])
+        return time.perf_counter() - t0
+
+    k = 2
+    t = run(k)
+    while t < 1.0 and k < P.n_mu:
+        k = min(P.n_mu, k * 4)
+        t = run(k)
+    k = int(max(1, min(P.n_mu, k * seconds / max(t, 1e-3))))
+    t = run(k)
+    return k / t, t, k, oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(False)
+    if rank != 0:
+        return
+    import synthetic as syn
+    P = syn.planck_size(n_x=args.n_x)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, t, k, cores = cpu_baseline(P, args.cpu_seconds / max(1, args.steps))
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    sample = (f"1 of {P.n_x} radial points x first {k} of {P.n_mu} GL nodes, all "
+              f"{P.n_late}x{P.n_prim} modes, per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "slices/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * P.slices / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": P.name, "l_max": P.l_max, "nb": P.nb_late, "n_x": P.n_x,
+                       "n_mu": P.n_mu, "slices": P.slices},
+            "cpu_baseline": {"value": value, "unit": "slices/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "slices/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_setup(True)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1503_08809_gb300 as mg
+    import synthetic as syn
+
+    prec_name = "fp64" if args.precision == "auto" else args.precision
+    prec = PREC[prec_name]
+    P = syn.planck_size(seed=1 + rank, n_x=args.n_x)
+    h = mg.Handle(dev)
+    dp = mg.DeviceProblem.from_host(P, device=dev, handle=h)
+    gamma = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def step():
+        mg.project_separable(dp, precision=prec, out=gamma, handle=h)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed region (profiler events on, clocks sampled) ----------
+    lib = mg.lib()
+    lib.modal_profile_enable(h.ptr, 1)
+    import ctypes
+    names = ctypes.create_string_buffer(32 * 64)
+    launches = (ctypes.c_int64 * 64)()
+    tms = (ctypes.c_double * 64)()
+    nout = ctypes.c_int32()
+    lib.modal_profile_read(h.ptr, 64, names, launches, tms, ctypes.byref(nout))  # reset
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    lib.modal_profile_read(h.ptr, 64, names, launches, tms, ctypes.byref(nout))
+    lib.modal_profile_enable(h.ptr, 0)
+    prof = {}
+    for i in range(nout.value):
+        nm = names.raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
+        prof[nm] = (int(launches[i]), float(tms[i]))
+    ms_max = max_over_ranks(ms, ws, dev)
+    value = ws * P.slices / (ms_max * 1e-3)
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    peaks, src = measured_peaks()
+    dom = max(prof, key=lambda k: prof[k][1]) if prof else None
+    roof = None
+    if dom:
+        nl, tot = prof[dom]
+        avg_s = tot / nl * 1e-3
+        g2 = P.nb_prim * (P.nb_prim + 1) // 2
+        gsize = g2 * P.nb_prim * P.n_late          # useful MACs per slice of the triple product
+        chunk_slices = P.slices / max(1, nl // args.steps)
+        if dom.startswith("triple"):
+            flops = 2.0 * gsize * chunk_slices
+        elif dom.startswith("contract"):
+            flops = 2.0 * P.nb_late * P.nb_prim * P.L * chunk_slices
+        else:
+            flops = float("nan")
+        achieved = flops / avg_s / 1e12
+        if prec_name == "ozaki":
+            peak, unit, bound, note = peaks["bf16_tflops"], "TFLOP/s", "tensor", f"bf16 {src}"
+        else:
+            peak, unit, bound, note = FP64_NOMINAL_TFLOPS, "TFLOP/s", "alu", "fp64 nominal"
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": note, "kernel_ms_avg": avg_s * 1e3,
+                "kernel_share_of_step": tot / (ms * args.steps)}
+    gpu_launches = sum(v[0] for v in prof.values())
+
+    # ---- end to end through host buffers -----------------------------------
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hq, hqt, hw, hx = pin(P.q), pin(P.qt), pin(P.w_l), pin(P.x)
+        hl, hp = pin(P.late_modes), pin(P.prim_modes)
+        hg = torch.empty(P.n_late, P.n_prim, dtype=torch.float64).pin_memory()
+        dq, dqt, dw, dx = (torch.empty_like(t, device=dev) for t in (hq, hqt, hw, hx))
+        dl, dpm = torch.empty_like(hl, device=dev), torch.empty_like(hp, device=dev)
+        h2d = sum(t.numel() * t.element_size() for t in (hq, hqt, hw, hx, hl, hp))
+        d2h = hg.numel() * hg.element_size()
+
+        def e2e_step():
+            for d, s in ((dq, hq), (dqt, hqt), (dw, hw), (dx, hx), (dl, hl), (dpm, hp)):
+                d.copy_(s, non_blocking=True)
+            xw = mg.x_weights(dx, handle=h)
+            dpe = mg.DeviceProblem(dq, dqt, dw, xw, dl, dpm, P.l_min, P.l_max, dev)
+            g = mg.project_separable(dpe, precision=prec, out=gamma, handle=h)
+            hg.copy_(g, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        e0.record(st)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws, dev)
+        e2e = {"value": ws * P.slices / (ms_e2e * 1e-3), "unit": "slices/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        v, t, k, cores = cpu_baseline(P, args.cpu_seconds)
+        cpu = {"value": v, "unit": "slices/s", "cores": cores, "kind": "oracle",
+               "sample": f"1 of {P.n_x} radial points x first {k} of {P.n_mu} GL nodes, all "
+                         f"{P.n_late}x{P.n_prim} modes ({t:.1f} s)"}
+    line = {"metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[prec_name], "data": "synthetic",
+            "config": {"workload": P.name, "l_max": P.l_max, "nb": P.nb_late, "n_x": P.n_x,
+                       "n_mu": P.n_mu, "slices": P.slices, "precision": prec_name,
+                       "n_modes": P.n_late,
+                       "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clk, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * modal.h -- C ABI of libmodal, a GB300 (sm_103a) implementation of the
+ * Modal Gamma' projection of arXiv 1503.08809 (Briggs, Pennycook,
+ * Fergusson, Jaykka, Shellard): the matrix that projects primordial modes
+ * (p,r,s), carried through the radial integral by q~_p(l,x), onto late-time
+ * CMB modes (a,b,c) over the triangle- and parity-bounded (l1,l2,l3) domain
+ * weighted by (l1 l2 l3; 0 0 0)^2.
+ *
+ * Conventions (every call):
+ *  - Arrays are row-major and contiguous.  Unless marked "host", a pointer
+ *    is a DEVICE pointer owned by the caller; the library never frees it.
+ *  - l runs over the dense range l_min..l_max (L = l_max - l_min + 1).
+ *    The paper's sums start at l = 2 (Eq. 3D), so l_min = 2 is the usual
+ *    choice; any l_min >= 0 is accepted.
+ *  - Calls are asynchronous on `stream` (NULL = legacy default stream)
+ *    unless documented otherwise.  The handle owns all scratch memory
+ *    (grown on demand with cudaMalloc, released by modal_handle_destroy);
+ *    concurrent calls on one handle are not allowed.
+ *  - Every call returns a status code (MODAL_OK = 0).  On error nothing is
+ *    aborted or thrown; modal_last_error() gives a one-line reason.
+ *  - Gamma'[n][n'] is FP64 with rows n = late-time modes and columns
+ *    n' = primordial modes; it includes the 1/(48 pi) prefactor of Eq. 2D.
+ */
+#ifndef MODAL_H
+#define MODAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* same type as cudaStream_t */
+typedef struct CUstream_st *modal_stream_t;
+
+/* status codes */
+#define MODAL_OK 0
+#define MODAL_EINVAL 1        /* bad argument (null pointer, size, mode index, ...) */
+#define MODAL_ENOMEM 2        /* device allocation for the handle's scratch failed */
+#define MODAL_ECUDA 3         /* a CUDA runtime/launch error (message has the CUDA text) */
+#define MODAL_ETIMEOUT 4      /* a bounded device-side wait gave up */
+#define MODAL_EUNSUPPORTED 5  /* valid request this build/device cannot serve */
+
+/* arithmetic of the separable path (modal_opts.precision) */
+#define MODAL_PREC_FP64 0        /* FP64 everywhere (CUDA cores) */
+#define MODAL_PREC_FP32 1        /* FP32 products, FP32 sums over short chunks,
+                                    FP64 accumulation of the chunk sums */
+#define MODAL_PREC_OZAKI_BF16 2  /* tcgen05 tensor cores: operands split into
+                                    exponent-aligned BF16 slices, exact FP32
+                                    chunk sums, FP64 accumulation */
+
+/* radial quadrature (modal_x_weights) */
+#define MODAL_XW_TRAPEZOID 0  /* trapezium rule (Section 3.2.4), times x^2 */
+#define MODAL_XW_HERMITE 1    /* local Hermite-cubic rule (Section 3.2.4), times x^2 */
+
+/* weights of the direct sum (modal_project_direct) */
+#define MODAL_W_EXACT_3J 0       /* exact (l1 l2 l3;000)^2: triangle + parity */
+#define MODAL_W_SMOOTH_GOSPER 1  /* 1/2 x Gosper form, triangle only (sparse grids) */
+
+typedef struct modal_handle modal_handle;
+
+/* One projection problem (Eq. 3D / Eq. 2D / Eq. legendre).  The struct itself
+ * lives in host memory; its array members are device pointers. */
+typedef struct modal_problem {
+  int32_t l_min, l_max;       /* dense l range of the tables */
+  int32_t nb_late, nb_prim;   /* sizes of the late-time and primordial 1D bases */
+  int32_t n_x;                /* radial points */
+  int32_t n_late, n_prim;     /* number of late / primordial 3D modes */
+  int32_t reserved0;
+  const double *q;            /* [nb_late][L]       q_a(l)              (Eq. 3D) */
+  const double *qt;           /* [n_x][nb_prim][L]  q~_p(l, x)           (Eq. 3D) */
+  const double *w_l;          /* [L] (2l+1)/(v_l sqrt(C_l))        (Eq. legendre) */
+  const double *x_w;          /* [n_x] radial weights incl. x^2 (modal_x_weights) */
+  const int32_t *late_modes;  /* [n_late][3] index triples (a,b,c), any order,
+                                 each < nb_late (Appendix A's n -> ijk map) */
+  const int32_t *prim_modes;  /* [n_prim][3] index triples (p,r,s), each < nb_prim */
+} modal_problem;
+
+typedef struct modal_opts {
+  int32_t n_mu;              /* GL order; 0 = ceil((3 l_max + 1)/2), the smallest
+                                order exact for P_l1 P_l2 P_l3 (Section 2.2) */
+  int32_t precision;         /* MODAL_PREC_* */
+  int32_t allow_inexact_gl;  /* nonzero: accept n_mu below that bound */
+  int32_t x_chunk;           /* radial points per streamed chunk; 0 = automatic */
+} modal_opts;
+
+/* ---- handle ------------------------------------------------------------ */
+int modal_handle_create(modal_handle **out);
+int modal_handle_destroy(modal_handle *h);
+/* One-line reason of the last failing call on h (h may be NULL: last
+ * failure of modal_handle_create on this thread).  Never NULL. */
+const char *modal_last_error(const modal_handle *h);
+/* Device scratch bytes modal_project_separable / _backward will hold for this
+ * problem and options (host pointers; no device work). */
+int modal_workspace_size(const modal_problem *prob, const modal_opts *opts,
+                         int for_backward, size_t *bytes);
+/* Pre-grow the handle's scratch to at least `bytes` (call before capturing a
+ * CUDA graph so that no allocation happens during capture). */
+int modal_handle_reserve(modal_handle *h, size_t bytes);
+
+/* Opt-in per-kernel timing: while enabled, the library records a CUDA event
+ * pair on the call's stream around each kernel it launches (negligible
+ * overhead; no synchronisation at record time).  modal_profile_read waits
+ * for the recorded events, then reports per kernel name the launch count and
+ * the summed device time since the last reset, and clears the records.
+ * names: host [max_entries][32] chars; launches, total_ms: host [max_entries]. */
+int modal_profile_enable(modal_handle *h, int32_t enable);
+int modal_profile_read(modal_handle *h, int32_t max_entries, char *names, int64_t *launches,
+                       double *total_ms, int32_t *n_out);
+
+/* ---- individual steps of the separable path ----------------------------- */
+
+/* Gauss-Legendre nodes (ascending) and weights of order n_mu, for the mu
+ * integral of Eq. 2D (Section 2.2: library nodes were not accurate enough,
+ * so the nodes are refined in double-double and rounded once to FP64).
+ * mu, om: device [n_mu].  n_mu >= 1. */
+int modal_gl_nodes(modal_handle *h, int32_t n_mu, double *mu, double *om,
+                   modal_stream_t stream);
+
+/* Legendre table with the l weight folded in (the `factor` array of the
+ * Modal2D listing, Section 3.1): A[j][l - l_min] = w_l P_l(mu_j) for
+ * l = l_min..l_max, by the three-term recurrence in FP64.
+ * mu: device [n_mu]; w_l: device [L] or NULL (then w_l = 1); A: device [n_mu][L]. */
+int modal_legendre_table(modal_handle *h, int32_t n_mu, const double *mu, int32_t l_min,
+                         int32_t l_max, const double *w_l, double *A, modal_stream_t stream);
+
+/* Radial weights W_x of "int r^2 dr" (Eq. 3D), including x^2 (Section 3.2.4).
+ * x: device [n_x] strictly increasing; w: device [n_x]. */
+int modal_x_weights(modal_handle *h, int32_t kind, int32_t n_x, const double *x, double *w,
+                    modal_stream_t stream);
+
+/* l contraction of Eq. legendre for every (x, mu_j) slice:
+ *   M[x][j][a][p] = sum_l A[j][l] q_a(l) q~_p(l, x),   A from modal_legendre_table.
+ * A: device [n_mu][L]; M: device [n_x][n_mu][nb_late][nb_prim] FP64.
+ * (prob->late_modes/prim_modes/x_w are not used.) */
+int modal_contract_l(modal_handle *h, const modal_problem *prob, int32_t n_mu,
+                     const double *A, double *M, modal_stream_t stream);
+
+/* ---- the projection ------------------------------------------------------ */
+
+/* Separable projection, Eq. 2D (Section 2.2):
+ *   Gamma'[n][n'] = 1/(48 pi) sum_x W_x sum_j om_j perm3(M(x, mu_j)[n, n'])
+ * where perm3 is the permanent of the 3x3 block of M picked by the late
+ * triple (rows) and the primordial triple (columns) -- the six products of
+ * the Modal2D listing.  gamma: device [n_late][n_prim] FP64 (overwritten).
+ * Exact (up to rounding) when n_mu >= (3 l_max + 1)/2; smaller n_mu is
+ * rejected with MODAL_EINVAL unless opts->allow_inexact_gl. opts may be NULL
+ * (FP64, automatic n_mu).  Stream-ordered, no host synchronisation. */
+int modal_project_separable(modal_handle *h, const modal_problem *prob,
+                            const modal_opts *opts, double *gamma, modal_stream_t stream);
+
+/* Direct (non-separable) projection, Eq. 3D (Section 2.1), on a multipole
+ * grid: the sum over sorted triples l1 <= l2 <= l3 from l_grid (device [n_grid],
+ * strictly increasing, inside [l_min, l_max]) with weight
+ *   mult(l) * dw1 dw2 dw3 * w_l1 w_l2 w_l3 * H(l) / (144 pi)
+ * times (sum over the 6 assignments of q_a q_b q_c) times (sum_x W_x times the
+ * 6 assignments of q~_p q~_r q~_s); mult = number of distinct orderings of
+ * (l1,l2,l3) (6, 3 or 1).  H = exact 3j^2 (MODAL_W_EXACT_3J) or 1/2 x the
+ * Gosper form with the triangle condition only (MODAL_W_SMOOTH_GOSPER).
+ * l_dw: device [n_grid] multipoles represented by each grid point (1 on a
+ * dense grid; NULL = all 1).  On a dense grid with EXACT weights this equals
+ * modal_project_separable.  gamma: device [n_late][n_prim] (overwritten).
+ * This call synchronises `stream` once (to size its triple batches). */
+int modal_project_direct(modal_handle *h, const modal_problem *prob, const int32_t *l_grid,
+                         const double *l_dw, int32_t n_grid, int32_t weight_mode,
+                         double *gamma, modal_stream_t stream);
+
+/* Adjoint of modal_project_separable (not in the paper; it follows from
+ * Eq. 2D and Eq. legendre): given dL_dgamma = dL/dGamma' (device
+ * [n_late][n_prim]) writes dL/dq~ (device [n_x][nb_prim][L], overwritten)
+ * and, if dL_dq is not NULL, dL/dq (device [nb_late][L], overwritten).
+ * M slices are recomputed, not stored.  opts as for the forward call
+ * (MODAL_PREC_OZAKI_BF16 is served by the FP32 adjoint). */
+int modal_project_backward(modal_handle *h, const modal_problem *prob, const modal_opts *opts,
+                           const double *dL_dgamma, double *dL_dqt, double *dL_dq,
+                           modal_stream_t stream);
+
+/* Many independent problems of uneven size in one call (host array `probs`
+ * of n problem descriptors, host array `gammas` of n device outputs).  Each
+ * result equals modal_project_separable on that problem with these opts. */
+int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_problem *probs,
+                                    const modal_opts *opts, double *const *gammas,
+                                    modal_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MODAL_H */

@@ -56,6 +56,7 @@ def _load():
                                            ctypes.c_int, _i, ctypes.c_int, _i, _d]
     lib.oracle_backward.argtypes = common + [ctypes.c_int, _d, _d, ctypes.c_int, _i,
                                              ctypes.c_int, _i, _d, _d, _d]
+    lib.oracle_M.argtypes = [ctypes.c_int] * 5 + [_d, _d, _d, ctypes.c_int, _d, _d]
     _LIB = lib
     return lib
 
@@ -116,6 +117,16 @@ def x_weights(x, kind: int = TRAPEZOID) -> np.ndarray:
 def _common(P, xw):
     return (int(P.l_min), int(P.l_max), int(P.nb_late), int(P.nb_prim), int(P.n_x),
             _f64(P.q), _f64(P.qt), _f64(P.w_l), _f64(xw))
+
+
+def M_table(P, mu) -> np.ndarray:
+    """P_{ii'}(x, mu_j) of Eq. legendre for every slice: [n_x][n_mu][nb_late][nb_prim]."""
+    mu = _f64(mu)
+    M = np.zeros((P.n_x, mu.size, P.nb_late, P.nb_prim))
+    _load().oracle_M(int(P.l_min), int(P.l_max), int(P.nb_late), int(P.nb_prim), int(P.n_x),
+                     _pd(_f64(P.q)), _pd(_f64(P.qt)), _pd(_f64(P.w_l)), int(mu.size), _pd(mu),
+                     _pd(M))
+    return M
 
 
 def separable(P, n_mu: int | None = None, xw=None, mu=None, om=None,

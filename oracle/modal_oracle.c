@@ -437,3 +437,27 @@ void oracle_backward(int l_min, int l_max, int nbl, int nbp, int nx, const doubl
   }
   free(all_a); free(all_p); free(P); free(M); free(dM);
 }
+
+/* ------------------------------------------------------------------------ */
+/* The table P_{ii'}(x, mu_j) of Eq. legendre on every slice, by plain       */
+/* loops: M[x][j][a][p] = sum_l wl[l] P_l(mu_j) q_a(l) q~_p(l, x).           */
+/* ------------------------------------------------------------------------ */
+void oracle_M(int l_min, int l_max, int nbl, int nbp, int nx, const double *q,
+              const double *qt, const double *wl, int nmu, const double *mu, double *M) {
+  int L = l_max - l_min + 1;
+  unsigned char *all_a = (unsigned char *)malloc((size_t)nbl);
+  unsigned char *all_p = (unsigned char *)malloc((size_t)nbp);
+  memset(all_a, 1, (size_t)nbl);
+  memset(all_p, 1, (size_t)nbp);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < nmu; ++j) {
+    double *P = (double *)malloc(sizeof(double) * (size_t)(l_max + 1));
+    oracle_legendre_row(l_max, mu[j], P);
+    for (int x = 0; x < nx; ++x)
+      legendre_table_M(l_min, L, nbl, nbp, q, qt + (size_t)x * nbp * L, wl, P, all_a, all_p,
+                       M + (((size_t)x * nmu + j) * nbl) * nbp);
+    free(P);
+  }
+  free(all_a);
+  free(all_p);
+}

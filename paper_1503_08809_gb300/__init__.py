@@ -1,0 +1,24 @@
+"""GB300 (sm_103a) implementation of the Modal Gamma' projection of
+arXiv 1503.08809 behind the C ABI in ``include/modal.h``.
+
+This module only marshals arguments: torch CUDA tensors for device memory
+and streams, ctypes for the calls.  Every step of the projection runs in
+``libmodal.so``'s kernels; there is no CPU fallback -- importing the library
+fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+from ._lib import (ModalError, PREC_FP32, PREC_FP64, PREC_OZAKI_BF16, W_EXACT_3J,
+                   W_SMOOTH_GOSPER, XW_HERMITE, XW_TRAPEZOID, lib, lib_path)
+from .api import (DeviceProblem, Handle, contract_l, default_handle, gl_nodes, legendre_table,
+                  project_backward, project_direct, project_separable,
+                  project_separable_batched, x_weights)
+from .autograd import ModalProjection, fit_loss_and_grads
+
+__all__ = [
+    "ModalError", "PREC_FP32", "PREC_FP64", "PREC_OZAKI_BF16", "W_EXACT_3J", "W_SMOOTH_GOSPER",
+    "XW_HERMITE", "XW_TRAPEZOID", "lib", "lib_path", "DeviceProblem", "Handle", "contract_l",
+    "default_handle", "gl_nodes", "legendre_table", "project_backward", "project_direct",
+    "project_separable", "project_separable_batched", "x_weights", "ModalProjection",
+    "fit_loss_and_grads",
+]

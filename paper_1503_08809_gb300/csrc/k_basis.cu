@@ -1,0 +1,198 @@
+// k_basis.cu -- rows a1-a3 of the separable path: Gauss-Legendre nodes,
+// the weighted Legendre table and the radial weights.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace modal {
+
+// ---------------------------------------------------------------------------
+// a1: Gauss-Legendre nodes/weights (Section 2.2).  One thread per root pair
+// (+-mu).  Newton in FP64 from the usual cosine guess, then two Newton steps
+// with P_n, P_{n-1} evaluated in double-double by the three-term recurrence
+//   (k+1) P_{k+1} = (2k+1) mu P_k - k P_{k-1},
+// then w = 2 / ((1 - mu^2) P_n'(mu)^2), P_n' = n (mu P_n - P_{n-1})/(mu^2-1),
+// in double-double, each rounded once to FP64.  Output ascending.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void leg_pair_d(int n, double x, double &pn, double &pm) {
+  double p0 = 1.0, p1 = x;
+  for (int k = 1; k < n; ++k) {
+    double p2 = ((2.0 * k + 1.0) * x * p1 - (double)k * p0) / (double)(k + 1);
+    p0 = p1;
+    p1 = p2;
+  }
+  pn = p1;
+  pm = p0;
+}
+
+__device__ __forceinline__ void leg_pair_dd(int n, dd x, dd &pn, dd &pm) {
+  dd p0 = {1.0, 0.0}, p1 = x;
+  for (int k = 1; k < n; ++k) {
+    dd t = dd_mul_d(dd_mul(x, p1), 2.0 * k + 1.0);
+    t = dd_sub(t, dd_mul_d(p0, (double)k));
+    dd p2 = dd_div_d(t, (double)(k + 1));
+    p0 = p1;
+    p1 = p2;
+  }
+  pn = p1;
+  pm = p0;
+}
+
+__global__ void k_gl_nodes(int n, double *__restrict__ mu, double *__restrict__ om) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int half = (n + 1) / 2;
+  if (i >= half) return;
+  if (n == 1) {
+    mu[0] = 0.0;
+    om[0] = 2.0;
+    return;
+  }
+  double x = cos(MODAL_PI * ((double)i + 0.75) / ((double)n + 0.5));
+  for (int it = 0; it < 60; ++it) {
+    double pn, pm;
+    leg_pair_d(n, x, pn, pm);
+    double dp = (double)n * (x * pn - pm) / (x * x - 1.0);
+    double dx = pn / dp;
+    x -= dx;
+    if (fabs(dx) <= 2e-16 * fabs(x)) break;
+  }
+  dd X = {x, 0.0};
+  dd pn, pm, dp;
+  const dd one = {1.0, 0.0};
+  for (int it = 0; it < 2; ++it) {
+    leg_pair_dd(n, X, pn, pm);
+    dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pn), pm), (double)n), dd_sub(dd_mul(X, X), one));
+    X = dd_sub(X, dd_div(pn, dp));
+  }
+  leg_pair_dd(n, X, pn, pm);
+  dd x2m1 = dd_sub(dd_mul(X, X), one);
+  dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pn), pm), (double)n), x2m1);
+  dd w = dd_div({2.0, 0.0}, dd_mul(dd_neg(x2m1), dd_mul(dp, dp)));
+  double xv = X.hi + X.lo, wv = w.hi + w.lo;
+  if ((n & 1) && i == n / 2) {  // exact centre node of an odd rule
+    mu[i] = 0.0;
+    om[i] = wv;
+    return;
+  }
+  mu[n - 1 - i] = xv;
+  om[n - 1 - i] = wv;
+  mu[i] = -xv;
+  om[i] = wv;
+}
+
+// ---------------------------------------------------------------------------
+// a2: A[j][l - l_min] = w_l P_l(mu_j) (the `factor` array of the Modal2D
+// listing).  A block of 128 threads owns 128 nodes; each thread runs the
+// FP64 recurrence for its node, 32 l at a time into shared memory, and the
+// block writes the 128 x 32 tile with coalesced row segments.
+// ---------------------------------------------------------------------------
+constexpr int LEG_NODES = 128;
+constexpr int LEG_LT = 32;
+
+__global__ void __launch_bounds__(LEG_NODES) k_legendre_table(int n_mu, const double *__restrict__ mu,
+                                                            int l_min, int l_max,
+                                                            const double *__restrict__ w_l,
+                                                            double *__restrict__ A) {
+  __shared__ double tile[LEG_NODES][LEG_LT + 1];
+  const int L = l_max - l_min + 1;
+  const int j0 = blockIdx.x * LEG_NODES;
+  const int j = j0 + threadIdx.x;
+  double x = (j < n_mu) ? mu[j] : 0.0;
+  double p0 = 1.0, p1 = x;  // P_{l}, P_{l+1} with l = next degree to emit
+  int lnext = 0;            // degree held in p0
+  for (int lb = l_min; lb <= l_max; lb += LEG_LT) {
+    for (int c = 0; c < LEG_LT; ++c) {
+      int l = lb + c;
+      // advance the recurrence until p0 = P_l
+      while (lnext < l) {
+        double p2 = ((2.0 * lnext + 3.0) * x * p1 - (double)(lnext + 1) * p0) / (double)(lnext + 2);
+        p0 = p1;
+        p1 = p2;
+        ++lnext;
+      }
+      double v = 0.0;
+      if (l <= l_max) v = (w_l ? w_l[l - l_min] : 1.0) * p0;
+      tile[threadIdx.x][c] = v;
+    }
+    __syncthreads();
+    // coalesced write: warp w writes rows w, w+4, ...; lane = column
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < LEG_NODES; r += LEG_NODES / 32) {
+      int jj = j0 + r, l = lb + lane;
+      if (jj < n_mu && l <= l_max) A[(size_t)jj * L + (l - l_min)] = tile[r][lane];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a3: radial weights including x^2 (Section 3.2.4).
+// kind 0: trapezium; kind 1: Hermite cubic with forward-difference slopes,
+// integrated exactly per interval:
+//   int_k = dr_k/2 (y_k + y_{k+1}) + dr_k^2/12 (D_k - D_{k+1}), D_k = dy_k/dr_k,
+// with D at the last node equal to the last interval's.  The weight of node
+// m collects the coefficient of y_m from every interval touching it.
+// ---------------------------------------------------------------------------
+__global__ void k_x_weights(int kind, int n, const double *__restrict__ x, double *__restrict__ w) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double s = 0.0;
+  if (n >= 2) {
+    // trapezium part
+    if (m > 0) s += 0.5 * (x[m] - x[m - 1]);
+    if (m < n - 1) s += 0.5 * (x[m + 1] - x[m]);
+    if (kind == 1) {
+      // slope D_k = (y_{k+1} - y_k) / h_k depends on y_k (-1/h_k) and y_{k+1} (+1/h_k).
+      // interval k adds h_k^2/12 (D_k - D_{k+1}); for k = n-2, D_{k+1} := D_k.
+      for (int k = max(0, m - 2); k <= min(n - 2, m); ++k) {
+        double hk = x[k + 1] - x[k];
+        double c = hk * hk / 12.0;
+        double dDk = (m == k + 1 ? 1.0 / hk : 0.0) - (m == k ? 1.0 / hk : 0.0);
+        double dDk1;
+        if (k + 2 <= n - 1) {
+          double h1 = x[k + 2] - x[k + 1];
+          dDk1 = (m == k + 2 ? 1.0 / h1 : 0.0) - (m == k + 1 ? 1.0 / h1 : 0.0);
+        } else {
+          dDk1 = dDk;
+        }
+        s += c * (dDk - dDk1);
+      }
+    }
+  }
+  w[m] = s * x[m] * x[m];
+}
+
+// Ratio table c_n = prod_{k=1..n} (1 - 1/(2k)), n = 0..nmax, each entry in
+// double-double then rounded: (l1 l2 l3;000)^2 = c_{g-l1} c_{g-l2} c_{g-l3} /
+// ((2g+1) c_g) with 2g = l1 + l2 + l3 (the factorial form, Section 2.1).
+__global__ void k_threej_table(int nmax, double *__restrict__ c) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n > nmax) return;
+  dd p = {1.0, 0.0};
+  for (int k = 1; k <= n; ++k) {
+    // 1 - 1/(2k) = (2k - 1)/(2k): exact numerator, one dd division
+    p = dd_div_d(dd_mul_d(p, 2.0 * k - 1.0), 2.0 * k);
+  }
+  c[n] = p.hi + p.lo;
+}
+
+// ---- launchers -------------------------------------------------------------
+cudaError_t launch_gl_nodes(int n, double *mu, double *om, cudaStream_t st) {
+  int half = (n + 1) / 2;
+  k_gl_nodes<<<cdiv(half, 32), 32, 0, st>>>(n, mu, om);
+  return cudaGetLastError();
+}
+cudaError_t launch_legendre_table(int n_mu, const double *mu, int l_min, int l_max,
+                                  const double *w_l, double *A, cudaStream_t st) {
+  k_legendre_table<<<cdiv(n_mu, LEG_NODES), LEG_NODES, 0, st>>>(n_mu, mu, l_min, l_max, w_l, A);
+  return cudaGetLastError();
+}
+cudaError_t launch_x_weights(int kind, int n, const double *x, double *w, cudaStream_t st) {
+  k_x_weights<<<cdiv(n, 128), 128, 0, st>>>(kind, n, x, w);
+  return cudaGetLastError();
+}
+cudaError_t launch_threej_table(int nmax, double *c, cudaStream_t st) {
+  k_threej_table<<<cdiv(nmax + 1, 128), 128, 0, st>>>(nmax, c);
+  return cudaGetLastError();
+}
+
+}  // namespace modal

@@ -1,0 +1,522 @@
+// modal_abi.cu -- the extern "C" boundary of libmodal: handle, scratch,
+// argument validation and the drivers that chain the kernels of the
+// separable path (rows a1-a7), the direct path (a8), the adjoint (a9) and
+// the batched form (a10).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "direct.cuh"
+#include "kernels.cuh"
+#include "tc.cuh"
+#include "backward.cuh"
+#include "profile.cuh"
+
+using namespace modal;
+
+struct modal_handle {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  void *slot_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t slot_bytes[4] = {0, 0, 0, 0};
+  int64_t *pinned_i64 = nullptr;  // host-pinned word for the direct path's triple count
+  Profiler prof;
+};
+
+// time the launch(es) of the enclosing block when profiling is on
+#define PROF(h, name, st) ProfScope _prof_scope((h)->prof.on ? &(h)->prof : nullptr, name, st)
+
+static thread_local std::string g_err_nohandle;
+
+static int fail(modal_handle *h, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_err_nohandle = buf;
+  return code;
+}
+
+#define CK(expr)                                                                              \
+  do {                                                                                        \
+    cudaError_t _e = (expr);                                                                  \
+    if (_e != cudaSuccess) return fail(h, MODAL_ECUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
+  } while (0)
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Grow-only device scratch per slot (0: general, 1: direct-path triples,
+// 2: batched problem table).  Growing frees the old block (cudaFree waits for
+// the device), so pointers from an earlier call must not be reused.
+static int ws_get(modal_handle *h, int slot, size_t bytes, void **out) {
+  if (bytes == 0) bytes = 256;
+  if (h->slot_bytes[slot] < bytes) {
+    if (h->slot_ptr[slot]) cudaFree(h->slot_ptr[slot]);
+    h->slot_ptr[slot] = nullptr;
+    h->slot_bytes[slot] = 0;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MODAL_ENOMEM, "cudaMalloc(%zu bytes) for scratch failed: %s", bytes,
+                  cudaGetErrorString(e));
+    }
+    h->slot_ptr[slot] = p;
+    h->slot_bytes[slot] = bytes;
+  }
+  *out = h->slot_ptr[slot];
+  return MODAL_OK;
+}
+
+struct Bump {
+  char *p;
+  size_t off = 0;
+  template <typename T>
+  T *take(size_t n) {
+    T *r = reinterpret_cast<T *>(p + off);
+    off += align256(sizeof(T) * (n ? n : 1));
+    return r;
+  }
+};
+
+static int check_handle(modal_handle *h) {
+  if (!h) return fail(nullptr, MODAL_EINVAL, "null handle");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
+    return fail(h, MODAL_EINVAL, "handle was created on device %d, current device is %d", h->device, dev);
+  return MODAL_OK;
+}
+
+static int n_mu_exact(int l_max) { return (3 * l_max + 2) / 2; }
+
+static int validate_problem(modal_handle *h, const modal_problem *p, bool need_modes, bool need_xw) {
+  if (!p) return fail(h, MODAL_EINVAL, "null problem");
+  if (p->l_min < 0 || p->l_max < p->l_min)
+    return fail(h, MODAL_EINVAL, "bad l range [%d, %d]", p->l_min, p->l_max);
+  if (p->nb_late < 1 || p->nb_prim < 1 || p->nb_late > 64 || p->nb_prim > 64)
+    return fail(h, MODAL_EINVAL, "basis sizes must be in [1, 64] (got %d, %d)", p->nb_late, p->nb_prim);
+  if (p->n_x < 0 || p->n_late < 0 || p->n_prim < 0)
+    return fail(h, MODAL_EINVAL, "negative size");
+  if (!p->q || !p->w_l) return fail(h, MODAL_EINVAL, "null q or w_l");
+  if (p->n_x > 0 && !p->qt) return fail(h, MODAL_EINVAL, "null qt");
+  if (need_xw && p->n_x > 0 && !p->x_w) return fail(h, MODAL_EINVAL, "null x_w");
+  if (need_modes && ((p->n_late && !p->late_modes) || (p->n_prim && !p->prim_modes)))
+    return fail(h, MODAL_EINVAL, "null mode list");
+  return MODAL_OK;
+}
+
+static int resolve_opts(modal_handle *h, const modal_problem *p, const modal_opts *o, int &n_mu, int &prec,
+                        int &x_chunk) {
+  n_mu = (o && o->n_mu > 0) ? o->n_mu : n_mu_exact(p->l_max);
+  prec = o ? o->precision : MODAL_PREC_FP64;
+  x_chunk = o ? o->x_chunk : 0;
+  if (o && o->n_mu < 0) return fail(h, MODAL_EINVAL, "n_mu < 0");
+  if (n_mu < n_mu_exact(p->l_max) && !(o && o->allow_inexact_gl))
+    return fail(h, MODAL_EINVAL,
+                "n_mu = %d is below ceil((3 l_max + 1)/2) = %d: the Gauss-Legendre rule would not be exact "
+                "(set allow_inexact_gl to accept)",
+                n_mu, n_mu_exact(p->l_max));
+  if (prec != MODAL_PREC_FP64 && prec != MODAL_PREC_FP32 && prec != MODAL_PREC_OZAKI_BF16)
+    return fail(h, MODAL_EINVAL, "unknown precision %d", prec);
+  if (x_chunk < 0) return fail(h, MODAL_EINVAL, "x_chunk < 0");
+  return MODAL_OK;
+}
+
+extern "C" {
+
+int modal_handle_create(modal_handle **out) {
+  if (!out) return fail(nullptr, MODAL_EINVAL, "null output pointer");
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, MODAL_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return fail(nullptr, MODAL_ECUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+  modal_handle *h = new modal_handle();
+  h->device = dev;
+  h->num_sms = prop.multiProcessorCount;
+  e = cudaMallocHost((void **)&h->pinned_i64, sizeof(int64_t));
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, MODAL_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return MODAL_OK;
+}
+
+int modal_handle_destroy(modal_handle *h) {
+  if (!h) return MODAL_OK;
+  for (int s = 0; s < 4; ++s)
+    if (h->slot_ptr[s]) cudaFree(h->slot_ptr[s]);
+  if (h->pinned_i64) cudaFreeHost(h->pinned_i64);
+  tc_release(h->device);
+  delete h;
+  return MODAL_OK;
+}
+
+const char *modal_last_error(const modal_handle *h) {
+  if (!h) return g_err_nohandle.c_str();
+  return h->err.c_str();
+}
+
+int modal_profile_enable(modal_handle *h, int32_t enable) {
+  if (int r = check_handle(h)) return r;
+  h->prof.on = enable != 0;
+  return MODAL_OK;
+}
+
+int modal_profile_read(modal_handle *h, int32_t max_entries, char *names, int64_t *launches,
+                       double *total_ms, int32_t *n_out) {
+  if (int r = check_handle(h)) return r;
+  if (max_entries < 0 || (max_entries > 0 && (!names || !launches || !total_ms)) || !n_out)
+    return fail(h, MODAL_EINVAL, "bad output arrays");
+  auto m = h->prof.drain();
+  int n = 0;
+  for (auto &kv : m) {
+    if (n >= max_entries) break;
+    strncpy(names + 32 * n, kv.first.c_str(), 31);
+    names[32 * n + 31] = 0;
+    launches[n] = kv.second.first;
+    total_ms[n] = kv.second.second;
+    ++n;
+  }
+  *n_out = n;
+  return MODAL_OK;
+}
+
+int modal_handle_reserve(modal_handle *h, size_t bytes) {
+  if (int r = check_handle(h)) return r;
+  void *p;
+  return ws_get(h, 0, bytes, &p);
+}
+
+int modal_gl_nodes(modal_handle *h, int32_t n_mu, double *mu, double *om, modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (n_mu < 1) return fail(h, MODAL_EINVAL, "n_mu must be >= 1");
+  if (!mu || !om) return fail(h, MODAL_EINVAL, "null output");
+  CK(launch_gl_nodes(n_mu, mu, om, (cudaStream_t)stream));
+  return MODAL_OK;
+}
+
+int modal_legendre_table(modal_handle *h, int32_t n_mu, const double *mu, int32_t l_min, int32_t l_max,
+                         const double *w_l, double *A, modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (n_mu < 0 || l_min < 0 || l_max < l_min) return fail(h, MODAL_EINVAL, "bad sizes");
+  if (!mu || !A) return fail(h, MODAL_EINVAL, "null pointer");
+  if (n_mu == 0) return MODAL_OK;
+  CK(launch_legendre_table(n_mu, mu, l_min, l_max, w_l, A, (cudaStream_t)stream));
+  return MODAL_OK;
+}
+
+int modal_x_weights(modal_handle *h, int32_t kind, int32_t n_x, const double *x, double *w,
+                    modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (kind != MODAL_XW_TRAPEZOID && kind != MODAL_XW_HERMITE) return fail(h, MODAL_EINVAL, "unknown kind");
+  if (n_x < 0) return fail(h, MODAL_EINVAL, "n_x < 0");
+  if (n_x == 0) return MODAL_OK;
+  if (!x || !w) return fail(h, MODAL_EINVAL, "null pointer");
+  CK(launch_x_weights(kind, n_x, x, w, (cudaStream_t)stream));
+  return MODAL_OK;
+}
+
+int modal_contract_l(modal_handle *h, const modal_problem *p, int32_t n_mu, const double *A, double *M,
+                     modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (int r = validate_problem(h, p, false, false)) return r;
+  if (n_mu < 0 || !A || !M) return fail(h, MODAL_EINVAL, "bad A/M/n_mu");
+  if (n_mu == 0 || p->n_x == 0) return MODAL_OK;
+  SepShape s{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};
+  CK(launch_contract_l<double>(s, A, p->q, p->qt, 0, p->n_x, M, (cudaStream_t)stream));
+  return MODAL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// separable projection (Eq. 2D)
+// ---------------------------------------------------------------------------
+struct SepPlan {
+  SepShape s;
+  int prec;
+  int nxc;      // radial points per chunk
+  int ksplit;   // K split of the SIMT triple product
+  size_t elem;  // bytes per M element
+  int64_t Gsize;
+  size_t bytes;
+};
+
+static int plan_separable(modal_handle *h, const modal_problem *p, const modal_opts *o, SepPlan &pl,
+                          int num_sms) {
+  int n_mu, prec, xch;
+  if (int r = resolve_opts(h, p, o, n_mu, prec, xch)) return r;
+  pl.s = SepShape{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};
+  pl.prec = prec;
+  pl.elem = (prec == MODAL_PREC_FP64) ? sizeof(double) : sizeof(float);
+  const int64_t nblp = (int64_t)p->nb_late * p->nb_prim;
+  if (xch > 0) {
+    pl.nxc = xch < p->n_x ? xch : p->n_x;
+  } else {
+    const int64_t budget = (int64_t)2 << 30;  // 2 GiB of M per chunk
+    int64_t per_x = (int64_t)n_mu * nblp * (int64_t)pl.elem;
+    int64_t c = budget / (per_x > 0 ? per_x : 1);
+    pl.nxc = (int)(c < 1 ? 1 : (c > p->n_x ? p->n_x : c));
+  }
+  if (pl.nxc < 1) pl.nxc = 1;
+  GLayout g = make_glayout(p->nb_late, p->nb_prim);
+  pl.Gsize = g.size();
+  pl.ksplit = triple_ksplit(pl.s, pl.nxc, num_sms);
+  const int nchunks = p->n_x > 0 ? (p->n_x + pl.nxc - 1) / pl.nxc : 0;
+  const bool need_part = pl.ksplit > 1 || nchunks > 1;
+  size_t b = 0;
+  b += 2 * align256(sizeof(double) * n_mu);                      // mu, om
+  b += align256(sizeof(double) * (size_t)n_mu * pl.s.L);          // A
+  b += align256(pl.elem * (size_t)pl.nxc * n_mu * nblp);          // M chunk
+  b += align256(sizeof(double) * (size_t)pl.Gsize);               // G
+  if (need_part) b += align256(sizeof(double) * (size_t)pl.Gsize * pl.ksplit);
+  if (prec == MODAL_PREC_OZAKI_BF16) b += tc_scratch_bytes(pl.s, pl.nxc);
+  pl.bytes = b + 1024;
+  return MODAL_OK;
+}
+
+static int run_separable(modal_handle *h, const modal_problem *p, const SepPlan &pl, double *gamma,
+                         cudaStream_t st, void *scratch) {
+  const SepShape &s = pl.s;
+  Bump bp{(char *)scratch};
+  double *mu = bp.take<double>(s.n_mu), *om = bp.take<double>(s.n_mu);
+  double *A = bp.take<double>((size_t)s.n_mu * s.L);
+  void *M = bp.take<char>(pl.elem * (size_t)pl.nxc * s.n_mu * s.nbl * s.nbp);
+  double *G = bp.take<double>((size_t)pl.Gsize);
+  const int nchunks = (p->n_x + pl.nxc - 1) / pl.nxc;
+  const bool need_part = pl.ksplit > 1 || nchunks > 1;
+  double *Gpart = need_part ? bp.take<double>((size_t)pl.Gsize * pl.ksplit) : nullptr;
+  void *tcs = (pl.prec == MODAL_PREC_OZAKI_BF16) ? bp.take<char>(tc_scratch_bytes(s, pl.nxc)) : nullptr;
+
+  {
+    PROF(h, "gl_nodes", st);
+    CK(launch_gl_nodes(s.n_mu, mu, om, st));                                   // a1
+  }
+  {
+    PROF(h, "legendre_table", st);
+    CK(launch_legendre_table(s.n_mu, mu, s.l_min, s.l_max, p->w_l, A, st));      // a2
+  }
+  if (p->n_x == 0) {
+    CK(launch_zero(G, (size_t)pl.Gsize, st));
+  }
+  for (int c = 0; c < nchunks; ++c) {
+    const int x0 = c * pl.nxc;
+    const int nxc = (p->n_x - x0) < pl.nxc ? (p->n_x - x0) : pl.nxc;
+    if (pl.prec == MODAL_PREC_FP64) {
+      {
+        PROF(h, "contract_l_f64", st);
+        CK(launch_contract_l<double>(s, A, p->q, p->qt, x0, nxc, (double *)M, st));         // a4+a5
+      }
+      PROF(h, "triple_f64", st);
+      CK(launch_triple<double>(s, (double *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
+                               h->num_sms, st));                                            // a6
+    } else if (pl.prec == MODAL_PREC_FP32) {
+      {
+        PROF(h, "contract_l_f32", st);
+        CK(launch_contract_l<float>(s, A, p->q, p->qt, x0, nxc, (float *)M, st));
+      }
+      PROF(h, "triple_f32", st);
+      CK(launch_triple<float>(s, (float *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
+                              h->num_sms, st));
+    } else {
+      int r = tc_separable_chunk(s, A, p->q, p->qt, om, p->x_w, x0, nxc, (float *)M, G, c > 0, tcs,
+                                 h->num_sms, st);
+      if (r) return fail(h, r, "tensor-core chunk failed: %s", tc_last_error());
+    }
+  }
+  PROF(h, "gather", st);
+  CK(launch_gather(s, G, p->late_modes, p->prim_modes, p->n_late, p->n_prim, 1.0 / (48.0 * MODAL_PI), gamma,
+                   st));                                                                    // a7
+  return MODAL_OK;
+}
+
+int modal_workspace_size(const modal_problem *p, const modal_opts *o, int for_backward, size_t *bytes) {
+  if (!bytes) return fail(nullptr, MODAL_EINVAL, "null output");
+  if (int r = validate_problem(nullptr, p, false, false)) return r;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  SepPlan pl;
+  if (int r = plan_separable(nullptr, p, o, pl, sms)) return r;
+  size_t b = pl.bytes;
+  if (for_backward) {
+    size_t bb = backward_scratch_bytes(pl.s, pl.nxc, pl.prec);
+    b = bb > b ? bb : b;
+  }
+  *bytes = b;
+  return MODAL_OK;
+}
+
+int modal_project_separable(modal_handle *h, const modal_problem *p, const modal_opts *o, double *gamma,
+                            modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (int r = validate_problem(h, p, true, true)) return r;
+  if ((int64_t)p->n_late * p->n_prim == 0) return MODAL_OK;
+  if (!gamma) return fail(h, MODAL_EINVAL, "null gamma");
+  SepPlan pl;
+  if (int r = plan_separable(h, p, o, pl, h->num_sms)) return r;
+  void *scratch;
+  if (int r = ws_get(h, 0, pl.bytes, &scratch)) return r;
+  return run_separable(h, p, pl, gamma, (cudaStream_t)stream, scratch);
+}
+
+int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_problem *probs,
+                                    const modal_opts *o, double *const *gammas, modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (n < 0) return fail(h, MODAL_EINVAL, "n < 0");
+  if (n == 0) return MODAL_OK;
+  if (!probs || !gammas) return fail(h, MODAL_EINVAL, "null probs/gammas");
+  std::vector<SepPlan> plans(n);
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) {
+    if (int r = validate_problem(h, &probs[i], true, true)) return fail(h, r, "problem %d: %s", i, h->err.c_str());
+    if (int r = plan_separable(h, &probs[i], o, plans[i], h->num_sms)) return fail(h, r, "problem %d: %s", i, h->err.c_str());
+    need = plans[i].bytes > need ? plans[i].bytes : need;
+  }
+  void *scratch;
+  if (int r = ws_get(h, 0, need, &scratch)) return r;
+  for (int i = 0; i < n; ++i) {
+    if ((int64_t)probs[i].n_late * probs[i].n_prim == 0) continue;
+    if (!gammas[i]) return fail(h, MODAL_EINVAL, "null gamma for problem %d", i);
+    if (int r = run_separable(h, &probs[i], plans[i], gammas[i], (cudaStream_t)stream, scratch)) return r;
+  }
+  return MODAL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// direct projection (Eq. 3D)
+// ---------------------------------------------------------------------------
+int modal_project_direct(modal_handle *h, const modal_problem *p, const int32_t *l_grid, const double *l_dw,
+                         int32_t ng, int32_t mode, double *gamma, modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (int r = validate_problem(h, p, true, true)) return r;
+  if (mode != MODAL_W_EXACT_3J && mode != MODAL_W_SMOOTH_GOSPER) return fail(h, MODAL_EINVAL, "unknown weight mode");
+  if (ng < 0) return fail(h, MODAL_EINVAL, "n_grid < 0");
+  if ((int64_t)p->n_late * p->n_prim == 0) return MODAL_OK;
+  if (!gamma) return fail(h, MODAL_EINVAL, "null gamma");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = p->l_max - p->l_min + 1;
+  if (ng == 0 || p->n_x == 0) {
+    CK(launch_zero(gamma, (size_t)p->n_late * p->n_prim, st));
+    return MODAL_OK;
+  }
+  if (!l_grid) return fail(h, MODAL_EINVAL, "null l_grid");
+  const int64_t npairs = (int64_t)ng * ng;
+  const int cmax = 3 * p->l_max / 2 + 2;
+  // phase 1: qt transpose, 3j table, counts, scan
+  size_t b1 = 0;
+  b1 += align256(sizeof(double) * (size_t)L * p->n_x * p->nb_prim);
+  b1 += 2 * align256(sizeof(int64_t) * (size_t)npairs);
+  b1 += align256(sizeof(double) * (size_t)(cmax + 1));
+  size_t scan_b = scan_tmp_bytes(npairs);
+  b1 += align256(scan_b) + 1024;
+  void *s1;
+  if (int r = ws_get(h, 0, b1, &s1)) return r;
+  Bump bp{(char *)s1};
+  double *qtT = bp.take<double>((size_t)L * p->n_x * p->nb_prim);
+  int64_t *counts = bp.take<int64_t>((size_t)npairs);
+  int64_t *offs = bp.take<int64_t>((size_t)npairs);
+  double *ctab = bp.take<double>((size_t)cmax + 1);
+  void *scan_tmp = bp.take<char>(scan_b);
+
+  {
+    int64_t rows = (int64_t)p->n_x * p->nb_prim, cols = L;
+    dim3 grid((unsigned)cdiv64(cols, 32), (unsigned)cdiv64(rows, 32));
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(p->qt, rows, cols, qtT);
+    CK(cudaGetLastError());
+  }
+  CK(launch_threej_table(cmax, ctab, st));
+  k_direct_count<<<(unsigned)cdiv64(npairs, 256), 256, 0, st>>>(ng, l_grid, mode, counts);
+  CK(cudaGetLastError());
+  CK(scan_exclusive_i64(scan_tmp, scan_b, counts, offs, npairs, st));
+  // total = offs[last] + counts[last]; one synchronisation to size the batches
+  int64_t last_off = 0, last_cnt = 0;
+  CK(cudaMemcpyAsync(h->pinned_i64, offs + npairs - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  last_off = *h->pinned_i64;
+  CK(cudaMemcpyAsync(h->pinned_i64, counts + npairs - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  last_cnt = *h->pinned_i64;
+  const int64_t ntri = last_off + last_cnt;
+  if (ntri == 0) {
+    CK(launch_zero(gamma, (size_t)p->n_late * p->n_prim, st));
+    return MODAL_OK;
+  }
+  // phase 2: triples, weights and batch buffers (slot 1)
+  int T = 32768;
+  {
+    int64_t cap = ((int64_t)1 << 30) / (8 * (int64_t)(p->n_late + p->n_prim));
+    if (cap < 256) cap = 256;
+    if (T > cap) T = (int)(cap / 32 * 32);
+    if (T > ntri) T = (int)ntri;
+  }
+  size_t b2 = align256(sizeof(int) * 3 * (size_t)ntri) + align256(sizeof(double) * (size_t)ntri) +
+              align256(sizeof(double) * (size_t)T * p->n_late) + align256(sizeof(double) * (size_t)T * p->n_prim) +
+              1024;
+  void *s2;
+  if (int r = ws_get(h, 1, b2, &s2)) return r;
+  Bump b2p{(char *)s2};
+  int *tri = b2p.take<int>(3 * (size_t)ntri);
+  double *z = b2p.take<double>((size_t)ntri);
+  double *Yb = b2p.take<double>((size_t)T * p->n_late);
+  double *Xb = b2p.take<double>((size_t)T * p->n_prim);
+  k_direct_fill<<<(unsigned)cdiv64(npairs, 256), 256, 0, st>>>(ng, l_grid, l_dw, p->w_l, p->l_min, ctab, mode,
+                                                                offs, tri, z);
+  CK(cudaGetLastError());
+  const int nbp = p->nb_prim, P2 = nbp * (nbp + 1) / 2;
+  int xc = 16;
+  size_t smem = 0;
+  for (;; xc /= 2) {
+    smem = sizeof(double) * ((size_t)nbp * P2 + (size_t)xc * P2 + 3 * (size_t)xc * nbp);
+    if (smem <= 200 * 1024 || xc == 1) break;
+  }
+  if (smem > 200 * 1024) return fail(h, MODAL_EUNSUPPORTED, "primordial basis too large for the direct path");
+  CK(cudaFuncSetAttribute(k_direct_X, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int64_t t0 = 0; t0 < ntri; t0 += T) {
+    int nb = (int)((ntri - t0) < T ? (ntri - t0) : T);
+    {
+      PROF(h, "direct_X", st);
+      k_direct_X<<<nb, 256, smem, st>>>(nbp, p->n_x, p->l_min, qtT, p->x_w, tri, t0, T, xc, p->prim_modes,
+                                        p->n_prim, Xb);
+      CK(cudaGetLastError());
+    }
+    {
+      PROF(h, "direct_Y", st);
+      int64_t ny = (int64_t)p->n_late * T;
+      k_direct_Y<<<(unsigned)cdiv64(ny, 256), 256, 0, st>>>(p->nb_late, L, p->l_min, p->q, tri, z, t0, T, nb,
+                                                            p->late_modes, p->n_late, Yb);
+      CK(cudaGetLastError());
+    }
+    PROF(h, "direct_gemm", st);
+    CK(launch_gemm_nt_f64(p->n_late, p->n_prim, nb, Yb, T, Xb, T, gamma, p->n_prim, t0 > 0, st));
+  }
+  return MODAL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint (not in the paper; from Eq. 2D and Eq. legendre)
+// ---------------------------------------------------------------------------
+int modal_project_backward(modal_handle *h, const modal_problem *p, const modal_opts *o,
+                           const double *dL_dgamma, double *dL_dqt, double *dL_dq, modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (int r = validate_problem(h, p, true, true)) return r;
+  if (!dL_dgamma || !dL_dqt) return fail(h, MODAL_EINVAL, "null dL_dgamma or dL_dqt");
+  SepPlan pl;
+  if (int r = plan_separable(h, p, o, pl, h->num_sms)) return r;
+  size_t bytes = backward_scratch_bytes(pl.s, pl.nxc, pl.prec);
+  void *scratch;
+  if (int r = ws_get(h, 0, bytes, &scratch)) return r;
+  int r = run_backward(pl.s, pl.nxc, pl.prec, p, dL_dgamma, dL_dqt, dL_dq, scratch, h->num_sms,
+                       (cudaStream_t)stream);
+  if (r) return fail(h, r, "adjoint failed: %s", backward_last_error());
+  return MODAL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+"""GPU parity of the direct path (row a8, Eq. 3D) against the FP64 oracle."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic as syn
+from tests._golden import delta_cases
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def normwise(a, ref):
+    a = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else a
+    return float(np.abs(a - ref).max() / np.abs(ref).max())
+
+
+@pytest.fixture(scope="module")
+def mg(gpu):
+    import paper_1503_08809_gb300 as mg
+    return mg
+
+
+def test_direct_dense_cpu_size(mg):
+    P = syn.cpu_size()
+    dp = mg.DeviceProblem.from_host(P)
+    g = mg.project_direct(dp)
+    assert normwise(g, oracle.direct(P)) < TOL
+    # the two forms agree on a dense grid (Section 2.2)
+    assert normwise(g, oracle.separable(P)) < TOL
+    assert normwise(mg.project_separable(dp), g.cpu().numpy()) < TOL
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_direct_sparse_grid(mg, mode):
+    P = syn.make_problem(160, 4, 9, seed=3, nb_prim=3)
+    lg, dw = syn.sparse_l_grid(160)
+    g = mg.project_direct(mg.DeviceProblem.from_host(P), lg, dw, weight_mode=mode)
+    ref = oracle.direct(P, l_grid=lg, l_dw=dw, weight_mode=mode)
+    assert normwise(g, ref) < TOL
+
+
+@pytest.mark.parametrize("case", list(delta_cases()), ids=lambda c: c[0])
+def test_direct_golden(mg, case):
+    name, P, expected = case
+    dp = mg.DeviceProblem.from_host(P, x_w=np.ones(1))
+    g = float(mg.project_direct(dp)[0, 0])
+    assert g == pytest.approx(expected, rel=1e-13, abs=1e-15 / (70 * math.pi))
+
+
+def test_direct_edge_cases(mg):
+    P = syn.make_problem(10, 2, 3, seed=1)
+    dp = mg.DeviceProblem.from_host(P)
+    # empty grid -> zeros
+    g = mg.project_direct(dp, l_grid=np.zeros(0, dtype=np.int32))
+    assert torch.count_nonzero(g) == 0
+    # a grid whose triples all break the triangle condition -> zeros
+    g = mg.project_direct(dp, l_grid=np.array([2, 9]), l_dw=np.ones(2))
+    ref = oracle.direct(P, l_grid=np.array([2, 9]), l_dw=np.ones(2))
+    assert np.allclose(g.cpu().numpy(), ref, rtol=1e-12, atol=0)
+    # single point grid (only (l,l,l))
+    g = mg.project_direct(dp, l_grid=np.array([4]), l_dw=np.array([2.5]))
+    ref = oracle.direct(P, l_grid=np.array([4]), l_dw=np.array([2.5]))
+    assert normwise(g, ref) < TOL
+
+
+def test_direct_planck_sparse_sampled(mg):
+    """Planck-scale direct check on the sparse grid (every l to 50, step 2 to
+    200, step 5 to 500, step 10 above): full Gamma' on the GPU, sampled
+    rows/columns from the oracle."""
+    P = syn.planck_size()
+    lg, dw = syn.sparse_l_grid(P.l_max)
+    g = mg.project_direct(mg.DeviceProblem.from_host(P), lg, dw).cpu().numpy()
+    rows = np.array([0, 5, 100, 777, 1539])
+    cols = np.array([3, 400, 1200])
+    ref = oracle.direct(P, l_grid=lg, l_dw=dw, late=P.late_modes[rows], prim=P.prim_modes[cols])
+    got = g[np.ix_(rows, cols)]
+    assert np.abs(got - ref).max() / np.abs(ref).max() < TOL
+    assert np.isfinite(g).all()

@@ -371,3 +371,15 @@ def test_backward_linearity_in_cotangent():
     a2, _ = oracle.backward(P, g2, want_dq=False)
     a3, _ = oracle.backward(P, 2 * g1 - g2, want_dq=False)
     assert np.allclose(a3, 2 * a1 - a2, rtol=1e-12, atol=1e-12 * np.abs(a1).max())
+
+
+def test_M_table_matches_library_legendre():
+    """P_{ii'} of Eq. legendre from the oracle equals the same sum formed with
+    numpy's legval for P_l (a library routine)."""
+    P = syn.make_problem(16, 3, 4, seed=12, nb_prim=2)
+    mu, _ = oracle.gl_nodes(P.n_mu)
+    M = oracle.M_table(P, mu)
+    ls = np.arange(P.l_min, P.l_max + 1)
+    Pl = np.array([[npleg.legval(m, np.eye(P.l_max + 1)[l]) for l in ls] for m in mu])
+    ref = np.einsum("jl,l,al,xpl->xjap", Pl, P.w_l, P.q, P.qt)
+    assert np.abs(M - ref).max() / np.abs(ref).max() < 1e-13
