@@ -138,31 +138,31 @@ def measured_peaks():
 
 # ---------------------------------------------------------------------------
 def cpu_baseline(P, seconds: float):
-    """The FP64 oracle as it stands, on a bounded sample of the workload: one
-    radial point (the one nearest the last-scattering peak) and the first K
-    Gauss-Legendre nodes, all 1540 x 1540 modes; K is sized for ~`seconds` of
-    work.  Returns slices/s (slices = K here) and a description."""
+    """The FP64 oracle as it stands, on a bounded sample of the workload: the
+    radial points nearest the last-scattering peak and the first K
+    Gauss-Legendre nodes, all 1540 x 1540 modes, sized for ~`seconds` of work.
+    Returns (slices/s, seconds, sample description, threads)."""
     import oracle
     import synthetic as syn
     mu, om = oracle.gl_nodes(P.n_mu)
-    xi = int(np.argmin(np.abs(P.x - syn.X_PEAK)))
-    Ps = syn.Problem(**{**P.__dict__, "qt": P.qt[xi:xi + 1].copy(), "x": P.x[xi:xi + 1],
-                        "n_x": 1})
-    xw = np.ones(1)
+    order = np.argsort(np.abs(P.x - syn.X_PEAK))
 
-    def run(k):
+    def run(nx, k):
+        idx = np.sort(order[:nx])
+        Ps = syn.Problem(**{**P.__dict__, "qt": P.qt[idx].copy(), "x": P.x[idx], "n_x": nx})
         t0 = time.perf_counter()
-        oracle.separable(Ps, xw=xw, mu=mu[:k], om=om[:k])
+        oracle.separable(Ps, xw=np.ones(nx), mu=mu[:k], om=om[:k])
         return time.perf_counter() - t0
 
-    k = 2
-    t = run(k)
-    while t < 1.0 and k < P.n_mu:
-        k = min(P.n_mu, k * 4)
-        t = run(k)
-    k = int(max(1, min(P.n_mu, k * seconds / max(t, 1e-3))))
-    t = run(k)
-    return k / t, t, k, oracle.num_threads()
+    k0 = min(64, P.n_mu)
+    per_slice = run(1, k0) / k0
+    want = max(1, int(seconds / max(per_slice, 1e-9)))
+    nx = min(P.n_x, max(1, want // P.n_mu))
+    k = P.n_mu if want >= P.n_mu else want
+    t = run(nx, k)
+    desc = (f"{nx} of {P.n_x} radial points x first {k} of {P.n_mu} GL nodes, all "
+            f"{P.n_late}x{P.n_prim} modes ({t:.1f} s)")
+    return nx * k / t, t, desc, oracle.num_threads()
 
 
 def run_reference(args):
@@ -172,13 +172,13 @@ def run_reference(args):
     import synthetic as syn
     P = syn.planck_size(n_x=args.n_x)
     vals = []
+    desc, cores = "", 1
     for i in range(args.warmup + args.steps):
-        v, t, k, cores = cpu_baseline(P, args.cpu_seconds / max(1, args.steps))
+        v, t, desc, cores = cpu_baseline(P, args.cpu_seconds / max(1, args.steps))
         if i >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
-    sample = (f"1 of {P.n_x} radial points x first {k} of {P.n_mu} GL nodes, all "
-              f"{P.n_late}x{P.n_prim} modes, per step")
+    sample = desc + " per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "slices/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * P.slices / value, "higher_is_better": True, "scaling": "weak",
@@ -311,10 +311,8 @@ def run_ours(args):
         return
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        v, t, k, cores = cpu_baseline(P, args.cpu_seconds)
-        cpu = {"value": v, "unit": "slices/s", "cores": cores, "kind": "oracle",
-               "sample": f"1 of {P.n_x} radial points x first {k} of {P.n_mu} GL nodes, all "
-                         f"{P.n_late}x{P.n_prim} modes ({t:.1f} s)"}
+        v, t, desc, cores = cpu_baseline(P, args.cpu_seconds)
+        cpu = {"value": v, "unit": "slices/s", "cores": cores, "kind": "oracle", "sample": desc}
     line = {"metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -99,6 +99,19 @@ int modal_workspace_size(const modal_problem *prob, const modal_opts *opts,
  * CUDA graph so that no allocation happens during capture). */
 int modal_handle_reserve(modal_handle *h, size_t bytes);
 
+/* Waits for the work of earlier calls on this handle that carries a device
+ * status word and returns MODAL_ETIMEOUT if any bounded device-side wait of
+ * the tensor-core kernels gave up (their results are then not valid),
+ * MODAL_OK otherwise.  Kernels never trap or spin forever: each wait on an
+ * mbarrier is bounded (default ~2 s of SM clock) and on give-up the CTA
+ * stops issuing work, waits for its own copies in flight, frees its tensor
+ * memory and returns. */
+int modal_handle_status(modal_handle *h);
+/* Bound (in SM clock cycles) of those device-side waits for later calls on
+ * this handle; 0 restores the default.  A tiny bound makes the waits give up
+ * on purpose (used by the tests of the status path). */
+int modal_handle_set_wait_limit(modal_handle *h, int64_t cycles);
+
 /* Opt-in per-kernel timing: while enabled, the library records a CUDA event
  * pair on the call's stream around each kernel it launches (negligible
  * overhead; no synchronisation at record time).  modal_profile_read waits
@@ -114,7 +127,7 @@ int modal_profile_read(modal_handle *h, int32_t max_entries, char *names, int64_
 /* Gauss-Legendre nodes (ascending) and weights of order n_mu, for the mu
  * integral of Eq. 2D (Section 2.2: library nodes were not accurate enough,
  * so the nodes are refined in double-double and rounded once to FP64).
- * mu, om: device [n_mu].  n_mu >= 1. */
+ * mu, om: device [n_mu].  1 <= n_mu <= 6400 (MODAL_EUNSUPPORTED above). */
 int modal_gl_nodes(modal_handle *h, int32_t n_mu, double *mu, double *om,
                    modal_stream_t stream);
 
@@ -133,9 +146,11 @@ int modal_x_weights(modal_handle *h, int32_t kind, int32_t n_x, const double *x,
 /* l contraction of Eq. legendre for every (x, mu_j) slice:
  *   M[x][j][a][p] = sum_l A[j][l] q_a(l) q~_p(l, x),   A from modal_legendre_table.
  * A: device [n_mu][L]; M: device [n_x][n_mu][nb_late][nb_prim] FP64.
+ * precision: MODAL_PREC_FP64 (CUDA cores) or MODAL_PREC_OZAKI_BF16 (tcgen05
+ * with exponent-aligned BF16 slices; ~1e-11 normwise).
  * (prob->late_modes/prim_modes/x_w are not used.) */
 int modal_contract_l(modal_handle *h, const modal_problem *prob, int32_t n_mu,
-                     const double *A, double *M, modal_stream_t stream);
+                     const double *A, int32_t precision, double *M, modal_stream_t stream);
 
 /* ---- the projection ------------------------------------------------------ */
 

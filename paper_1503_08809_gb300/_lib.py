@@ -19,7 +19,7 @@ EXPORTS = [
     "modal_handle_reserve", "modal_gl_nodes", "modal_legendre_table", "modal_x_weights",
     "modal_contract_l", "modal_project_separable", "modal_project_direct",
     "modal_project_backward", "modal_project_separable_batched", "modal_profile_enable",
-    "modal_profile_read",
+    "modal_profile_read", "modal_handle_status", "modal_handle_set_wait_limit",
 ]
 
 
@@ -73,12 +73,14 @@ def lib():
         "modal_gl_nodes": [vp, i32, vp, vp, vp],
         "modal_legendre_table": [vp, i32, vp, i32, i32, vp, vp, vp],
         "modal_x_weights": [vp, i32, i32, vp, vp, vp],
-        "modal_contract_l": [vp, P, i32, vp, vp, vp],
+        "modal_contract_l": [vp, P, i32, vp, i32, vp, vp],
         "modal_project_separable": [vp, P, O, vp, vp],
         "modal_project_direct": [vp, P, vp, vp, i32, i32, vp, vp],
         "modal_project_backward": [vp, P, O, vp, vp, vp, vp],
         "modal_project_separable_batched": [vp, i32, P, O, ctypes.POINTER(vp), vp],
         "modal_profile_enable": [vp, i32],
+        "modal_handle_status": [vp],
+        "modal_handle_set_wait_limit": [vp, ctypes.c_int64],
         "modal_profile_read": [vp, i32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)],
     }

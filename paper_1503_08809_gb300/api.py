@@ -171,14 +171,30 @@ def x_weights(x: torch.Tensor, kind: int = _lib.XW_TRAPEZOID, handle=None):
     return w
 
 
-def contract_l(dp: DeviceProblem, n_mu: int, A: torch.Tensor, handle=None):
+def contract_l(dp: DeviceProblem, n_mu: int, A: torch.Tensor, precision: int = _lib.PREC_FP64,
+               handle=None):
     """modal_contract_l: M[x][j][a][p] (FP64)."""
     h = _h(handle, dp.device)
     M = torch.empty(dp.n_x, n_mu, dp.nb_late, dp.nb_prim, dtype=_f64, device=dp.device)
     s = dp.struct()
-    check(lib().modal_contract_l(h.ptr, ctypes.byref(s), int(n_mu), _ptr(A), _ptr(M),
-                                 _stream(dp.device)), h.ptr)
+    check(lib().modal_contract_l(h.ptr, ctypes.byref(s), int(n_mu), _ptr(A), int(precision),
+                                 _ptr(M), _stream(dp.device)), h.ptr)
     return M
+
+
+def handle_status(handle=None, device=None) -> int:
+    """modal_handle_status: MODAL_OK, or raise ModalError(ETIMEOUT) if a bounded
+    device-side wait of an earlier call gave up."""
+    h = _h(handle, device)
+    code = lib().modal_handle_status(h.ptr)
+    check(code, h.ptr)
+    return code
+
+
+def set_wait_limit(cycles: int, handle=None, device=None):
+    """modal_handle_set_wait_limit (0 restores the default bound)."""
+    h = _h(handle, device)
+    check(lib().modal_handle_set_wait_limit(h.ptr, int(cycles)), h.ptr)
 
 
 def project_separable(dp: DeviceProblem, precision: int = _lib.PREC_FP64, n_mu: int = 0,

@@ -203,11 +203,11 @@ __global__ void __launch_bounds__(256) k_gemm_ops(int64_t Mr, int64_t Nc, int64_
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   const int64_t kb = (int64_t)blockIdx.z * kps, ke = min(K, kb + kps);
   T acc[TM][TN];
-  double accd[TM][TN];
+  float hi[TM][TN], lo[TM][TN];  // double-FP32 running sum of FP32 chunk sums (FP32 form)
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) { acc[i][j] = 0; accd[i][j] = 0.0; }
+    for (int j = 0; j < TN; ++j) { acc[i][j] = 0; hi[i][j] = 0.f; lo[i][j] = 0.f; }
   int step = 0;
   for (int64_t k0 = kb; k0 < ke; k0 += BK, ++step) {
     for (int e = tid; e < BM * BK; e += NT) {
@@ -238,7 +238,14 @@ __global__ void __launch_bounds__(256) k_gemm_ops(int64_t Mr, int64_t Nc, int64_
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) { accd[i][j] += (double)acc[i][j]; acc[i][j] = 0; }
+        for (int j = 0; j < TN; ++j) {
+          float a = hi[i][j], b = (float)acc[i][j];
+          float s = a + b, bb = s - a;
+          float e = (a - (s - bb)) + (b - bb) + lo[i][j];
+          hi[i][j] = s + e;
+          lo[i][j] = e - (hi[i][j] - s);
+          acc[i][j] = 0;
+        }
     }
   }
 #pragma unroll
@@ -249,7 +256,7 @@ __global__ void __launch_bounds__(256) k_gemm_ops(int64_t Mr, int64_t Nc, int64_
     for (int j = 0; j < TN; ++j) {
       int64_t n = n0 + tx + j * TX;
       if (n >= Nc) continue;
-      double v = accd[i][j] + (double)acc[i][j];
+      double v = (double)hi[i][j] + (double)lo[i][j] + (double)acc[i][j];
       if (ATOMIC) atomicAdd(out + m * ldo + n, v);
       else out[m * ldo + n] = v;
     }

@@ -13,10 +13,16 @@ namespace modal {
 // then w = 2 / ((1 - mu^2) P_n'(mu)^2), P_n' = n (mu P_n - P_{n-1})/(mu^2-1),
 // in double-double, each rounded once to FP64.  Output ascending.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void leg_pair_d(int n, double x, double &pn, double &pm) {
+// Recurrence coefficients a_k = (2k+1)/(k+1), b_k = k/(k+1) (k >= 1) are
+// tabulated once per block in shared memory in double-double, so the inner
+// loops carry no division:  P_{k+1} = a_k mu P_k - b_k P_{k-1}.
+constexpr int GL_TPB = 8;  // few threads per block: spread the roots over all SMs
+
+__device__ __forceinline__ void leg_pair_tab_d(int n, double x, const dd *ca, const dd *cb, double &pn,
+                                               double &pm) {
   double p0 = 1.0, p1 = x;
   for (int k = 1; k < n; ++k) {
-    double p2 = ((2.0 * k + 1.0) * x * p1 - (double)k * p0) / (double)(k + 1);
+    double p2 = fma(ca[k].hi * x, p1, -cb[k].hi * p0);
     p0 = p1;
     p1 = p2;
   }
@@ -24,12 +30,10 @@ __device__ __forceinline__ void leg_pair_d(int n, double x, double &pn, double &
   pm = p0;
 }
 
-__device__ __forceinline__ void leg_pair_dd(int n, dd x, dd &pn, dd &pm) {
+__device__ __forceinline__ void leg_pair_tab_dd(int n, dd x, const dd *ca, const dd *cb, dd &pn, dd &pm) {
   dd p0 = {1.0, 0.0}, p1 = x;
   for (int k = 1; k < n; ++k) {
-    dd t = dd_mul_d(dd_mul(x, p1), 2.0 * k + 1.0);
-    t = dd_sub(t, dd_mul_d(p0, (double)k));
-    dd p2 = dd_div_d(t, (double)(k + 1));
+    dd p2 = dd_sub(dd_mul(ca[k], dd_mul(x, p1)), dd_mul(cb[k], p0));
     p0 = p1;
     p1 = p2;
   }
@@ -37,7 +41,14 @@ __device__ __forceinline__ void leg_pair_dd(int n, dd x, dd &pn, dd &pm) {
   pm = p0;
 }
 
-__global__ void k_gl_nodes(int n, double *__restrict__ mu, double *__restrict__ om) {
+__global__ void __launch_bounds__(GL_TPB) k_gl_nodes(int n, double *__restrict__ mu, double *__restrict__ om) {
+  extern __shared__ dd coef[];
+  dd *ca = coef, *cb = coef + n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    ca[k] = dd_div_d({2.0 * k + 1.0, 0.0}, (double)(k + 1));
+    cb[k] = dd_div_d({(double)k, 0.0}, (double)(k + 1));
+  }
+  __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int half = (n + 1) / 2;
   if (i >= half) return;
@@ -46,26 +57,28 @@ __global__ void k_gl_nodes(int n, double *__restrict__ mu, double *__restrict__ 
     om[0] = 2.0;
     return;
   }
-  double x = cos(MODAL_PI * ((double)i + 0.75) / ((double)n + 0.5));
-  for (int it = 0; it < 60; ++it) {
+  // i-th largest root: Tricomi's asymptotic start, then FP64 Newton
+  const double nn = (double)n;
+  double x = (1.0 - (nn - 1.0) / (8.0 * nn * nn * nn)) * cos(MODAL_PI * (4.0 * i + 3.0) / (4.0 * nn + 2.0));
+  for (int it = 0; it < 12; ++it) {
     double pn, pm;
-    leg_pair_d(n, x, pn, pm);
-    double dp = (double)n * (x * pn - pm) / (x * x - 1.0);
+    leg_pair_tab_d(n, x, ca, cb, pn, pm);
+    double dp = nn * (x * pn - pm) / (x * x - 1.0);
     double dx = pn / dp;
     x -= dx;
-    if (fabs(dx) <= 2e-16 * fabs(x)) break;
+    if (fabs(dx) <= 1e-15 * fabs(x)) break;
   }
+  // one Newton step in double-double squares the ~1e-16 error
   dd X = {x, 0.0};
   dd pn, pm, dp;
   const dd one = {1.0, 0.0};
-  for (int it = 0; it < 2; ++it) {
-    leg_pair_dd(n, X, pn, pm);
-    dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pn), pm), (double)n), dd_sub(dd_mul(X, X), one));
-    X = dd_sub(X, dd_div(pn, dp));
-  }
-  leg_pair_dd(n, X, pn, pm);
+  leg_pair_tab_dd(n, X, ca, cb, pn, pm);
   dd x2m1 = dd_sub(dd_mul(X, X), one);
-  dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pn), pm), (double)n), x2m1);
+  dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pn), pm), nn), x2m1);
+  X = dd_sub(X, dd_div(pn, dp));
+  leg_pair_tab_dd(n, X, ca, cb, pn, pm);
+  x2m1 = dd_sub(dd_mul(X, X), one);
+  dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pn), pm), nn), x2m1);
   dd w = dd_div({2.0, 0.0}, dd_mul(dd_neg(x2m1), dd_mul(dp, dp)));
   double xv = X.hi + X.lo, wv = w.hi + w.lo;
   if ((n & 1) && i == n / 2) {  // exact centre node of an odd rule
@@ -178,7 +191,11 @@ __global__ void k_threej_table(int nmax, double *__restrict__ c) {
 // ---- launchers -------------------------------------------------------------
 cudaError_t launch_gl_nodes(int n, double *mu, double *om, cudaStream_t st) {
   int half = (n + 1) / 2;
-  k_gl_nodes<<<cdiv(half, 32), 32, 0, st>>>(n, mu, om);
+  size_t smem = 2 * sizeof(dd) * (size_t)n;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;  // n > 6400: not supported
+  cudaError_t e = cudaFuncSetAttribute(k_gl_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gl_nodes<<<cdiv(half, GL_TPB), GL_TPB, smem, st>>>(n, mu, om);
   return cudaGetLastError();
 }
 cudaError_t launch_legendre_table(int n_mu, const double *mu, int l_min, int l_max,

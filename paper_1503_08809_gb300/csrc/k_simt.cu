@@ -37,32 +37,46 @@ __device__ __forceinline__ void simt_fma_tile(const T (*As)[BM + 1], const T (*B
   }
 }
 
-// Promote an FP32 chunk sum into the FP64 accumulator (no-op for FP64).
+// Running sum of the FP32 chunk sums: a double-FP32 (hi, lo) pair updated
+// with Knuth's TwoSum -- FP32 operations only (GB300's FP64 rate is 1/64 of
+// its FP32 rate), ~48 significant bits.  For FP64 tiles it is unused.
+template <typename T, int TM, int TN>
+struct ChunkAcc;
 template <int TM, int TN>
-__device__ __forceinline__ void promote(float (&acc)[TM][TN], double (&accd)[TM][TN]) {
+struct ChunkAcc<float, TM, TN> {
+  float hi[TM][TN], lo[TM][TN];
+  __device__ __forceinline__ void zero() {
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      accd[i][j] += (double)acc[i][j];
-      acc[i][j] = 0.f;
-    }
-}
+      for (int j = 0; j < TN; ++j) { hi[i][j] = 0.f; lo[i][j] = 0.f; }
+  }
+  __device__ __forceinline__ void promote(float (&acc)[TM][TN]) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        float a = hi[i][j], b = acc[i][j];
+        float s = a + b, bb = s - a;
+        float e = (a - (s - bb)) + (b - bb);
+        e += lo[i][j];
+        hi[i][j] = s + e;
+        lo[i][j] = e - (hi[i][j] - s);
+        acc[i][j] = 0.f;
+      }
+  }
+  __device__ __forceinline__ double value(const float (&acc)[TM][TN], int i, int j) const {
+    return (double)hi[i][j] + (double)lo[i][j] + (double)acc[i][j];
+  }
+};
 template <int TM, int TN>
-__device__ __forceinline__ void promote(double (&acc)[TM][TN], double (&accd)[TM][TN]) {}
+struct ChunkAcc<double, TM, TN> {
+  __device__ __forceinline__ void zero() {}
+  __device__ __forceinline__ void promote(double (&)[TM][TN]) {}
+  __device__ __forceinline__ double value(const double (&acc)[TM][TN], int i, int j) const { return acc[i][j]; }
+};
 
-template <int TM, int TN>
-__device__ __forceinline__ double final_value(const float (&acc)[TM][TN], const double (&accd)[TM][TN],
-                                              int i, int j) {
-  return accd[i][j] + (double)acc[i][j];
-}
-template <int TM, int TN>
-__device__ __forceinline__ double final_value(const double (&acc)[TM][TN], const double (&accd)[TM][TN],
-                                              int i, int j) {
-  return acc[i][j];
-}
-
-// FP32 chunk length (in K steps of BK) before promotion to FP64.
+// FP32 chunk length (in K steps of BK) before promotion into the running sum.
 constexpr int PROMOTE_STEPS = 2;
 
 // ---------------------------------------------------------------------------
@@ -85,11 +99,12 @@ __global__ void __launch_bounds__(256) k_contract_l(SepShape s, const double *__
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   T acc[TM][TN];
-  double accd[TM][TN];
+  ChunkAcc<T, TM, TN> run;
+  run.zero();
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) { acc[i][j] = 0; accd[i][j] = 0.0; }
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0;
 
   int step = 0;
   for (int k0 = 0; k0 < L; k0 += BK, ++step) {
@@ -118,7 +133,7 @@ __global__ void __launch_bounds__(256) k_contract_l(SepShape s, const double *__
     __syncthreads();
     simt_fma_tile<T, BM, BN, BK, TM, TN>(As, Bs, acc, tx, ty);
     __syncthreads();
-    if ((step + 1) % PROMOTE_STEPS == 0) promote<TM, TN>(acc, accd);
+    if ((step + 1) % PROMOTE_STEPS == 0) run.promote(acc);
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
@@ -130,7 +145,7 @@ __global__ void __launch_bounds__(256) k_contract_l(SepShape s, const double *__
       int64_t n = n0 + tx + jj * TX;
       if (n >= cols) continue;
       int xl = (int)(n / nbp), p = (int)(n % nbp);
-      M[(((size_t)xl * s.n_mu + j) * nbl + a) * nbp + p] = (T)final_value<TM, TN>(acc, accd, i, jj);
+      M[(((size_t)xl * s.n_mu + j) * nbl + a) * nbp + p] = (T)run.value(acc, i, jj);
     }
   }
 }
@@ -226,11 +241,12 @@ __global__ void __launch_bounds__(256) k_triple(SepShape s, GLayout g, const T *
   }
 
   T acc[TM][TN];
-  double accd[TM][TN];
+  ChunkAcc<T, TM, TN> run;
+  run.zero();
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) { acc[i][j] = 0; accd[i][j] = 0.0; }
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0;
 
   const int64_t kbeg = (int64_t)blockIdx.y * k_per_split;
   const int64_t kend = min(S, kbeg + k_per_split);
@@ -259,7 +275,7 @@ __global__ void __launch_bounds__(256) k_triple(SepShape s, GLayout g, const T *
     __syncthreads();
     simt_fma_tile<T, BM, BN, BK, TM, TN>(As, Bs, acc, tx, ty);
     __syncthreads();
-    if ((step + 1) % PROMOTE_STEPS == 0) promote<TM, TN>(acc, accd);
+    if ((step + 1) % PROMOTE_STEPS == 0) run.promote(acc);
   }
   double *o = out + (int64_t)blockIdx.y * out_stride + g.offset(b);
 #pragma unroll
@@ -270,7 +286,7 @@ __global__ void __launch_bounds__(256) k_triple(SepShape s, GLayout g, const T *
     for (int jj = 0; jj < TN; ++jj) {
       int64_t col = (int64_t)ct * BN + tx + jj * TX;
       if (col >= Cn) continue;
-      o[row * Cn + col] = final_value<TM, TN>(acc, accd, i, jj);
+      o[row * Cn + col] = run.value(acc, i, jj);
     }
   }
 }

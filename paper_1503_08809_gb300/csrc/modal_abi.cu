@@ -24,6 +24,10 @@ struct modal_handle {
   void *slot_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t slot_bytes[4] = {0, 0, 0, 0};
   int64_t *pinned_i64 = nullptr;  // host-pinned word for the direct path's triple count
+  int *pinned_err = nullptr;      // host-pinned copy of the tensor path's device error word
+  cudaEvent_t err_event = nullptr;
+  bool err_pending = false;
+  long long wait_cycles = TC_DEFAULT_WAIT_CYCLES;
   Profiler prof;
 };
 
@@ -122,6 +126,7 @@ static int resolve_opts(modal_handle *h, const modal_problem *p, const modal_opt
                 "n_mu = %d is below ceil((3 l_max + 1)/2) = %d: the Gauss-Legendre rule would not be exact "
                 "(set allow_inexact_gl to accept)",
                 n_mu, n_mu_exact(p->l_max));
+  if (n_mu > 6400) return fail(h, MODAL_EUNSUPPORTED, "n_mu > 6400 (l_max > 4266) is not supported");
   if (prec != MODAL_PREC_FP64 && prec != MODAL_PREC_FP32 && prec != MODAL_PREC_OZAKI_BF16)
     return fail(h, MODAL_EINVAL, "unknown precision %d", prec);
   if (x_chunk < 0) return fail(h, MODAL_EINVAL, "x_chunk < 0");
@@ -142,10 +147,18 @@ int modal_handle_create(modal_handle **out) {
   modal_handle *h = new modal_handle();
   h->device = dev;
   h->num_sms = prop.multiProcessorCount;
-  e = cudaMallocHost((void **)&h->pinned_i64, sizeof(int64_t));
+  e = cudaMallocHost((void **)&h->pinned_i64, 2 * sizeof(int64_t));
   if (e != cudaSuccess) {
     delete h;
     return fail(nullptr, MODAL_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+  }
+  h->pinned_err = (int *)(h->pinned_i64 + 1);
+  *h->pinned_err = 0;
+  e = cudaEventCreateWithFlags(&h->err_event, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaFreeHost(h->pinned_i64);
+    delete h;
+    return fail(nullptr, MODAL_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
   }
   *out = h;
   return MODAL_OK;
@@ -155,6 +168,7 @@ int modal_handle_destroy(modal_handle *h) {
   if (!h) return MODAL_OK;
   for (int s = 0; s < 4; ++s)
     if (h->slot_ptr[s]) cudaFree(h->slot_ptr[s]);
+  if (h->err_event) cudaEventDestroy(h->err_event);
   if (h->pinned_i64) cudaFreeHost(h->pinned_i64);
   tc_release(h->device);
   delete h;
@@ -191,6 +205,26 @@ int modal_profile_read(modal_handle *h, int32_t max_entries, char *names, int64_
   return MODAL_OK;
 }
 
+int modal_handle_status(modal_handle *h) {
+  if (int r = check_handle(h)) return r;
+  if (!h->err_pending) return MODAL_OK;
+  cudaError_t e = cudaEventSynchronize(h->err_event);
+  if (e != cudaSuccess) return fail(h, MODAL_ECUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+  h->err_pending = false;
+  if (*h->pinned_err) {
+    *h->pinned_err = 0;
+    return fail(h, MODAL_ETIMEOUT, "a bounded device-side wait of the tensor-core kernels gave up");
+  }
+  return MODAL_OK;
+}
+
+int modal_handle_set_wait_limit(modal_handle *h, int64_t cycles) {
+  if (int r = check_handle(h)) return r;
+  if (cycles < 0) return fail(h, MODAL_EINVAL, "negative wait limit");
+  h->wait_cycles = cycles == 0 ? TC_DEFAULT_WAIT_CYCLES : (long long)cycles;
+  return MODAL_OK;
+}
+
 int modal_handle_reserve(modal_handle *h, size_t bytes) {
   if (int r = check_handle(h)) return r;
   void *p;
@@ -200,6 +234,7 @@ int modal_handle_reserve(modal_handle *h, size_t bytes) {
 int modal_gl_nodes(modal_handle *h, int32_t n_mu, double *mu, double *om, modal_stream_t stream) {
   if (int r = check_handle(h)) return r;
   if (n_mu < 1) return fail(h, MODAL_EINVAL, "n_mu must be >= 1");
+  if (n_mu > 6400) return fail(h, MODAL_EUNSUPPORTED, "n_mu > 6400 is not supported");
   if (!mu || !om) return fail(h, MODAL_EINVAL, "null output");
   CK(launch_gl_nodes(n_mu, mu, om, (cudaStream_t)stream));
   return MODAL_OK;
@@ -226,14 +261,31 @@ int modal_x_weights(modal_handle *h, int32_t kind, int32_t n_x, const double *x,
   return MODAL_OK;
 }
 
-int modal_contract_l(modal_handle *h, const modal_problem *p, int32_t n_mu, const double *A, double *M,
-                     modal_stream_t stream) {
+int modal_contract_l(modal_handle *h, const modal_problem *p, int32_t n_mu, const double *A, int32_t precision,
+                     double *M, modal_stream_t stream) {
   if (int r = check_handle(h)) return r;
   if (int r = validate_problem(h, p, false, false)) return r;
   if (n_mu < 0 || !A || !M) return fail(h, MODAL_EINVAL, "bad A/M/n_mu");
+  if (precision != MODAL_PREC_FP64 && precision != MODAL_PREC_OZAKI_BF16)
+    return fail(h, MODAL_EINVAL, "modal_contract_l supports FP64 and OZAKI_BF16");
   if (n_mu == 0 || p->n_x == 0) return MODAL_OK;
+  cudaStream_t st = (cudaStream_t)stream;
   SepShape s{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};
-  CK(launch_contract_l<double>(s, A, p->q, p->qt, 0, p->n_x, M, (cudaStream_t)stream));
+  if (precision == MODAL_PREC_FP64) {
+    PROF(h, "contract_l_f64", st);
+    CK(launch_contract_l<double>(s, A, p->q, p->qt, 0, p->n_x, M, st));
+    return MODAL_OK;
+  }
+  void *scratch;
+  if (int r = ws_get(h, 0, tc_scratch_bytes(s, p->n_x), &scratch)) return r;
+  {
+    PROF(h, "tc_contract_l", st);
+    if (int r = tc_contract_l(s, A, p->q, p->qt, 0, p->n_x, M, scratch, h->wait_cycles, st, nullptr, true))
+      return fail(h, r, "%s", tc_last_error());
+  }
+  CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(scratch, s, p->n_x), sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(h->err_event, st));
+  h->err_pending = true;
   return MODAL_OK;
 }
 
@@ -256,10 +308,18 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   if (int r = resolve_opts(h, p, o, n_mu, prec, xch)) return r;
   pl.s = SepShape{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};
   pl.prec = prec;
-  pl.elem = (prec == MODAL_PREC_FP64) ? sizeof(double) : sizeof(float);
+  pl.elem = (prec == MODAL_PREC_FP32) ? sizeof(float) : sizeof(double);
   const int64_t nblp = (int64_t)p->nb_late * p->nb_prim;
   if (xch > 0) {
     pl.nxc = xch < p->n_x ? xch : p->n_x;
+  } else if (prec == MODAL_PREC_OZAKI_BF16) {
+    // the split Y operand dominates: 5 BF16 slices per (row, slice)
+    const int64_t P2 = (int64_t)p->nb_prim * (p->nb_prim + 1) / 2;
+    const int64_t rowsY = P2 * p->nb_late * (p->nb_late + 1) / 2;
+    const int64_t per_x = 10 * rowsY * (int64_t)n_mu + 16 * (int64_t)n_mu * nblp;
+    const int64_t budget = (int64_t)6 << 30;
+    int64_t c = budget / (per_x > 0 ? per_x : 1);
+    pl.nxc = (int)(c < 1 ? 1 : (c > p->n_x ? p->n_x : c));
   } else {
     const int64_t budget = (int64_t)2 << 30;  // 2 GiB of M per chunk
     int64_t per_x = (int64_t)n_mu * nblp * (int64_t)pl.elem;
@@ -327,10 +387,17 @@ static int run_separable(modal_handle *h, const modal_problem *p, const SepPlan 
       CK(launch_triple<float>(s, (float *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
                               h->num_sms, st));
     } else {
-      int r = tc_separable_chunk(s, A, p->q, p->qt, om, p->x_w, x0, nxc, (float *)M, G, c > 0, tcs,
-                                 h->num_sms, st);
+      PROF(h, "tc_chunk", st);
+      int r = tc_separable_chunk(s, A, p->q, p->qt, om, p->x_w, x0, nxc, (double *)M, G, c > 0, tcs,
+                                 h->num_sms, h->wait_cycles, st);
       if (r) return fail(h, r, "tensor-core chunk failed: %s", tc_last_error());
     }
+  }
+  if (pl.prec == MODAL_PREC_OZAKI_BF16 && nchunks > 0) {
+    // surface a bounded-wait give-up through modal_handle_status (no sync here)
+    CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(tcs, s, pl.nxc), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(h->err_event, st));
+    h->err_pending = true;
   }
   PROF(h, "gather", st);
   CK(launch_gather(s, G, p->late_modes, p->prim_modes, p->n_late, p->n_prim, 1.0 / (48.0 * MODAL_PI), gamma,

@@ -23,6 +23,8 @@
 // two-stage mbarrier pipeline; one thread issues the MMAs.  Every wait is
 // bounded: on give-up the CTA raises an error word, drains its copies in
 // flight, frees TMEM and returns.
+#include <cuda_bf16.h>
+
 #include <cstdio>
 #include <cstring>
 
@@ -124,10 +126,13 @@ __global__ void k_split_lrows(int64_t rows, int L, int Kpad, const double *__res
   }
 }
 
-// words[0] = error bits, words[1..] = running exponent maxima
-__global__ void k_init_words(int *w) {
-  if (threadIdx.x == 0) w[0] = 0;
-  else if (threadIdx.x < 8) w[threadIdx.x] = -100000;
+// words[0] = error bits (cleared once per call), words[1..] = exponent maxima
+__global__ void k_init_words(int *w, int reset_err) {
+  if (threadIdx.x == 0) {
+    if (reset_err) w[0] = 0;
+  } else if (threadIdx.x < 8) {
+    w[threadIdx.x] = -100000;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (*abort_flag) {
         for (int i = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); i < issued; ++i) {
           volatile int dummy = 0;
-          ptx::mbar_wait(&full[i % OZ_STAGES], (uint32_t)((i / OZ_STAGES) & 1), &dummy, P.wait_cycles);
+          ptx::mbar_wait(&full[i % OZ_STAGES], (uint32_t)((i / OZ_STAGES) & 1), &dummy, OZ_WAIT_CYCLES);
         }
       }
     }
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       // every MMA this thread issued has retired before TMEM can be freed
       ptx::mma_commit(mma_done);
       volatile int dummy = 0;
-      ptx::mbar_wait(mma_done, 0, &dummy, P.wait_cycles);
+      ptx::mbar_wait(mma_done, 0, &dummy, OZ_WAIT_CYCLES);
     }
   } else {
     // ================= epilogue: drain each chunk into double-FP32 =================
@@ -426,19 +431,22 @@ size_t tc_scratch_bytes(const SepShape &s, int nxc) {
 }
 
 int tc_contract_l(const SepShape &s, const double *A, const double *q, const double *qt, int x0, int nxc,
-                  double *M, void *scratch, long long wait_cycles, cudaStream_t st, char **scratch_end) {
+                  double *M, void *scratch, long long wait_cycles, cudaStream_t st, char **scratch_end,
+                  bool reset_err) {
   const int Kpad = cdiv(s.L, OZ_BK) * OZ_BK;
   const int nch = cdiv(s.L, OZ_KC);
   const int64_t rowsA = (int64_t)s.n_mu * s.nbl, rowsB = (int64_t)nxc * s.nbp;
+  // status words first, at a fixed offset whatever the chunk size:
+  // [0] error bits, [1] emaxA, [2] emaxB, [3] emax of the triple's B, [4] of Y
   char *w = (char *)scratch;
+  int *words = (int *)w; w += 256 * 4;
   __nv_bfloat16 *As = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * rowsA * Kpad * 2);
   __nv_bfloat16 *Bs = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * rowsB * Kpad * 2);
   int *eA = (int *)w; w += up256((size_t)nch * rowsA * 4);
   int *eB = (int *)w; w += up256((size_t)nch * rowsB * 4);
-  int *words = (int *)w; w += 256 * 4;  // [0] err, [1] emaxA, [2] emaxB, [3..] triple
   if (scratch_end) *scratch_end = w;
   cudaError_t e;
-  k_init_words<<<1, 32, 0, st>>>(words);
+  k_init_words<<<1, 32, 0, st>>>(words, reset_err ? 1 : 0);
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   {
     const int64_t wa = rowsA * nch, wb = rowsB * nch;
@@ -480,6 +488,278 @@ cuda_fail:
   snprintf(g_tc_err, sizeof g_tc_err, "l contraction: %s", cudaGetErrorString(e));
   return MODAL_ECUDA;
 }
+
+// ===========================================================================
+// Triple product (Eq. 2D slice reduction) on the tensor cores.
+//   A operand: Y rows (b, a, {u,v}) over all b, Y = w_k (M_au M_bv + M_av M_bu)
+//              formed in double-FP32 from the FP64 M of the chunk, split with a
+//              per-(row, K chunk) exponent from the bound
+//              |Y| <= m_au m_bv + m_av m_bu,  m_au = max_k sqrt(w_k) |M_au(k)|;
+//   B operand: M columns (c, t) transposed to K-major, exact per-chunk maxima;
+//   output:    G block b (rows (a,{u,v}), columns (c,t) with c >= b), FP64 add.
+// ===========================================================================
+struct f2 {
+  float h, l;
+};
+__device__ __forceinline__ f2 df_from_d(double x) {
+  float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ f2 df_two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ f2 df_mul(f2 a, f2 b) {
+  float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  float s = p + e;
+  return {s, e - (s - p)};
+}
+__device__ __forceinline__ f2 df_addv(f2 a, f2 b) {
+  f2 s = df_two_sum(a.h, b.h);
+  float e = s.l + a.l + b.l;
+  float h = s.h + e;
+  return {h, e - (h - s.h)};
+}
+
+// Slices of a double-FP32 value y with |y| <= 2^e: q_s 2^(-7 s).
+__device__ __forceinline__ void split5_df(f2 y, int e, __nv_bfloat16 (&out)[OZ_SLICES]) {
+  if (e < -99999) {
+#pragma unroll
+    for (int s = 0; s < OZ_SLICES; ++s) out[s] = __float2bfloat16_rn(0.f);
+    return;
+  }
+  float h = ldexpf(y.h, OZ_BETA - e), l = ldexpf(y.l, OZ_BETA - e);
+#pragma unroll
+  for (int s = 0; s < OZ_SLICES; ++s) {
+    float q = rintf(h);
+    f2 r = df_two_sum(h - q, l);  // h - q is exact (|h - q| <= 1/2)
+    out[s] = __float2bfloat16_rn(ldexpf(q, -OZ_BETA * s));
+    h = r.h * (float)(1 << OZ_BETA);
+    l = r.l * (float)(1 << OZ_BETA);
+  }
+}
+
+// Per chunk of OZ_KC slices and block of 64 columns: exact max |M| (B-operand
+// exponent), max sqrt(w)|M| (Y bound), double-FP32 copy of M and of w, and the
+// K-major BF16 slices of M.
+constexpr int TP_COLS = 64;
+__global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int nblp, int n_mu, int x0,
+                                                      const double *__restrict__ M, const double *__restrict__ om,
+                                                      const double *__restrict__ xw, f2 *__restrict__ Mdf,
+                                                      f2 *__restrict__ wdf, double *__restrict__ mxW,
+                                                      int *__restrict__ eB, __nv_bfloat16 *__restrict__ Bt,
+                                                      int *__restrict__ emaxB) {
+  __shared__ double red1[4][TP_COLS], red2[4][TP_COLS];
+  __shared__ int esh[TP_COLS];
+  __shared__ __nv_bfloat16 tile[OZ_SLICES][TP_COLS][32 + 8];
+  const int ch = blockIdx.y;
+  const int c0 = blockIdx.x * TP_COLS;
+  const int tc = threadIdx.x % TP_COLS, tk = threadIdx.x / TP_COLS;  // 64 cols x 4 k-lanes
+  const int col = c0 + tc;
+  const int64_t k0 = (int64_t)ch * OZ_KC, k1 = min(K, k0 + OZ_KC);
+  double m1 = 0.0, m2 = 0.0;
+  if (col < nblp) {
+    for (int64_t k = k0 + tk; k < k1; k += 4) {
+      const double v = M[k * nblp + col];
+      const double w = om[k % n_mu] * xw[x0 + k / n_mu];
+      m1 = fmax(m1, fabs(v));
+      m2 = fmax(m2, sqrt(w) * fabs(v));
+      Mdf[k * nblp + col] = df_from_d(v);
+      if (col == 0) wdf[k] = df_from_d(w);
+    }
+  }
+  red1[tk][tc] = m1;
+  red2[tk][tc] = m2;
+  __syncthreads();
+  if (tk == 0) {
+    for (int i = 1; i < 4; ++i) {
+      m1 = fmax(m1, red1[i][tc]);
+      m2 = fmax(m2, red2[i][tc]);
+    }
+    const int e = exp_bound(m1);
+    esh[tc] = e;
+    if (col < nblp) {
+      eB[(int64_t)ch * nblp + col] = e;
+      mxW[(int64_t)ch * nblp + col] = m2 * (1.0 + 1e-12);  // room for the rounding of sqrt(w)
+      if (e > -99999) atomicMax(emaxB, e);
+    }
+  }
+  __syncthreads();
+  const int e = esh[tc];
+  const int64_t kpend = min((int64_t)Kpad, k0 + OZ_KC);
+  for (int64_t kt = k0; kt < kpend; kt += 32) {
+    // each thread splits 8 k of its column
+    for (int i = 0; i < 8; ++i) {
+      const int kk = tk * 8 + i;
+      const int64_t k = kt + kk;
+      const double v = (col < nblp && k < K) ? M[k * nblp + col] : 0.0;
+      __nv_bfloat16 o[OZ_SLICES];
+      split5_df(df_from_d(v), e, o);
+#pragma unroll
+      for (int s = 0; s < OZ_SLICES; ++s) tile[s][tc][kk] = o[s];
+    }
+    __syncthreads();
+    // write: per (slice, column) one 64-byte row of 32 k
+    for (int idx = threadIdx.x; idx < OZ_SLICES * TP_COLS * 4; idx += 256) {
+      const int part = idx & 3, cc = (idx >> 2) % TP_COLS, s = idx / (4 * TP_COLS);
+      if (c0 + cc < nblp && kt + part * 8 < Kpad) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(&tile[s][cc][part * 8]);
+        uint4 *dst = reinterpret_cast<uint4 *>(Bt + ((int64_t)s * nblp + c0 + cc) * Kpad + kt + part * 8);
+        *dst = *src;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Y rows: global row r -> (b, a, uv) with rows ordered by b, then a, then uv.
+__device__ __forceinline__ void y_row_decode(int64_t r, int P2, int &b, int &a, int &u, int &v) {
+  // rows before block b: P2 * b (b + 1) / 2
+  int bb = (int)((sqrt(8.0 * (double)(r / P2) + 1.0) - 1.0) * 0.5);
+  while ((int64_t)P2 * bb * (bb + 1) / 2 > r) --bb;
+  while ((int64_t)P2 * (bb + 1) * (bb + 2) / 2 <= r) ++bb;
+  const int64_t loc = r - (int64_t)P2 * bb * (bb + 1) / 2;
+  b = bb;
+  a = (int)(loc / P2);
+  pair_decode((int)(loc % P2), u, v);
+}
+
+constexpr int TY_ROWS = 64, TY_K = 64;
+__global__ void __launch_bounds__(256) k_tp_make_y(int64_t rowsY, int64_t K, int Kpad, int nbp, int nblp, int P2,
+                                                   const f2 *__restrict__ Mdf, const f2 *__restrict__ wdf,
+                                                   const double *__restrict__ mxW, int *__restrict__ eY,
+                                                   __nv_bfloat16 *__restrict__ Ysl, int *__restrict__ emaxY) {
+  __shared__ __nv_bfloat16 tile[OZ_SLICES][TY_ROWS][TY_K + 8];
+  const int64_t r0 = (int64_t)blockIdx.x * TY_ROWS;
+  const int64_t kb = (int64_t)blockIdx.y * TY_K;
+  const int ch = (int)(kb / OZ_KC);
+  const int tr = threadIdx.x % TY_ROWS, tk = threadIdx.x / TY_ROWS;  // 64 rows x 4 k-lanes
+  const int64_t r = r0 + tr;
+  int b = 0, a = 0, u = 0, v = 0, e = -100000;
+  if (r < rowsY) {
+    y_row_decode(r, P2, b, a, u, v);
+    const double *mw = mxW + (int64_t)ch * nblp;
+    const double bound = mw[a * nbp + u] * mw[b * nbp + v] + mw[a * nbp + v] * mw[b * nbp + u];
+    e = exp_bound(bound);
+    if (tk == 0 && (kb % OZ_KC) == 0) {
+      eY[(int64_t)ch * rowsY + r] = e;
+      if (e > -99999) atomicMax(emaxY, e);
+    }
+  }
+  for (int i = 0; i < TY_K / 4; ++i) {
+    const int kk = tk * (TY_K / 4) + i;
+    const int64_t k = kb + kk;
+    __nv_bfloat16 o[OZ_SLICES];
+    f2 y = {0.f, 0.f};
+    if (r < rowsY && k < K) {
+      const f2 *Mk = Mdf + k * nblp;
+      const f2 s = df_addv(df_mul(Mk[a * nbp + u], Mk[b * nbp + v]), df_mul(Mk[a * nbp + v], Mk[b * nbp + u]));
+      y = df_mul(wdf[k], s);
+    }
+    split5_df(y, e, o);
+#pragma unroll
+    for (int s = 0; s < OZ_SLICES; ++s) tile[s][tr][kk] = o[s];
+  }
+  __syncthreads();
+  // write 64-row x 64-k tiles: per (slice, row) 128 bytes = 8 x 16 B
+  for (int idx = threadIdx.x; idx < OZ_SLICES * TY_ROWS * 8; idx += 256) {
+    const int part = idx & 7, rr = (idx >> 3) % TY_ROWS, s = idx / (8 * TY_ROWS);
+    const int64_t kk = kb + part * 8;
+    if (r0 + rr < rowsY && kk < Kpad) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(&tile[s][rr][part * 8]);
+      uint4 *dst = reinterpret_cast<uint4 *>(Ysl + ((int64_t)s * rowsY + r0 + rr) * Kpad + kk);
+      *dst = *src;
+    }
+  }
+}
+
+static int64_t y_rows(const SepShape &s) {
+  const int64_t P2 = (int64_t)s.nbp * (s.nbp + 1) / 2;
+  return P2 * s.nbl * (s.nbl + 1) / 2;
+}
+
+size_t tc_triple_scratch_bytes(const SepShape &s, int nxc) {
+  const int64_t K = (int64_t)nxc * s.n_mu;
+  const int Kpad = (int)(cdiv64(K, 64) * 64);
+  const int64_t nblp = (int64_t)s.nbl * s.nbp;
+  const int nch = (int)cdiv64(K, OZ_KC);
+  const int64_t rowsY = y_rows(s);
+  size_t b = 0;
+  b += up256((size_t)K * nblp * 8) + up256((size_t)K * 8);            // Mdf, wdf
+  b += up256((size_t)nch * nblp * 8) + up256((size_t)nch * nblp * 4);  // mxW, eB
+  b += up256((size_t)OZ_SLICES * nblp * Kpad * 2);                     // Bt
+  b += up256((size_t)nch * rowsY * 4);                                 // eY
+  b += up256((size_t)OZ_SLICES * rowsY * Kpad * 2);                    // Y slices
+  return b;
+}
+
+int tc_separable_chunk(const SepShape &s, const double *A, const double *q, const double *qt, const double *om,
+                       const double *xw, int x0, int nxc, double *M, double *G, bool accumulate, void *scratch,
+                       int num_sms, long long wait_cycles, cudaStream_t st) {
+  (void)num_sms;
+  char *w = nullptr;
+  if (int r = tc_contract_l(s, A, q, qt, x0, nxc, M, scratch, wait_cycles, st, &w, !accumulate)) return r;
+  int *words = (int *)scratch;  // status words written by tc_contract_l
+  cudaError_t e;
+  const int64_t K = (int64_t)nxc * s.n_mu;
+  const int Kpad = (int)(cdiv64(K, 64) * 64);
+  const int nblp = s.nbl * s.nbp;
+  const int nch = (int)cdiv64(K, OZ_KC);
+  const int64_t rowsY = y_rows(s);
+  const int P2 = s.nbp * (s.nbp + 1) / 2;
+  f2 *Mdf = (f2 *)w; w += up256((size_t)K * nblp * 8);
+  f2 *wdf = (f2 *)w; w += up256((size_t)K * 8);
+  double *mxW = (double *)w; w += up256((size_t)nch * nblp * 8);
+  int *eB = (int *)w; w += up256((size_t)nch * nblp * 4);
+  __nv_bfloat16 *Bt = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * nblp * Kpad * 2);
+  int *eY = (int *)w; w += up256((size_t)nch * rowsY * 4);
+  __nv_bfloat16 *Ysl = (__nv_bfloat16 *)w;
+  if (!accumulate) {
+    GLayout g = make_glayout(s.nbl, s.nbp);
+    if ((e = launch_zero(G, (size_t)g.size(), st)) != cudaSuccess) goto cuda_fail;
+  }
+  k_tp_prep_cols<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)nch), 256, 0, st>>>(
+      K, Kpad, nblp, s.n_mu, x0, M, om, xw, Mdf, wdf, mxW, eB, Bt, words + 3);
+  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  k_tp_make_y<<<dim3((unsigned)cdiv64(rowsY, TY_ROWS), (unsigned)(Kpad / TY_K)), 256, 0, st>>>(
+      rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, wdf, mxW, eY, Ysl, words + 4);
+  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  {
+    CUtensorMap ta, tb;
+    if (int r = make_slices_map(&ta, Ysl, rowsY, Kpad, OZ_BM)) return r;
+    if (int r = make_slices_map(&tb, Bt, nblp, Kpad, OZ_BN)) return r;
+    OzParams P{};
+    P.rowsA = rowsY;
+    P.rowsB = nblp;
+    P.Kpad = Kpad;
+    P.nchunks = nch;
+    P.eA = eY;
+    P.eB = eB;
+    P.emaxA = words + 4;
+    P.emaxB = words + 3;
+    P.out = G;
+    P.err = words;
+    P.g = make_glayout(s.nbl, s.nbp);
+    P.wait_cycles = wait_cycles;
+    int64_t tiles = 0;
+    for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(P.g.rows(b), OZ_BM) * cdiv64(P.g.cols(b), OZ_BN);
+    if ((e = cudaFuncSetAttribute(k_ozaki_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
+        cudaSuccess)
+      goto cuda_fail;
+    k_ozaki_gemm<1><<<(unsigned)tiles, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  }
+  return MODAL_OK;
+cuda_fail:
+  snprintf(g_tc_err, sizeof g_tc_err, "triple product: %s", cudaGetErrorString(e));
+  return MODAL_ECUDA;
+}
+
+int *tc_error_word(void *scratch, const SepShape &, int) { return (int *)scratch; }
 
 void tc_release(int) {}
 
