@@ -198,6 +198,33 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
                                     const modal_opts *opts, double *const *gammas,
                                     modal_stream_t stream);
 
+/* Allocation-free form of modal_project_separable, for callers that cannot
+ * allocate device memory: programs that hand all of a GPU's memory to their
+ * own allocator or budget, plugins whose host forbids cudaMalloc, and
+ * latency-critical loops where cudaMalloc (which may synchronise the device)
+ * is not acceptable.  The paper has no counterpart; this is an interface
+ * convenience.
+ *  - Same problem, opts and output as modal_project_separable, but no handle:
+ *    it calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - Scratch lives in a fixed 48 MiB device array compiled into the library;
+ *    every GPU that loads the library holds it until the process exits.
+ *    Problems whose scratch does not fit (radial points are streamed in
+ *    smaller chunks first) are rejected with MODAL_EINVAL and a message
+ *    giving the bytes needed; e.g. 20-function bases (the 52 MB triple-product
+ *    table alone) do not fit.
+ *  - precision: MODAL_PREC_FP64 or MODAL_PREC_FP32 (the tensor-core form
+ *    needs more scratch than the fixed buffer).
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture begins.
+ *  - All calls share the one buffer and it keeps the last call's contents
+ *    (everything a call reads is written first).  Calls that overlap on the
+ *    GPU -- on different streams, or from different threads, without
+ *    ordering between them -- race on it: order them (one stream, or events).
+ *  - Errors: status codes as elsewhere; modal_last_error(NULL) gives the reason. */
+int modal_project_separable_noalloc(const modal_problem *prob, const modal_opts *opts, double *gamma,
+                                    modal_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ EXPORTS = [
     "modal_contract_l", "modal_project_separable", "modal_project_direct",
     "modal_project_backward", "modal_project_separable_batched", "modal_profile_enable",
     "modal_profile_read", "modal_handle_status", "modal_handle_set_wait_limit",
+    "modal_project_separable_noalloc",
 ]
 
 
@@ -80,6 +81,7 @@ def lib():
         "modal_project_separable_batched": [vp, i32, P, O, ctypes.POINTER(vp), vp],
         "modal_profile_enable": [vp, i32],
         "modal_handle_status": [vp],
+        "modal_project_separable_noalloc": [P, O, vp, vp],
         "modal_handle_set_wait_limit": [vp, ctypes.c_int64],
         "modal_profile_read": [vp, i32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)],

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -32,7 +33,7 @@ struct modal_handle {
 };
 
 // time the launch(es) of the enclosing block when profiling is on
-#define PROF(h, name, st) ProfScope _prof_scope((h)->prof.on ? &(h)->prof : nullptr, name, st)
+#define PROF(h, name, st) ProfScope _prof_scope(((h) && (h)->prof.on) ? &(h)->prof : nullptr, name, st)
 
 static thread_local std::string g_err_nohandle;
 
@@ -343,8 +344,8 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   return MODAL_OK;
 }
 
-static int run_separable(modal_handle *h, const modal_problem *p, const SepPlan &pl, double *gamma,
-                         cudaStream_t st, void *scratch) {
+static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, const SepPlan &pl,
+                         double *gamma, cudaStream_t st, void *scratch) {
   const SepShape &s = pl.s;
   Bump bp{(char *)scratch};
   double *mu = bp.take<double>(s.n_mu), *om = bp.take<double>(s.n_mu);
@@ -377,7 +378,7 @@ static int run_separable(modal_handle *h, const modal_problem *p, const SepPlan 
       }
       PROF(h, "triple_f64", st);
       CK(launch_triple<double>(s, (double *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
-                               h->num_sms, st));                                            // a6
+                               num_sms, st));                                               // a6
     } else if (pl.prec == MODAL_PREC_FP32) {
       {
         PROF(h, "contract_l_f32", st);
@@ -385,7 +386,7 @@ static int run_separable(modal_handle *h, const modal_problem *p, const SepPlan 
       }
       PROF(h, "triple_f32", st);
       CK(launch_triple<float>(s, (float *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
-                              h->num_sms, st));
+                              num_sms, st));
     } else {
       PROF(h, "tc_chunk", st);
       int r = tc_separable_chunk(s, A, p->q, p->qt, om, p->x_w, x0, nxc, (double *)M, G, c > 0, tcs,
@@ -431,7 +432,7 @@ int modal_project_separable(modal_handle *h, const modal_problem *p, const modal
   if (int r = plan_separable(h, p, o, pl, h->num_sms)) return r;
   void *scratch;
   if (int r = ws_get(h, 0, pl.bytes, &scratch)) return r;
-  return run_separable(h, p, pl, gamma, (cudaStream_t)stream, scratch);
+  return run_separable(h, h->num_sms, p, pl, gamma, (cudaStream_t)stream, scratch);
 }
 
 int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_problem *probs,
@@ -452,9 +453,80 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
   for (int i = 0; i < n; ++i) {
     if ((int64_t)probs[i].n_late * probs[i].n_prim == 0) continue;
     if (!gammas[i]) return fail(h, MODAL_EINVAL, "null gamma for problem %d", i);
-    if (int r = run_separable(h, &probs[i], plans[i], gammas[i], (cudaStream_t)stream, scratch)) return r;
+    if (int r = run_separable(h, h->num_sms, &probs[i], plans[i], gammas[i], (cudaStream_t)stream, scratch))
+      return r;
   }
   return MODAL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of modal_project_separable.  Its scratch is this
+// file-scope device array (present on every GPU that loads the library, for
+// the life of the process).  In host code the array's name is only a
+// host-side stand-in, so the device address is taken once per device with
+// cudaGetSymbolAddress and cached; kernels receive that address.
+// ---------------------------------------------------------------------------
+#define MODAL_NOALLOC_SCRATCH_BYTES ((size_t)48 << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MODAL_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+struct NoallocDevice {
+  void *scratch = nullptr;
+  int num_sms = 0;
+  bool ready = false;
+};
+constexpr int NOALLOC_MAX_DEVICES = 64;
+NoallocDevice g_noalloc_dev[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+extern "C" int modal_project_separable_noalloc(const modal_problem *p, const modal_opts *o, double *gamma,
+                                               modal_stream_t stream) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, MODAL_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+    return fail(nullptr, MODAL_EUNSUPPORTED, "device ordinal %d beyond %d", dev, NOALLOC_MAX_DEVICES);
+  NoallocDevice nd;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocDevice &slot = g_noalloc_dev[dev];
+    if (!slot.ready) {  // one-time set-up on this device (no allocation)
+      void *ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return fail(nullptr, MODAL_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+      int sms = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess)
+        return fail(nullptr, MODAL_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+      slot.scratch = ptr;
+      slot.num_sms = sms;
+      slot.ready = true;
+    }
+    nd = slot;
+  }
+  if (int r = validate_problem(nullptr, p, true, true)) return r;
+  if ((int64_t)p->n_late * p->n_prim == 0) return MODAL_OK;
+  if (!gamma) return fail(nullptr, MODAL_EINVAL, "null gamma");
+  const int prec = o ? o->precision : MODAL_PREC_FP64;
+  if (prec != MODAL_PREC_FP64 && prec != MODAL_PREC_FP32)
+    return fail(nullptr, MODAL_EINVAL, "the allocation-free entry point serves MODAL_PREC_FP64 and MODAL_PREC_FP32");
+  // largest radial chunk whose scratch fits the static buffer
+  modal_opts oo = o ? *o : modal_opts{0, MODAL_PREC_FP64, 0, 0};
+  SepPlan pl;
+  if (int r = plan_separable(nullptr, p, &oo, pl, nd.num_sms)) return r;
+  int nxc = pl.nxc;
+  while (pl.bytes > MODAL_NOALLOC_SCRATCH_BYTES && nxc > 1) {
+    nxc = nxc > 2 ? nxc / 2 : 1;
+    oo.x_chunk = nxc;
+    if (int r = plan_separable(nullptr, p, &oo, pl, nd.num_sms)) return r;
+  }
+  if (pl.bytes > MODAL_NOALLOC_SCRATCH_BYTES)
+    return fail(nullptr, MODAL_EINVAL,
+                "problem needs %zu bytes of scratch; the allocation-free entry point's static scratch holds %zu",
+                pl.bytes, MODAL_NOALLOC_SCRATCH_BYTES);
+  return run_separable(nullptr, nd.num_sms, p, pl, gamma, (cudaStream_t)stream, nd.scratch);
 }
 
 // ---------------------------------------------------------------------------
