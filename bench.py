@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--tc-fused", type=int, default=0, choices=[0, 1],
+                    help="tensor-core triple product: 0 = Y through HBM, 1 = Y in shared memory")
+    ap.add_argument("--once", action="store_true",
+                    help="run one projection and exit (a small case for profiler captures)")
     return ap.parse_args()
 
 
@@ -205,6 +209,7 @@ def run_ours(args):
     prec = PREC[prec_name]
     P = syn.planck_size(seed=1 + rank, n_x=args.n_x)
     h = mg.Handle(dev)
+    mg.set_option(mg.OPT_TC_TRIPLE_FUSED, args.tc_fused, handle=h)
     dp = mg.DeviceProblem.from_host(P, device=dev, handle=h)
     gamma = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream(dev)
@@ -261,6 +266,10 @@ def run_ours(args):
             flops = 2.0 * gsize * chunk_slices
         elif dom.startswith("contract"):
             flops = 2.0 * P.nb_late * P.nb_prim * P.L * chunk_slices
+        elif dom == "tc_gemm_triple":      # 15 BF16 slice products per useful MAC (issued)
+            flops = 15 * 2.0 * gsize * chunk_slices
+        elif dom == "tc_gemm_l":
+            flops = 15 * 2.0 * P.nb_late * P.nb_prim * P.L * chunk_slices
         else:
             flops = float("nan")
         achieved = flops / avg_s / 1e12
@@ -272,6 +281,9 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": None, "kernel": dom,
                 "peak_source": note, "kernel_ms_avg": avg_s * 1e3,
                 "kernel_share_of_step": tot / (ms * args.steps)}
+        if dom.startswith("tc_gemm"):
+            roof["flops_counted"] = "issued tensor flops (15 BF16 slice products per useful MAC)"
+            roof["useful_achieved"] = achieved / 15.0
     gpu_launches = sum(v[0] for v in prof.values())
 
     # ---- end to end through host buffers -----------------------------------
@@ -319,15 +331,34 @@ def run_ours(args):
             "dtype": DTYPE[prec_name], "data": "synthetic",
             "config": {"workload": P.name, "l_max": P.l_max, "nb": P.nb_late, "n_x": P.n_x,
                        "n_mu": P.n_mu, "slices": P.slices, "precision": prec_name,
-                       "n_modes": P.n_late,
+                       "n_modes": P.n_late, "tc_triple": ("shared-memory Y" if args.tc_fused
+                                                            else "Y through HBM"),
                        "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clk, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
 
 
+def run_once(args):
+    """One projection of the workload (with --n-x radial points), no timing."""
+    import torch
+    import paper_1503_08809_gb300 as mg
+    import synthetic as syn
+    prec = PREC["fp64" if args.precision == "auto" else args.precision]
+    P = syn.planck_size(n_x=args.n_x)
+    mg.set_option(mg.OPT_TC_TRIPLE_FUSED, args.tc_fused)
+    g = mg.project_separable(mg.DeviceProblem.from_host(P), precision=prec)
+    if prec == PREC["ozaki"]:
+        mg.handle_status()
+    torch.cuda.synchronize()
+    print(json.dumps({"once": P.name, "max_abs_gamma": float(g.abs().max())}))
+
+
 def main():
     args = parse()
+    if args.once:
+        run_once(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

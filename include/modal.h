@@ -101,12 +101,24 @@ int modal_handle_reserve(modal_handle *h, size_t bytes);
 
 /* Waits for the work of earlier calls on this handle that carries a device
  * status word and returns MODAL_ETIMEOUT if any bounded device-side wait of
- * the tensor-core kernels gave up (their results are then not valid),
- * MODAL_OK otherwise.  Kernels never trap or spin forever: each wait on an
+ * the tensor-core kernels gave up, MODAL_EUNSUPPORTED if the tensor-core form
+ * met values outside its exponent range (|M| >= 1e37 or sqrt(om W)|M| >= 1e18;
+ * use MODAL_PREC_FP64 then) -- in both cases the results are not valid --
+ * and MODAL_OK otherwise.  Kernels never trap or spin forever: each wait on an
  * mbarrier is bounded (default ~2 s of SM clock) and on give-up the CTA
  * stops issuing work, waits for its own copies in flight, frees its tensor
  * memory and returns. */
 int modal_handle_status(modal_handle *h);
+/* Tunables of the tensor-core form for later calls on this handle.
+ * MODAL_OPT_TC_TRIPLE_FUSED: 0 (default) writes the BF16 slices of the Y
+ *   operand of the triple product to device memory and runs a TMA-fed GEMM;
+ *   1 forms Y in shared memory inside the GEMM (no Y traffic through HBM).
+ *   Both give the same results to rounding.
+ * MODAL_OPT_TC_SPLIT_K: K splits of the shared-memory variant (0 = automatic). */
+#define MODAL_OPT_TC_TRIPLE_FUSED 1
+#define MODAL_OPT_TC_SPLIT_K 2
+int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value);
+
 /* Bound (in SM clock cycles) of those device-side waits for later calls on
  * this handle; 0 restores the default.  A tiny bound makes the waits give up
  * on purpose (used by the tests of the status path). */
@@ -193,7 +205,12 @@ int modal_project_backward(modal_handle *h, const modal_problem *prob, const mod
 
 /* Many independent problems of uneven size in one call (host array `probs`
  * of n problem descriptors, host array `gammas` of n device outputs).  Each
- * result equals modal_project_separable on that problem with these opts. */
+ * result equals modal_project_separable on that problem with these opts.
+ * The launches of the whole batch are captured once into a CUDA graph,
+ * cached on the handle under the problem set (descriptors, pointers, opts,
+ * tunables) and replayed on `stream` by later calls with the same set; the
+ * data may change between calls, the pointers and sizes may not.  Scratch
+ * growth on the handle drops the cached graphs. */
 int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_problem *probs,
                                     const modal_opts *opts, double *const *gammas,
                                     modal_stream_t stream);

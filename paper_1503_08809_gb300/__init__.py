@@ -8,17 +8,18 @@ fails loudly if it has not been built.
 """
 from __future__ import annotations
 
-from ._lib import (ModalError, PREC_FP32, PREC_FP64, PREC_OZAKI_BF16, W_EXACT_3J,
-                   W_SMOOTH_GOSPER, XW_HERMITE, XW_TRAPEZOID, lib, lib_path)
+from ._lib import (OPT_TC_SPLIT_K, OPT_TC_TRIPLE_FUSED, ModalError, PREC_FP32, PREC_FP64,
+                   PREC_OZAKI_BF16, W_EXACT_3J, W_SMOOTH_GOSPER, XW_HERMITE, XW_TRAPEZOID, lib,
+                   lib_path)
 from .api import (DeviceProblem, Handle, contract_l, default_handle, gl_nodes, handle_status,
                   legendre_table, project_backward, project_direct, project_separable,
-                  project_separable_batched, set_wait_limit, x_weights)
+                  project_separable_batched, set_option, set_wait_limit, x_weights)
 from .autograd import ModalProjection, fit_loss_and_grads
 
 __all__ = [
     "ModalError", "PREC_FP32", "PREC_FP64", "PREC_OZAKI_BF16", "W_EXACT_3J", "W_SMOOTH_GOSPER",
     "XW_HERMITE", "XW_TRAPEZOID", "lib", "lib_path", "DeviceProblem", "Handle", "contract_l",
-    "default_handle", "gl_nodes", "handle_status", "set_wait_limit", "legendre_table", "project_backward", "project_direct",
+    "default_handle", "gl_nodes", "handle_status", "set_option", "set_wait_limit", "legendre_table", "project_backward", "project_direct",
     "project_separable", "project_separable_batched", "x_weights", "ModalProjection",
     "fit_loss_and_grads",
 ]

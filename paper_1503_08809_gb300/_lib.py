@@ -9,6 +9,7 @@ _PKG = Path(__file__).resolve().parent
 MODAL_OK, MODAL_EINVAL, MODAL_ENOMEM, MODAL_ECUDA, MODAL_ETIMEOUT, MODAL_EUNSUPPORTED = range(6)
 PREC_FP64, PREC_FP32, PREC_OZAKI_BF16 = 0, 1, 2
 XW_TRAPEZOID, XW_HERMITE = 0, 1
+OPT_TC_TRIPLE_FUSED, OPT_TC_SPLIT_K = 1, 2
 W_EXACT_3J, W_SMOOTH_GOSPER = 0, 1
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
@@ -20,7 +21,7 @@ EXPORTS = [
     "modal_contract_l", "modal_project_separable", "modal_project_direct",
     "modal_project_backward", "modal_project_separable_batched", "modal_profile_enable",
     "modal_profile_read", "modal_handle_status", "modal_handle_set_wait_limit",
-    "modal_project_separable_noalloc",
+    "modal_project_separable_noalloc", "modal_handle_set_option",
 ]
 
 
@@ -81,6 +82,7 @@ def lib():
         "modal_project_separable_batched": [vp, i32, P, O, ctypes.POINTER(vp), vp],
         "modal_profile_enable": [vp, i32],
         "modal_handle_status": [vp],
+        "modal_handle_set_option": [vp, i32, ctypes.c_int64],
         "modal_project_separable_noalloc": [P, O, vp, vp],
         "modal_handle_set_wait_limit": [vp, ctypes.c_int64],
         "modal_profile_read": [vp, i32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),

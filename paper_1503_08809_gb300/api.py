@@ -191,6 +191,12 @@ def handle_status(handle=None, device=None) -> int:
     return code
 
 
+def set_option(option: int, value: int, handle=None, device=None):
+    """modal_handle_set_option (tunables of the tensor-core form)."""
+    h = _h(handle, device)
+    check(lib().modal_handle_set_option(h.ptr, int(option), int(value)), h.ptr)
+
+
 def set_wait_limit(cycles: int, handle=None, device=None):
     """modal_handle_set_wait_limit (0 restores the default bound)."""
     h = _h(handle, device)

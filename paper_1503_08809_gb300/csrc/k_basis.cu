@@ -30,10 +30,12 @@ __device__ __forceinline__ void leg_pair_tab_d(int n, double x, const dd *ca, co
   pm = p0;
 }
 
-__device__ __forceinline__ void leg_pair_tab_dd(int n, dd x, const dd *ca, const dd *cb, dd &pn, dd &pm) {
-  dd p0 = {1.0, 0.0}, p1 = x;
+// P_n and P_{n-1} at a double x in double-double: the products are
+// double-double x double (cheaper than full double-double products).
+__device__ __forceinline__ void leg_pair_tab_dd_at(int n, double x, const dd *ca, const dd *cb, dd &pn, dd &pm) {
+  dd p0 = {1.0, 0.0}, p1 = {x, 0.0};
   for (int k = 1; k < n; ++k) {
-    dd p2 = dd_sub(dd_mul(ca[k], dd_mul(x, p1)), dd_mul(cb[k], p0));
+    dd p2 = dd_sub(dd_mul(ca[k], dd_mul_d(p1, x)), dd_mul(cb[k], p0));
     p0 = p1;
     p1 = p2;
   }
@@ -41,6 +43,12 @@ __device__ __forceinline__ void leg_pair_tab_dd(int n, dd x, const dd *ca, const
   pm = p0;
 }
 
+// Each root: Tricomi's asymptotic start, FP64 Newton to ~1 ulp at x0, then
+// P_n(x0), P_{n-1}(x0) in double-double give the last Newton correction
+// d = P_n/P_n' (so the node is x0 - d to ~1e-30) and P_n'(x0); the
+// derivative at the node follows from the Legendre equation,
+// P_n'' = (2 x P_n' - n(n+1) P_n)/(1 - x^2), as P_n'(x) ~ P_n'(x0) - d P_n''(x0).
+// The weight 2 / ((1 - x^2) P_n'(x)^2) is formed from these and rounded once.
 __global__ void __launch_bounds__(GL_TPB) k_gl_nodes(int n, double *__restrict__ mu, double *__restrict__ om) {
   extern __shared__ dd coef[];
   dd *ca = coef, *cb = coef + n;
@@ -57,7 +65,6 @@ __global__ void __launch_bounds__(GL_TPB) k_gl_nodes(int n, double *__restrict__
     om[0] = 2.0;
     return;
   }
-  // i-th largest root: Tricomi's asymptotic start, then FP64 Newton
   const double nn = (double)n;
   double x = (1.0 - (nn - 1.0) / (8.0 * nn * nn * nn)) * cos(MODAL_PI * (4.0 * i + 3.0) / (4.0 * nn + 2.0));
   for (int it = 0; it < 12; ++it) {
@@ -68,20 +75,21 @@ __global__ void __launch_bounds__(GL_TPB) k_gl_nodes(int n, double *__restrict__
     x -= dx;
     if (fabs(dx) <= 1e-15 * fabs(x)) break;
   }
-  // one Newton step in double-double squares the ~1e-16 error
-  dd X = {x, 0.0};
-  dd pn, pm, dp;
+  if ((n & 1) && i == n / 2) x = 0.0;  // exact centre node of an odd rule
+  dd pn, pm;
+  leg_pair_tab_dd_at(n, x, ca, cb, pn, pm);
   const dd one = {1.0, 0.0};
-  leg_pair_tab_dd(n, X, ca, cb, pn, pm);
-  dd x2m1 = dd_sub(dd_mul(X, X), one);
-  dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pn), pm), nn), x2m1);
-  X = dd_sub(X, dd_div(pn, dp));
-  leg_pair_tab_dd(n, X, ca, cb, pn, pm);
-  x2m1 = dd_sub(dd_mul(X, X), one);
-  dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pn), pm), nn), x2m1);
-  dd w = dd_div({2.0, 0.0}, dd_mul(dd_neg(x2m1), dd_mul(dp, dp)));
-  double xv = X.hi + X.lo, wv = w.hi + w.lo;
-  if ((n & 1) && i == n / 2) {  // exact centre node of an odd rule
+  const dd X0 = {x, 0.0};
+  const dd x2m1 = dd_sub(dd_mul_d(X0, x), one);                             // x0^2 - 1 (exact-ish)
+  const dd dp0 = dd_div(dd_mul_d(dd_sub(dd_mul_d(pn, x), pm), nn), x2m1);  // P_n'(x0)
+  const double d = (pn.hi + pn.lo) / (dp0.hi + dp0.lo);                    // Newton step
+  const double ddp = (2.0 * x * (dp0.hi + dp0.lo) - nn * (nn + 1.0) * (pn.hi + pn.lo)) / (1.0 - x * x);
+  const dd X = dd_sub(X0, {d, 0.0});                                        // node
+  const dd dpx = dd_sub(dp0, {d * ddp, 0.0});                               // P_n'(node)
+  const dd omx = dd_sub(one, dd_mul(X, X));
+  const dd w = dd_div({2.0, 0.0}, dd_mul(omx, dd_mul(dpx, dpx)));
+  const double xv = X.hi + X.lo, wv = w.hi + w.lo;
+  if ((n & 1) && i == n / 2) {
     mu[i] = 0.0;
     om[i] = wv;
     return;

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -29,7 +30,16 @@ struct modal_handle {
   cudaEvent_t err_event = nullptr;
   bool err_pending = false;
   long long wait_cycles = TC_DEFAULT_WAIT_CYCLES;
+  int opt_triple_variant = TC_TRIPLE_MATERIALISED;
+  int opt_split_k = 0;
   Profiler prof;
+  // batched calls: graphs of all launches, keyed by the problem set
+  cudaStream_t cap_stream = nullptr;
+  std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
+  void clear_graphs() {
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
 };
 
 // time the launch(es) of the enclosing block when profiling is on
@@ -62,6 +72,7 @@ static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 static int ws_get(modal_handle *h, int slot, size_t bytes, void **out) {
   if (bytes == 0) bytes = 256;
   if (h->slot_bytes[slot] < bytes) {
+    h->clear_graphs();  // captured graphs point into the old block
     if (h->slot_ptr[slot]) cudaFree(h->slot_ptr[slot]);
     h->slot_ptr[slot] = nullptr;
     h->slot_bytes[slot] = 0;
@@ -169,6 +180,8 @@ int modal_handle_destroy(modal_handle *h) {
   if (!h) return MODAL_OK;
   for (int s = 0; s < 4; ++s)
     if (h->slot_ptr[s]) cudaFree(h->slot_ptr[s]);
+  h->clear_graphs();
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->err_event) cudaEventDestroy(h->err_event);
   if (h->pinned_i64) cudaFreeHost(h->pinned_i64);
   tc_release(h->device);
@@ -212,11 +225,30 @@ int modal_handle_status(modal_handle *h) {
   cudaError_t e = cudaEventSynchronize(h->err_event);
   if (e != cudaSuccess) return fail(h, MODAL_ECUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
   h->err_pending = false;
-  if (*h->pinned_err) {
-    *h->pinned_err = 0;
-    return fail(h, MODAL_ETIMEOUT, "a bounded device-side wait of the tensor-core kernels gave up");
-  }
+  const int word = *h->pinned_err;
+  *h->pinned_err = 0;
+  if (word & 1) return fail(h, MODAL_ETIMEOUT, "a bounded device-side wait of the tensor-core kernels gave up");
+  if (word & 2)
+    return fail(h, MODAL_EUNSUPPORTED,
+                "values outside the range of the tensor-core form (|M| < 1e37, sqrt(w)|M| < 1e18, "
+                "|w_l P_l q| < 1e37); use MODAL_PREC_FP64");
   return MODAL_OK;
+}
+
+int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value) {
+  if (int r = check_handle(h)) return r;
+  switch (option) {
+    case MODAL_OPT_TC_TRIPLE_FUSED:
+      if (value != 0 && value != 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_TRIPLE_FUSED takes 0 or 1");
+      h->opt_triple_variant = value ? TC_TRIPLE_FUSED : TC_TRIPLE_MATERIALISED;
+      return MODAL_OK;
+    case MODAL_OPT_TC_SPLIT_K:
+      if (value < 0 || value > 4096) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_SPLIT_K out of range");
+      h->opt_split_k = (int)value;
+      return MODAL_OK;
+    default:
+      return fail(h, MODAL_EINVAL, "unknown option %d", option);
+  }
 }
 
 int modal_handle_set_wait_limit(modal_handle *h, int64_t cycles) {
@@ -278,13 +310,14 @@ int modal_contract_l(modal_handle *h, const modal_problem *p, int32_t n_mu, cons
     return MODAL_OK;
   }
   void *scratch;
-  if (int r = ws_get(h, 0, tc_scratch_bytes(s, p->n_x), &scratch)) return r;
+  if (int r = ws_get(h, 0, tc_scratch_bytes(s, p->n_x, TC_TRIPLE_FUSED), &scratch)) return r;
   {
     PROF(h, "tc_contract_l", st);
-    if (int r = tc_contract_l(s, A, p->q, p->qt, 0, p->n_x, M, scratch, h->wait_cycles, st, nullptr, true))
+    if (int r = tc_prepare_l(s, A, p->q, scratch, p->n_x, st)) return fail(h, r, "%s", tc_last_error());
+    if (int r = tc_contract_l(s, p->qt, 0, p->n_x, p->n_x, M, scratch, h->wait_cycles, st))
       return fail(h, r, "%s", tc_last_error());
   }
-  CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(scratch, s, p->n_x), sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(scratch), sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(h->err_event, st));
   h->err_pending = true;
   return MODAL_OK;
@@ -296,6 +329,7 @@ int modal_contract_l(modal_handle *h, const modal_problem *p, int32_t n_mu, cons
 struct SepPlan {
   SepShape s;
   int prec;
+  int variant;  // tensor-core triple-product variant
   int nxc;      // radial points per chunk
   int ksplit;   // K split of the SIMT triple product
   size_t elem;  // bytes per M element
@@ -305,6 +339,7 @@ struct SepPlan {
 
 static int plan_separable(modal_handle *h, const modal_problem *p, const modal_opts *o, SepPlan &pl,
                           int num_sms) {
+  pl.variant = h ? h->opt_triple_variant : TC_TRIPLE_MATERIALISED;
   int n_mu, prec, xch;
   if (int r = resolve_opts(h, p, o, n_mu, prec, xch)) return r;
   pl.s = SepShape{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};
@@ -314,12 +349,19 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   if (xch > 0) {
     pl.nxc = xch < p->n_x ? xch : p->n_x;
   } else if (prec == MODAL_PREC_OZAKI_BF16) {
-    // the split Y operand dominates: 5 BF16 slices per (row, slice)
-    const int64_t P2 = (int64_t)p->nb_prim * (p->nb_prim + 1) / 2;
-    const int64_t rowsY = P2 * p->nb_late * (p->nb_late + 1) / 2;
-    const int64_t per_x = 10 * rowsY * (int64_t)n_mu + 16 * (int64_t)n_mu * nblp;
-    const int64_t budget = (int64_t)6 << 30;
+    // per radial point: M (FP64), its double-FP32 copy and its 5 BF16 slices,
+    // the 5 slices of the q~ rows of the l contraction and, unless Y is formed
+    // in shared memory, the 5 BF16 slices of Y (which then dominate)
+    const int64_t L = p->l_max - p->l_min + 1;
+    int64_t per_x = 26 * (int64_t)n_mu * nblp + 10 * (int64_t)p->nb_prim * L;
+    int64_t budget = (int64_t)2 << 30;
+    if (pl.variant == TC_TRIPLE_MATERIALISED) {
+      const int64_t P2 = (int64_t)p->nb_prim * (p->nb_prim + 1) / 2;
+      per_x += 10 * P2 * p->nb_late * (p->nb_late + 1) / 2 * (int64_t)n_mu;
+      budget = (int64_t)6 << 30;
+    }
     int64_t c = budget / (per_x > 0 ? per_x : 1);
+    if (c > 64) c = 64;
     pl.nxc = (int)(c < 1 ? 1 : (c > p->n_x ? p->n_x : c));
   } else {
     const int64_t budget = (int64_t)2 << 30;  // 2 GiB of M per chunk
@@ -339,13 +381,14 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   b += align256(pl.elem * (size_t)pl.nxc * n_mu * nblp);          // M chunk
   b += align256(sizeof(double) * (size_t)pl.Gsize);               // G
   if (need_part) b += align256(sizeof(double) * (size_t)pl.Gsize * pl.ksplit);
-  if (prec == MODAL_PREC_OZAKI_BF16) b += tc_scratch_bytes(pl.s, pl.nxc);
+  if (prec == MODAL_PREC_OZAKI_BF16) b += tc_scratch_bytes(pl.s, pl.nxc, pl.variant);
   pl.bytes = b + 1024;
   return MODAL_OK;
 }
 
 static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, const SepPlan &pl,
-                         double *gamma, cudaStream_t st, void *scratch) {
+                         double *gamma, cudaStream_t st, void *scratch, bool first_in_call = true,
+                         bool capturing = false) {
   const SepShape &s = pl.s;
   Bump bp{(char *)scratch};
   double *mu = bp.take<double>(s.n_mu), *om = bp.take<double>(s.n_mu);
@@ -355,7 +398,7 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
   const int nchunks = (p->n_x + pl.nxc - 1) / pl.nxc;
   const bool need_part = pl.ksplit > 1 || nchunks > 1;
   double *Gpart = need_part ? bp.take<double>((size_t)pl.Gsize * pl.ksplit) : nullptr;
-  void *tcs = (pl.prec == MODAL_PREC_OZAKI_BF16) ? bp.take<char>(tc_scratch_bytes(s, pl.nxc)) : nullptr;
+  void *tcs = (pl.prec == MODAL_PREC_OZAKI_BF16) ? bp.take<char>(tc_scratch_bytes(s, pl.nxc, pl.variant)) : nullptr;
 
   {
     PROF(h, "gl_nodes", st);
@@ -388,15 +431,20 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
       CK(launch_triple<float>(s, (float *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
                               num_sms, st));
     } else {
-      PROF(h, "tc_chunk", st);
-      int r = tc_separable_chunk(s, A, p->q, p->qt, om, p->x_w, x0, nxc, (double *)M, G, c > 0, tcs,
-                                 h->num_sms, h->wait_cycles, st);
+      Profiler *prof = (h && h->prof.on && !capturing) ? &h->prof : nullptr;
+      if (c == 0) {
+        int r = tc_prepare_l(s, A, p->q, tcs, pl.nxc, st, prof, first_in_call);
+        if (r) return fail(h, r, "tensor-core operand split failed: %s", tc_last_error());
+      }
+      int r = tc_separable_chunk(s, p->qt, om, p->x_w, x0, nxc, pl.nxc, (double *)M, G, c > 0, tcs,
+                                 h ? h->wait_cycles : TC_DEFAULT_WAIT_CYCLES, num_sms, pl.variant,
+                                 h ? h->opt_split_k : 0, st, prof);
       if (r) return fail(h, r, "tensor-core chunk failed: %s", tc_last_error());
     }
   }
-  if (pl.prec == MODAL_PREC_OZAKI_BF16 && nchunks > 0) {
+  if (pl.prec == MODAL_PREC_OZAKI_BF16 && nchunks > 0 && !capturing) {
     // surface a bounded-wait give-up through modal_handle_status (no sync here)
-    CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(tcs, s, pl.nxc), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(tcs), sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(h->err_event, st));
     h->err_pending = true;
   }
@@ -435,26 +483,79 @@ int modal_project_separable(modal_handle *h, const modal_problem *p, const modal
   return run_separable(h, h->num_sms, p, pl, gamma, (cudaStream_t)stream, scratch);
 }
 
+// FNV-1a over the bytes of the problem set: the key of a captured graph
+static uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+  const unsigned char *c = (const unsigned char *)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
 int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_problem *probs,
                                     const modal_opts *o, double *const *gammas, modal_stream_t stream) {
   if (int r = check_handle(h)) return r;
   if (n < 0) return fail(h, MODAL_EINVAL, "n < 0");
   if (n == 0) return MODAL_OK;
   if (!probs || !gammas) return fail(h, MODAL_EINVAL, "null probs/gammas");
+  cudaStream_t st = (cudaStream_t)stream;
   std::vector<SepPlan> plans(n);
   size_t need = 0;
+  bool any_tc = false;
   for (int i = 0; i < n; ++i) {
     if (int r = validate_problem(h, &probs[i], true, true)) return fail(h, r, "problem %d: %s", i, h->err.c_str());
-    if (int r = plan_separable(h, &probs[i], o, plans[i], h->num_sms)) return fail(h, r, "problem %d: %s", i, h->err.c_str());
+    if (int r = plan_separable(h, &probs[i], o, plans[i], h->num_sms))
+      return fail(h, r, "problem %d: %s", i, h->err.c_str());
+    if ((int64_t)probs[i].n_late * probs[i].n_prim > 0 && !gammas[i])
+      return fail(h, MODAL_EINVAL, "null gamma for problem %d", i);
     need = plans[i].bytes > need ? plans[i].bytes : need;
+    any_tc = any_tc || plans[i].prec == MODAL_PREC_OZAKI_BF16;
   }
   void *scratch;
-  if (int r = ws_get(h, 0, need, &scratch)) return r;
-  for (int i = 0; i < n; ++i) {
-    if ((int64_t)probs[i].n_late * probs[i].n_prim == 0) continue;
-    if (!gammas[i]) return fail(h, MODAL_EINVAL, "null gamma for problem %d", i);
-    if (int r = run_separable(h, h->num_sms, &probs[i], plans[i], gammas[i], (cudaStream_t)stream, scratch))
-      return r;
+  if (int r = ws_get(h, 0, need, &scratch)) return r;  // before capture: no allocation inside
+  uint64_t key = 1469598103934665603ULL;
+  key = fnv1a(key, &n, sizeof n);
+  key = fnv1a(key, probs, sizeof(modal_problem) * (size_t)n);
+  if (o) key = fnv1a(key, o, sizeof *o);
+  key = fnv1a(key, gammas, sizeof(double *) * (size_t)n);
+  key = fnv1a(key, &scratch, sizeof scratch);
+  key = fnv1a(key, &h->opt_triple_variant, sizeof(int));
+  key = fnv1a(key, &h->opt_split_k, sizeof(int));
+  key = fnv1a(key, &h->wait_cycles, sizeof(long long));
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    // capture every launch of the batch once, on a private stream
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const bool prof_on = h->prof.on;
+    h->prof.on = false;  // no event records inside the capture
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+    int rr = MODAL_OK;
+    bool first = true;
+    for (int i = 0; i < n && rr == MODAL_OK; ++i) {
+      if ((int64_t)probs[i].n_late * probs[i].n_prim == 0) continue;
+      rr = run_separable(h, h->num_sms, &probs[i], plans[i], gammas[i], h->cap_stream, scratch, first, true);
+      first = false;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+    h->prof.on = prof_on;
+    if (rr != MODAL_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rr;
+    }
+    if (ce != cudaSuccess) return fail(h, MODAL_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(h, MODAL_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    it = h->graphs.emplace(key, exec).first;
+  }
+  CK(cudaGraphLaunch(it->second, st));
+  if (any_tc) {
+    CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(scratch), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(h->err_event, st));
+    h->err_pending = true;
   }
   return MODAL_OK;
 }

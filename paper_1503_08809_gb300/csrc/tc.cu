@@ -52,12 +52,15 @@ constexpr int OZ_B_BYTES = OZ_SLICES * OZ_BN * OZ_ROWB;  // 40 KB
 constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;       // TMA warp, MMA warp, epilogue
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int OZ_LO_BYTES = OZ_BM * OZ_BN * 4;            // low halves of the running sums
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + OZ_LO_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+static_assert(OZ_SMEM <= 232448, "shared memory per CTA");
 constexpr long long OZ_WAIT_CYCLES = 4000000000LL;       // ~2 s at 2 GHz
 static_assert(OZ_KC % OZ_BK == 0, "chunk must hold whole stages");
 
 // error word bits
 constexpr int ERR_TIMEOUT = 1;
+constexpr int ERR_RANGE = 2;  // a value outside the FP32 exponent range of the split operands
 
 // ---------------------------------------------------------------------------
 // Splitting helpers (FP64 input)
@@ -69,30 +72,57 @@ __device__ __forceinline__ int exp_bound(double m) {  // smallest e with m <= 2^
   return e;
 }
 
-// Write the five slices of x / 2^e as BF16 values q_s 2^(-7 s).
-__device__ __forceinline__ void split5(double x, int e, __nv_bfloat16 *out, int64_t slice_stride) {
+// Exact 2^k as a float for k in [-126, 127] (built from the exponent bits).
+__device__ __forceinline__ float pow2f(int k) {
+  k = max(-126, min(127, k));
+  return __int_as_float((k + 127) << 23);
+}
+
+// Five slices of a double-FP32 value y = (h, l) with |y| <= 2^e: BF16 values
+// q_s 2^(-7 s) with q_s = round-to-nearest of the running residual x 2^7.
+__device__ __forceinline__ void split5_f2(float h, float l, int e, __nv_bfloat16 (&out)[OZ_SLICES]) {
   if (e < -99999) {
 #pragma unroll
-    for (int s = 0; s < OZ_SLICES; ++s) out[s * slice_stride] = __float2bfloat16_rn(0.f);
+    for (int s = 0; s < OZ_SLICES; ++s) out[s] = __float2bfloat16_rn(0.f);
     return;
   }
-  double r = ldexp(x, OZ_BETA - e);
+  // scale by 2^(7 - e) in two exact steps (the exponent range of y may be wide)
+  const int k = OZ_BETA - e;
+  const float s1 = pow2f(k / 2), s2 = pow2f(k - k / 2);
+  h = (h * s1) * s2;
+  l = (l * s1) * s2;
+  float w = 1.0f;
 #pragma unroll
   for (int s = 0; s < OZ_SLICES; ++s) {
-    double q = rint(r);
-    r = (r - q) * (double)(1 << OZ_BETA);
-    out[s * slice_stride] = __float2bfloat16_rn((float)ldexp(q, -OZ_BETA * s));
+    const float q = rintf(h);
+    const float t = h - q;  // exact: |h - q| <= 1/2
+    const float sum = t + l, bb = sum - t;
+    const float err = (t - (sum - bb)) + (l - bb);
+    out[s] = __float2bfloat16_rn(q * w);
+    h = sum * (float)(1 << OZ_BETA);
+    l = err * (float)(1 << OZ_BETA);
+    w *= 1.0f / (float)(1 << OZ_BETA);
   }
+}
+
+// exponent e with |x| <= 2^e for every |x| <= m (1 + 2^-20): room for the
+// low part of a double-FP32 value and for rounding of the maximum itself
+__device__ __forceinline__ int exp_bound_f(float m) {
+  if (!(m > 0.f)) return -100000;
+  int e;
+  frexpf(m * (1.0f + 1.0f / 1048576.0f), &e);
+  return e;
 }
 
 // Rows of the l-contraction operands.  Row r of A is A[j][l] q_a(l) with
 // r = (j, a); row r of B is q~_p(l, x0 + xl) with r = (xl, p).  One warp per
-// (row, K chunk): pass 1 finds max |x|, pass 2 writes the slices.
+// (row, K chunk): pass 1 finds max |x|, pass 2 writes the slices; only the
+// one product A q and the FP64 -> double-FP32 conversion use the FP64 unit.
 template <bool IS_A>
 __global__ void k_split_lrows(int64_t rows, int L, int Kpad, const double *__restrict__ Atab,
                               const double *__restrict__ q, const double *__restrict__ qt, int nbl, int nbp,
                               int x0, __nv_bfloat16 *__restrict__ out, int *__restrict__ ex,
-                              int *__restrict__ emax) {
+                              int *__restrict__ emax, int *__restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nch = cdiv(L, OZ_KC);
@@ -109,16 +139,25 @@ __global__ void k_split_lrows(int64_t rows, int L, int Kpad, const double *__res
     }
   };
   const int l0 = ch * OZ_KC, l1 = min(L, l0 + OZ_KC);
-  double m = 0.0;
-  for (int l = l0 + lane; l < l1; l += 32) m = fmax(m, fabs(val(l)));
+  float m = 0.f;
+  for (int l = l0 + lane; l < l1; l += 32) m = fmaxf(m, fabsf(__double2float_rn(val(l))));
 #pragma unroll
-  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  const int e = exp_bound(m);
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (!(m < 1e37f)) {  // also catches inf/NaN
+    if (lane == 0) atomicOr(err, ERR_RANGE);
+    m = 0.f;
+  }
+  const int e = exp_bound_f(m);
   const int64_t sstride = rows * (int64_t)Kpad;
   const int lend = min(Kpad, l0 + OZ_KC);
   for (int l = l0 + lane; l < lend; l += 32) {
-    double v = l < L ? val(l) : 0.0;
-    split5(v, e, out + r * Kpad + l, sstride);
+    const double v = l < L ? val(l) : 0.0;
+    const float h = __double2float_rn(v);
+    const float lo = __double2float_rn(v - (double)h);
+    __nv_bfloat16 o[OZ_SLICES];
+    split5_f2(h, lo, e, o);
+#pragma unroll
+    for (int s = 0; s < OZ_SLICES; ++s) out[s * sstride + r * Kpad + l] = o[s];
   }
   if (lane == 0) {
     ex[(int64_t)ch * rows + r] = e;
@@ -126,12 +165,18 @@ __global__ void k_split_lrows(int64_t rows, int L, int Kpad, const double *__res
   }
 }
 
-// words[0] = error bits (cleared once per call), words[1..] = exponent maxima
-__global__ void k_init_words(int *w, int reset_err) {
-  if (threadIdx.x == 0) {
-    if (reset_err) w[0] = 0;
-  } else if (threadIdx.x < 8) {
-    w[threadIdx.x] = -100000;
+// words[0] = error bits and words[1] = exponent maximum of the A operand of
+// the l contraction (both set once per call); words[2..7] = per-chunk maxima.
+// mode 0: per chunk (words 2..7); 1: per call (all); 2: per problem of a
+// batch (word 1 and 2..7, keeping the error bits of earlier problems)
+__global__ void k_init_words(int *w, int mode) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    if (mode == 1) w[0] = 0;
+  } else if (t == 1) {
+    if (mode != 0) w[1] = -100000;
+  } else if (t < 8) {
+    w[t] = -100000;
   }
 }
 
@@ -172,7 +217,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams P) {
   extern __shared__ unsigned char smraw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  uint64_t *full = (uint64_t *)(sm + OZ_STAGES * OZ_STAGE_BYTES);
+  float *lo_s = (float *)(sm + OZ_STAGES * OZ_STAGE_BYTES);  // [col][row]
+  uint64_t *full = (uint64_t *)(sm + OZ_STAGES * OZ_STAGE_BYTES + OZ_LO_BYTES);
   uint64_t *empty = full + OZ_STAGES;
   uint64_t *acc_full = empty + OZ_STAGES;
   uint64_t *acc_empty = acc_full + 1;
@@ -275,7 +321,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (!ptx::mbar_wait(&full[s], ph, abort_flag, P.wait_cycles)) break;
         ptx::tc_fence_after();
         const uint32_t a0 = sbase + s * OZ_STAGE_BYTES;
-        const uint32_t b0 = a0 + OZ_A_BYTES;
+        // descriptors of slice 0 at k = 0; the other operands differ only in the
+        // start-address field, by compile-time offsets (>> 4)
+        const uint64_t ad0 = ptx::smem_desc(a0, 16, 8 * OZ_ROWB, ptx::SW_64B);
+        const uint64_t bd0 = ptx::smem_desc(a0 + OZ_A_BYTES, 16, 8 * OZ_ROWB, ptx::SW_64B);
         bool fresh[3] = {chunk_start, chunk_start, chunk_start};
 #pragma unroll
         for (int kk = 0; kk < OZ_BK / 16; ++kk) {
@@ -285,8 +334,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int sb = 0; sb < OZ_SLICES; ++sb) {
               if (sa + sb > OZ_MAXLEV) continue;
               const int lev = sa + sb < 2 ? sa + sb : 2;
-              const uint64_t ad = ptx::smem_desc(a0 + sa * OZ_BM * OZ_ROWB + kk * 32, 16, 8 * OZ_ROWB, ptx::SW_64B);
-              const uint64_t bd = ptx::smem_desc(b0 + sb * OZ_BN * OZ_ROWB + kk * 32, 16, 8 * OZ_ROWB, ptx::SW_64B);
+              const uint64_t ad = ad0 + (uint64_t)((sa * OZ_BM * OZ_ROWB + kk * 32) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((sb * OZ_BN * OZ_ROWB + kk * 32) >> 4);
               ptx::mma_bf16(tmem + lev * OZ_BN, ad, bd, idesc, fresh[lev] ? 0u : 1u);
               fresh[lev] = false;
             }
@@ -312,9 +361,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int row = quarter * 32 + lane;     // tile row of this thread
     const int col0 = chalf * 64;
     const int ebias = (*P.emaxA) + (*P.emaxB) + 40;
-    float hi[64], lo[64];
+    float hi[64];  // high halves in registers, low halves in lo_s
 #pragma unroll
-    for (int c = 0; c < 64; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+    for (int c = 0; c < 64; ++c) {
+      hi[c] = 0.f;
+      lo_s[(col0 + c) * OZ_BM + row] = 0.f;
+    }
     bool ok = true;
     for (int ch = 0; ch < P.nchunks; ++ch) {
       if (!ptx::mbar_wait(acc_full, (uint32_t)(ch & 1), abort_flag, P.wait_cycles)) { ok = false; break; }
@@ -322,16 +374,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int ea = (a_row0 + row < P.rowsA) ? P.eA[(int64_t)ch * P.rowsA + a_row0 + row] : -100000;
       const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
-      for (int cb = 0; cb < 4; ++cb) {
-        float v0[16], v1[16], v2[16];
-        const uint32_t cc = (uint32_t)(col0 + cb * 16);
-        ptx::tmem_ld16(tl + cc, v0);
-        ptx::tmem_ld16(tl + OZ_BN + cc, v1);
-        ptx::tmem_ld16(tl + 2 * OZ_BN + cc, v2);
+      for (int cb = 0; cb < 16; ++cb) {
+        float v0[4], v1[4], v2[4];
+        const uint32_t cc = (uint32_t)(col0 + cb * 4);
+        ptx::tmem_ld4(tl + cc, v0);
+        ptx::tmem_ld4(tl + OZ_BN + cc, v1);
+        ptx::tmem_ld4(tl + 2 * OZ_BN + cc, v2);
         ptx::tmem_ld_wait();
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int c = cb * 16 + k;
+        for (int k = 0; k < 4; ++k) {
+          const int c = cb * 4 + k;
           const int64_t bcol = b_row0 + col0 + c;
           const int eb = (bcol < P.rowsB) ? __ldg(P.eB + (int64_t)ch * P.rowsB + bcol) : -100000;
           if (ea < -99999 || eb < -99999) continue;
@@ -340,19 +392,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           float bb = s - v0[k];
           float e = (v0[k] - (s - bb)) + (v1[k] - bb);
           e += v2[k];
-          const int sh = ea + eb - 2 * OZ_BETA - ebias;
-          df_add(hi[c], lo[c], ldexpf(s, sh), ldexpf(e, sh));
+          const int sh = ea + eb - 2 * OZ_BETA - ebias;  // <= -54 by the bias
+          const float f1 = pow2f(sh / 2), f2 = pow2f(sh - sh / 2);
+          float lo = lo_s[(col0 + c) * OZ_BM + row];
+          df_add(hi[c], lo, (s * f1) * f2, (e * f1) * f2);
+          lo_s[(col0 + c) * OZ_BM + row] = lo;
         }
       }
       ptx::tc_fence_before();
       ptx::mbar_arrive(acc_empty);
     }
     if (ok && !*abort_flag && row < R) {
-#pragma unroll 4
+#pragma unroll  // full unroll keeps hi[]/lo[] in registers
       for (int c = 0; c < 64; ++c) {
         const int col = col0 + c;
         if (col >= C) continue;
-        const double v = ldexp((double)hi[c] + (double)lo[c], ebias);
+        const double v = ldexp((double)hi[c] + (double)lo_s[(col0 + c) * OZ_BM + row], ebias);
         if (OUT_MODE == 0) {
           const int64_t rA = a_row0 + row, rB = b_row0 + col;
           const int j = (int)(rA / P.nbl), a = (int)(rA % P.nbl);
@@ -417,61 +472,90 @@ static int make_slices_map(CUtensorMap *m, const void *base, int64_t rows, int K
 
 static size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// scratch for one radial chunk: l-contraction slices + exponents, error word
-size_t tc_scratch_bytes(const SepShape &s, int nxc) {
+// Scratch layout (fixed order, sized for the largest radial chunk):
+//   [status words 1 KB][A slices][A exponents][B slices][B exponents][triple]
+struct LScratch {
+  int *words;
+  __nv_bfloat16 *As, *Bs;
+  int *eA, *eB;
+  char *end;
+};
+static LScratch l_scratch(void *scratch, const SepShape &s, int nxc) {
   const int Kpad = cdiv(s.L, OZ_BK) * OZ_BK;
   const int nch = cdiv(s.L, OZ_KC);
   const int64_t rowsA = (int64_t)s.n_mu * s.nbl, rowsB = (int64_t)nxc * s.nbp;
-  size_t b = 0;
-  b += up256((size_t)OZ_SLICES * rowsA * Kpad * 2) + up256((size_t)OZ_SLICES * rowsB * Kpad * 2);
-  b += up256((size_t)nch * rowsA * 4) + up256((size_t)nch * rowsB * 4);
-  b += 256 * 4;
-  b += tc_triple_scratch_bytes(s, nxc);
-  return b + 1024;
+  LScratch r;
+  char *w = (char *)scratch;
+  r.words = (int *)w; w += 256 * 4;
+  r.As = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * rowsA * Kpad * 2);
+  r.eA = (int *)w; w += up256((size_t)nch * rowsA * 4);
+  r.Bs = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * rowsB * Kpad * 2);
+  r.eB = (int *)w; w += up256((size_t)nch * rowsB * 4);
+  r.end = w;
+  return r;
 }
 
-int tc_contract_l(const SepShape &s, const double *A, const double *q, const double *qt, int x0, int nxc,
-                  double *M, void *scratch, long long wait_cycles, cudaStream_t st, char **scratch_end,
-                  bool reset_err) {
+size_t tc_scratch_bytes(const SepShape &s, int nxc, int variant) {
+  LScratch r = l_scratch(nullptr, s, nxc);
+  return (size_t)(r.end - (char *)nullptr) + tc_triple_scratch_bytes(s, nxc, variant) + 1024;
+}
+
+// Split the A operand of the l contraction (rows (j, a): w_l P_l(mu_j) q_a(l)),
+// which does not depend on x: once per call.
+int tc_prepare_l(const SepShape &s, const double *A, const double *q, void *scratch, int nxc_max, cudaStream_t st,
+                 Profiler *prof, bool reset_status) {
+  LScratch r = l_scratch(scratch, s, nxc_max);
+  const int Kpad = cdiv(s.L, OZ_BK) * OZ_BK;
+  const int nch = cdiv(s.L, OZ_KC);
+  const int64_t rowsA = (int64_t)s.n_mu * s.nbl;
+  cudaError_t e;
+  k_init_words<<<1, 32, 0, st>>>(r.words, reset_status ? 1 : 2);
+  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  {
+    ProfScope ps(prof, "tc_split_lA", st);
+    k_split_lrows<true><<<(unsigned)cdiv64(rowsA * nch * 32, 256), 256, 0, st>>>(rowsA, s.L, Kpad, A, q, nullptr,
+                                                                               s.nbl, s.nbp, 0, r.As, r.eA,
+                                                                               r.words + 1, r.words);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  return MODAL_OK;
+cuda_fail:
+  snprintf(g_tc_err, sizeof g_tc_err, "l-contraction operand split: %s", cudaGetErrorString(e));
+  return MODAL_ECUDA;
+}
+
+// l contraction of one radial chunk (A prepared by tc_prepare_l).
+int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_max, double *M, void *scratch,
+                  long long wait_cycles, cudaStream_t st, Profiler *prof) {
+  LScratch r = l_scratch(scratch, s, nxc_max);
   const int Kpad = cdiv(s.L, OZ_BK) * OZ_BK;
   const int nch = cdiv(s.L, OZ_KC);
   const int64_t rowsA = (int64_t)s.n_mu * s.nbl, rowsB = (int64_t)nxc * s.nbp;
-  // status words first, at a fixed offset whatever the chunk size:
-  // [0] error bits, [1] emaxA, [2] emaxB, [3] emax of the triple's B, [4] of Y
-  char *w = (char *)scratch;
-  int *words = (int *)w; w += 256 * 4;
-  __nv_bfloat16 *As = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * rowsA * Kpad * 2);
-  __nv_bfloat16 *Bs = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * rowsB * Kpad * 2);
-  int *eA = (int *)w; w += up256((size_t)nch * rowsA * 4);
-  int *eB = (int *)w; w += up256((size_t)nch * rowsB * 4);
-  if (scratch_end) *scratch_end = w;
   cudaError_t e;
-  k_init_words<<<1, 32, 0, st>>>(words, reset_err ? 1 : 0);
+  k_init_words<<<1, 32, 0, st>>>(r.words, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   {
-    const int64_t wa = rowsA * nch, wb = rowsB * nch;
-    k_split_lrows<true><<<(unsigned)cdiv64(wa * 32, 256), 256, 0, st>>>(rowsA, s.L, Kpad, A, q, qt, s.nbl, s.nbp,
-                                                                      x0, As, eA, words + 1);
-    if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
-    k_split_lrows<false><<<(unsigned)cdiv64(wb * 32, 256), 256, 0, st>>>(rowsB, s.L, Kpad, A, q, qt, s.nbl,
-                                                                       s.nbp, x0, Bs, eB, words + 2);
-    if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+    ProfScope ps(prof, "tc_split_lB", st);
+    k_split_lrows<false><<<(unsigned)cdiv64(rowsB * nch * 32, 256), 256, 0, st>>>(rowsB, s.L, Kpad, nullptr,
+                                                                                nullptr, qt, s.nbl, s.nbp, x0,
+                                                                                r.Bs, r.eB, r.words + 2, r.words);
   }
+  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   {
     CUtensorMap ta, tb;
-    if (int r = make_slices_map(&ta, As, rowsA, Kpad, OZ_BM)) return r;
-    if (int r = make_slices_map(&tb, Bs, rowsB, Kpad, OZ_BN)) return r;
+    if (int rr = make_slices_map(&ta, r.As, rowsA, Kpad, OZ_BM)) return rr;
+    if (int rr = make_slices_map(&tb, r.Bs, rowsB, Kpad, OZ_BN)) return rr;
     OzParams P{};
     P.rowsA = rowsA;
     P.rowsB = rowsB;
     P.Kpad = Kpad;
     P.nchunks = nch;
-    P.eA = eA;
-    P.eB = eB;
-    P.emaxA = words + 1;
-    P.emaxB = words + 2;
+    P.eA = r.eA;
+    P.eB = r.eB;
+    P.emaxA = r.words + 1;
+    P.emaxB = r.words + 2;
     P.out = M;
-    P.err = words;
+    P.err = r.words;
     P.n_mu = s.n_mu;
     P.nbl = s.nbl;
     P.nbp = s.nbp;
@@ -480,6 +564,7 @@ int tc_contract_l(const SepShape &s, const double *A, const double *q, const dou
         cudaSuccess)
       goto cuda_fail;
     dim3 grid((unsigned)cdiv64(rowsA, OZ_BM), (unsigned)cdiv64(rowsB, OZ_BN));
+    ProfScope ps(prof, "tc_gemm_l", st);
     k_ozaki_gemm<0><<<grid, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   }
@@ -525,22 +610,8 @@ __device__ __forceinline__ f2 df_addv(f2 a, f2 b) {
   return {h, e - (h - s.h)};
 }
 
-// Slices of a double-FP32 value y with |y| <= 2^e: q_s 2^(-7 s).
 __device__ __forceinline__ void split5_df(f2 y, int e, __nv_bfloat16 (&out)[OZ_SLICES]) {
-  if (e < -99999) {
-#pragma unroll
-    for (int s = 0; s < OZ_SLICES; ++s) out[s] = __float2bfloat16_rn(0.f);
-    return;
-  }
-  float h = ldexpf(y.h, OZ_BETA - e), l = ldexpf(y.l, OZ_BETA - e);
-#pragma unroll
-  for (int s = 0; s < OZ_SLICES; ++s) {
-    float q = rintf(h);
-    f2 r = df_two_sum(h - q, l);  // h - q is exact (|h - q| <= 1/2)
-    out[s] = __float2bfloat16_rn(ldexpf(q, -OZ_BETA * s));
-    h = r.h * (float)(1 << OZ_BETA);
-    l = r.l * (float)(1 << OZ_BETA);
-  }
+  split5_f2(y.h, y.l, e, out);
 }
 
 // Per chunk of OZ_KC slices and block of 64 columns: exact max |M| (B-operand
@@ -552,7 +623,7 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
                                                       const double *__restrict__ xw, f2 *__restrict__ Mdf,
                                                       f2 *__restrict__ wdf, double *__restrict__ mxW,
                                                       int *__restrict__ eB, __nv_bfloat16 *__restrict__ Bt,
-                                                      int *__restrict__ emaxB) {
+                                                      int *__restrict__ emaxB, int *__restrict__ err) {
   __shared__ double red1[4][TP_COLS], red2[4][TP_COLS];
   __shared__ int esh[TP_COLS];
   __shared__ __nv_bfloat16 tile[OZ_SLICES][TP_COLS][32 + 8];
@@ -580,12 +651,20 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
       m1 = fmax(m1, red1[i][tc]);
       m2 = fmax(m2, red2[i][tc]);
     }
+    // Y = w (M M + M M) must stay inside the FP32 range of the double-FP32 form
+    if (!(m1 < 1e37) || !(m2 < 1e18)) {
+      atomicOr(err, ERR_RANGE);
+      m1 = 0.0;
+      m2 = 0.0;
+    }
     const int e = exp_bound(m1);
     esh[tc] = e;
     if (col < nblp) {
       eB[(int64_t)ch * nblp + col] = e;
       mxW[(int64_t)ch * nblp + col] = m2 * (1.0 + 1e-12);  // room for the rounding of sqrt(w)
       if (e > -99999) atomicMax(emaxB, e);
+      const int ew = exp_bound(m2 * (1.0 + 1e-12));
+      if (ew > -99999) atomicMax(emaxB + 2, ew);  // words[5]: bound of max sqrt(w)|M|
     }
   }
   __syncthreads();
@@ -677,58 +756,359 @@ __global__ void __launch_bounds__(256) k_tp_make_y(int64_t rowsY, int64_t K, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused triple product: the eight producer/epilogue warps form the Y operand
+// (double-FP32 products of M entries, split into five BF16 slices) directly in
+// the 64-byte-swizzled shared-memory stage that the tensor core reads, so Y
+// never goes through HBM; the B operand (M slices) comes by TMA.
+//   warp 0: TMA for B;  warp 1: TMEM allocation and MMA issue;
+//   warps 2-9: produce Y stages, and drain the accumulators of chunk c while
+//              producing chunk c+1 (after OZ_STAGES stages of it).
+// ---------------------------------------------------------------------------
+struct FusedParams {
+  int64_t rowsB;  // B operand rows (nb_late * nb_prim)
+  int Kpad;
+  int64_t K;      // valid slices of this launch
+  int nchunks, nbp, nblp, P2;
+  const f2 *Mdf;     // [K][nblp]
+  const f2 *wdf;     // [K]
+  const double *mxW; // [nchunks][nblp]
+  const int *eB;     // [nchunks][nblp]
+  const int *emaxB;  // max of eB
+  const int *emaxW;  // exponent bound of max mxW
+  double *G;
+  GLayout g;
+  int *err;
+  long long wait_cycles;
+  int chunks_per_split;  // K chunks per CTA along blockIdx.y (split-K)
+  int split_k;           // number of K splits (> 1: FP64 atomic adds into G)
+};
+
+__device__ __forceinline__ int y_exp(const double *mw, int nbp, int a, int b, int u, int v) {
+  return exp_bound(mw[a * nbp + u] * mw[b * nbp + v] + mw[a * nbp + v] * mw[b * nbp + u]);
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_ozaki_triple_fused(const __grid_constant__ CUtensorMap tmB, FusedParams P) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  float *lo_s = (float *)(sm + OZ_STAGES * OZ_STAGE_BYTES);  // [col][row]
+  uint64_t *full = (uint64_t *)(sm + OZ_STAGES * OZ_STAGE_BYTES + OZ_LO_BYTES);
+  uint64_t *empty = full + OZ_STAGES;
+  uint64_t *acc_full = empty + OZ_STAGES;
+  uint64_t *acc_empty = acc_full + 1;
+  uint64_t *mma_done = acc_empty + 1;
+  uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NPROD = 32 * OZ_EPI_WARPS;  // 256 producer threads
+
+  // ---- tile of the G block ----
+  int t = blockIdx.x, rt = 0, ct = 0, bblk;
+  int64_t rowoff = 0;
+  for (bblk = 0; bblk < P.g.nbl; ++bblk) {
+    const int nrt = (int)cdiv64(P.g.rows(bblk), OZ_BM), nct = (int)cdiv64(P.g.cols(bblk), OZ_BN);
+    if (t < nrt * nct) {
+      rt = t / nct;
+      ct = t % nct;
+      break;
+    }
+    t -= nrt * nct;
+    rowoff += P.g.rows(bblk);
+  }
+  if (bblk >= P.g.nbl) return;
+  const int64_t a_row0 = rowoff + (int64_t)rt * OZ_BM;  // global Y row of the tile start
+  const int64_t b_row0 = (int64_t)bblk * P.g.nbp + (int64_t)ct * OZ_BN;
+  const int64_t R = min((int64_t)OZ_BM, P.g.rows(bblk) - (int64_t)rt * OZ_BM);
+  const int64_t C = min((int64_t)OZ_BN, P.g.cols(bblk) - (int64_t)ct * OZ_BN);
+  const int64_t out_base = P.g.offset(bblk) + (int64_t)rt * OZ_BM * P.g.cols(bblk) + (int64_t)ct * OZ_BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      ptx::mbar_init(&full[s], 1 + NPROD);  // TMA expect_tx arrival + every producer
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(acc_full, 1);
+    ptx::mbar_init(acc_empty, NPROD);
+    ptx::mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_slot, 512);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int steps_per_chunk = OZ_KC / OZ_BK;
+  // this CTA's K range: chunks [c_lo, c_hi), stages [i_lo, i_hi)
+  const int c_lo = blockIdx.y * P.chunks_per_split;
+  const int c_hi = min(P.nchunks, c_lo + P.chunks_per_split);
+  const int i_lo = c_lo * steps_per_chunk;
+  const int i_hi = min(P.Kpad / OZ_BK, c_hi * steps_per_chunk);
+  const int nloc = c_hi - c_lo;  // chunks of this CTA
+
+  if (warp == 0) {
+    // ================= TMA producer (B operand) =================
+    if (lane == 0) {
+      ptx::prefetch_tmap(&tmB);
+      int issued = 0;
+      for (int i = i_lo; i < i_hi; ++i) {
+        const int s = (i - i_lo) % OZ_STAGES;
+        const uint32_t ph = (uint32_t)(((i - i_lo) / OZ_STAGES) & 1);
+        if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_cycles)) break;
+        ptx::mbar_arrive_expect_tx(&full[s], OZ_B_BYTES);
+        ptx::tma_load_3d(sm + s * OZ_STAGE_BYTES + OZ_A_BYTES, &tmB, &full[s], i * OZ_BK, (int)b_row0, 0);
+        ++issued;
+      }
+      if (*abort_flag) {  // let the copies in flight land before the CTA ends
+        for (int j = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); j < issued; ++j) {
+          volatile int dummy = 0;
+          ptx::mbar_wait(&full[j % OZ_STAGES], (uint32_t)((j / OZ_STAGES) & 1), &dummy, OZ_WAIT_CYCLES);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ================= MMA issuer =================
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_bf16_f32(OZ_BM, OZ_BN);
+      const uint32_t sbase = ptx::smem_u32(sm);
+      int chunk = 0;  // local chunk count
+      for (int i = i_lo; i < i_hi; ++i) {
+        const int s = (i - i_lo) % OZ_STAGES;
+        const uint32_t ph = (uint32_t)(((i - i_lo) / OZ_STAGES) & 1);
+        const bool chunk_start = (i % steps_per_chunk) == 0;
+        if (chunk_start && chunk > 0) {
+          if (!ptx::mbar_wait(acc_empty, (uint32_t)((chunk - 1) & 1), abort_flag, P.wait_cycles)) break;
+        }
+        if (!ptx::mbar_wait(&full[s], ph, abort_flag, P.wait_cycles)) break;
+        ptx::tc_fence_after();
+        const uint32_t a0 = sbase + s * OZ_STAGE_BYTES;
+        const uint64_t ad0 = ptx::smem_desc(a0, 16, 8 * OZ_ROWB, ptx::SW_64B);
+        const uint64_t bd0 = ptx::smem_desc(a0 + OZ_A_BYTES, 16, 8 * OZ_ROWB, ptx::SW_64B);
+        bool fresh[3] = {chunk_start, chunk_start, chunk_start};
+#pragma unroll
+        for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+#pragma unroll
+          for (int sa = 0; sa < OZ_SLICES; ++sa) {
+#pragma unroll
+            for (int sb = 0; sb < OZ_SLICES; ++sb) {
+              if (sa + sb > OZ_MAXLEV) continue;
+              const int lev = sa + sb < 2 ? sa + sb : 2;
+              const uint64_t ad = ad0 + (uint64_t)((sa * OZ_BM * OZ_ROWB + kk * 32) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((sb * OZ_BN * OZ_ROWB + kk * 32) >> 4);
+              ptx::mma_bf16(tmem + lev * OZ_BN, ad, bd, idesc, fresh[lev] ? 0u : 1u);
+              fresh[lev] = false;
+            }
+          }
+        }
+        ptx::mma_commit(&empty[s]);
+        const bool chunk_end = ((i + 1) % steps_per_chunk) == 0 || i + 1 == i_hi;
+        if (chunk_end) {
+          ptx::mma_commit(acc_full);
+          ++chunk;
+        }
+      }
+      ptx::mma_commit(mma_done);
+      volatile int dummy = 0;
+      ptx::mbar_wait(mma_done, 0, &dummy, OZ_WAIT_CYCLES);
+    }
+  } else {
+    // ================= Y producers + accumulator drains =================
+    const int tp = threadIdx.x - 64;  // 0..255
+    // production role: row prow of the tile, 16 of the 32 k of each stage
+    const int prow = tp & (OZ_BM - 1), khalf = tp >> 7;
+    const bool pvalid = prow < R;
+    int pa = 0, pb = 0, pu = 0, pv = 0;
+    if (pvalid) y_row_decode(a_row0 + prow, P.P2, pb, pa, pu, pv);
+    const int o_au = pa * P.nbp + pu, o_bv = pb * P.nbp + pv, o_av = pa * P.nbp + pv, o_bu = pb * P.nbp + pu;
+    const uint32_t swz = (uint32_t)((prow >> 1) & 3);
+    // drain role: TMEM lane quarter of this warp, one half of the columns
+    const int quarter = warp & 3, chalf = (warp - 2) >> 2;
+    const int erow = quarter * 32 + lane, col0 = chalf * 64;
+    const bool evalid = erow < R;
+    int ea_a = 0, ea_b = 0, ea_u = 0, ea_v = 0;
+    if (evalid) y_row_decode(a_row0 + erow, P.P2, ea_b, ea_a, ea_u, ea_v);
+    const int ebias = 2 * (*P.emaxW) + 1 + (*P.emaxB) + 40;
+    float hi[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+      hi[c] = 0.f;
+      lo_s[(col0 + c) * OZ_BM + erow] = 0.f;
+    }
+    const uint32_t sbase = ptx::smem_u32(sm);
+    int drained = 0, e_row = -100000;
+    bool ok = true;
+
+    // drain local chunk lc (global chunk c_lo + lc)
+    auto drain = [&](int lc) -> bool {
+      const int ch = c_lo + lc;
+      if (!ptx::mbar_wait(acc_full, (uint32_t)(lc & 1), abort_flag, P.wait_cycles)) return false;
+      ptx::tc_fence_after();
+      const int ea = evalid ? y_exp(P.mxW + (int64_t)ch * P.nblp, P.nbp, ea_a, ea_b, ea_u, ea_v) : -100000;
+      const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+      for (int cb = 0; cb < 16; ++cb) {
+        float v0[4], v1[4], v2[4];
+        const uint32_t cc = (uint32_t)(col0 + cb * 4);
+        ptx::tmem_ld4(tl + cc, v0);
+        ptx::tmem_ld4(tl + OZ_BN + cc, v1);
+        ptx::tmem_ld4(tl + 2 * OZ_BN + cc, v2);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = cb * 4 + k;
+          const int64_t bcol = b_row0 + col0 + c;
+          const int eb = (bcol < P.rowsB) ? __ldg(P.eB + (int64_t)ch * P.rowsB + bcol) : -100000;
+          if (ea < -99999 || eb < -99999) continue;
+          float sv = v0[k] + v1[k];
+          float bb = sv - v0[k];
+          float ev = (v0[k] - (sv - bb)) + (v1[k] - bb);
+          ev += v2[k];
+          const int sh = ea + eb - 2 * OZ_BETA - ebias;
+          const float f1 = pow2f(sh / 2), f2v = pow2f(sh - sh / 2);
+          float lo = lo_s[(col0 + c) * OZ_BM + erow];
+          df_add(hi[c], lo, (sv * f1) * f2v, (ev * f1) * f2v);
+          lo_s[(col0 + c) * OZ_BM + erow] = lo;
+        }
+      }
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(acc_empty);
+      return true;
+    };
+
+    for (int i = i_lo; i < i_hi && ok; ++i) {
+      const int ch = i / steps_per_chunk, lc = ch - c_lo;
+      if (i % steps_per_chunk == 0) {
+        e_row = pvalid ? y_exp(P.mxW + (int64_t)ch * P.nblp, P.nbp, pa, pb, pu, pv) : -100000;
+      }
+      if (lc >= 1 && i % steps_per_chunk == OZ_STAGES && drained == lc - 1) {
+        if (!drain(lc - 1)) { ok = false; break; }
+        drained = lc;
+      }
+      const int s = (i - i_lo) % OZ_STAGES;
+      const uint32_t ph = (uint32_t)(((i - i_lo) / OZ_STAGES) & 1);
+      if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_cycles)) { ok = false; break; }
+      const uint32_t abase = sbase + s * OZ_STAGE_BYTES + prow * OZ_ROWB;
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {  // two 16-byte granules (8 k each) of this thread
+        uint32_t pk[OZ_SLICES][4];
+#pragma unroll
+        for (int kk = 0; kk < 8; kk += 2) {
+          __nv_bfloat16 o0[OZ_SLICES], o1[OZ_SLICES];
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int64_t kg = (int64_t)i * OZ_BK + khalf * 16 + g * 8 + kk + h2;
+            f2 y = {0.f, 0.f};
+            if (pvalid && kg < P.K) {
+              const f2 *Mk = P.Mdf + kg * P.nblp;
+              const f2 sv = df_addv(df_mul(Mk[o_au], Mk[o_bv]), df_mul(Mk[o_av], Mk[o_bu]));
+              y = df_mul(P.wdf[kg], sv);
+            }
+            if (h2 == 0) split5_f2(y.h, y.l, e_row, o0);
+            else split5_f2(y.h, y.l, e_row, o1);
+          }
+#pragma unroll
+          for (int sl = 0; sl < OZ_SLICES; ++sl)
+            pk[sl][kk / 2] = (uint32_t)__bfloat16_as_ushort(o0[sl]) | ((uint32_t)__bfloat16_as_ushort(o1[sl]) << 16);
+        }
+        const uint32_t gran = (uint32_t)(khalf * 2 + g) ^ swz;
+#pragma unroll
+        for (int sl = 0; sl < OZ_SLICES; ++sl)
+          ptx::st_shared_v4(abase + sl * OZ_BM * OZ_ROWB + (gran << 4), pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+      }
+      ptx::fence_proxy_async_smem();
+      ptx::mbar_arrive(&full[s]);
+    }
+    // chunks not drained inside the loop (the last one or two)
+    for (int lc = drained; ok && lc < nloc; ++lc) {
+      if (!drain(lc)) { ok = false; break; }
+    }
+    if (ok && !*abort_flag && evalid) {
+#pragma unroll
+      for (int c = 0; c < 64; ++c) {
+        const int col = col0 + c;
+        if (col >= C) continue;
+        const double v = ldexp((double)hi[c] + (double)lo_s[col * OZ_BM + erow], ebias);
+        double *d = P.G + out_base + (int64_t)erow * P.g.cols(bblk) + col;
+        if (P.split_k > 1) atomicAdd(d, v);
+        else *d += v;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(P.err, ERR_TIMEOUT);
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 512);
+  }
+}
+
 static int64_t y_rows(const SepShape &s) {
   const int64_t P2 = (int64_t)s.nbp * (s.nbp + 1) / 2;
   return P2 * s.nbl * (s.nbl + 1) / 2;
 }
 
-size_t tc_triple_scratch_bytes(const SepShape &s, int nxc) {
+size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
   const int64_t K = (int64_t)nxc * s.n_mu;
   const int Kpad = (int)(cdiv64(K, 64) * 64);
   const int64_t nblp = (int64_t)s.nbl * s.nbp;
   const int nch = (int)cdiv64(K, OZ_KC);
-  const int64_t rowsY = y_rows(s);
   size_t b = 0;
   b += up256((size_t)K * nblp * 8) + up256((size_t)K * 8);            // Mdf, wdf
   b += up256((size_t)nch * nblp * 8) + up256((size_t)nch * nblp * 4);  // mxW, eB
   b += up256((size_t)OZ_SLICES * nblp * Kpad * 2);                     // Bt
-  b += up256((size_t)nch * rowsY * 4);                                 // eY
-  b += up256((size_t)OZ_SLICES * rowsY * Kpad * 2);                    // Y slices
+  if (variant == TC_TRIPLE_MATERIALISED) {
+    const int64_t rowsY = y_rows(s);
+    b += up256((size_t)nch * rowsY * 4);                                // eY
+    b += up256((size_t)OZ_SLICES * rowsY * Kpad * 2);                   // Y slices
+  }
   return b;
 }
 
-int tc_separable_chunk(const SepShape &s, const double *A, const double *q, const double *qt, const double *om,
-                       const double *xw, int x0, int nxc, double *M, double *G, bool accumulate, void *scratch,
-                       int num_sms, long long wait_cycles, cudaStream_t st) {
-  (void)num_sms;
-  char *w = nullptr;
-  if (int r = tc_contract_l(s, A, q, qt, x0, nxc, M, scratch, wait_cycles, st, &w, !accumulate)) return r;
-  int *words = (int *)scratch;  // status words written by tc_contract_l
+int tc_separable_chunk(const SepShape &s, const double *qt, const double *om, const double *xw, int x0, int nxc,
+                       int nxc_max, double *M, double *G, bool accumulate, void *scratch, long long wait_cycles,
+                       int num_sms, int variant, int split_k, cudaStream_t st, Profiler *prof) {
+  if (int r = tc_contract_l(s, qt, x0, nxc, nxc_max, M, scratch, wait_cycles, st, prof)) return r;
+  LScratch ls = l_scratch(scratch, s, nxc_max);
+  char *w = ls.end;
+  int *words = ls.words;
   cudaError_t e;
   const int64_t K = (int64_t)nxc * s.n_mu;
   const int Kpad = (int)(cdiv64(K, 64) * 64);
   const int nblp = s.nbl * s.nbp;
   const int nch = (int)cdiv64(K, OZ_KC);
-  const int64_t rowsY = y_rows(s);
   const int P2 = s.nbp * (s.nbp + 1) / 2;
   f2 *Mdf = (f2 *)w; w += up256((size_t)K * nblp * 8);
   f2 *wdf = (f2 *)w; w += up256((size_t)K * 8);
   double *mxW = (double *)w; w += up256((size_t)nch * nblp * 8);
   int *eB = (int *)w; w += up256((size_t)nch * nblp * 4);
-  __nv_bfloat16 *Bt = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * nblp * Kpad * 2);
-  int *eY = (int *)w; w += up256((size_t)nch * rowsY * 4);
-  __nv_bfloat16 *Ysl = (__nv_bfloat16 *)w;
+  __nv_bfloat16 *Bt = (__nv_bfloat16 *)w;
   if (!accumulate) {
     GLayout g = make_glayout(s.nbl, s.nbp);
     if ((e = launch_zero(G, (size_t)g.size(), st)) != cudaSuccess) goto cuda_fail;
   }
-  k_tp_prep_cols<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)nch), 256, 0, st>>>(
-      K, Kpad, nblp, s.n_mu, x0, M, om, xw, Mdf, wdf, mxW, eB, Bt, words + 3);
-  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
-  k_tp_make_y<<<dim3((unsigned)cdiv64(rowsY, TY_ROWS), (unsigned)(Kpad / TY_K)), 256, 0, st>>>(
-      rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, wdf, mxW, eY, Ysl, words + 4);
-  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   {
+    ProfScope ps(prof, "tc_prep_M", st);
+    k_tp_prep_cols<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)nch), 256, 0, st>>>(
+        K, Kpad, nblp, s.n_mu, x0, M, om, xw, Mdf, wdf, mxW, eB, Bt, words + 3, words);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  if (variant == TC_TRIPLE_MATERIALISED) {
+    // Y slices through HBM, then the TMA-fed GEMM for both operands
+    const int64_t rowsY = y_rows(s);
+    char *wy = (char *)Bt + up256((size_t)OZ_SLICES * nblp * Kpad * 2);
+    int *eY = (int *)wy;
+    wy += up256((size_t)nch * rowsY * 4);
+    __nv_bfloat16 *Ysl = (__nv_bfloat16 *)wy;
+    {
+      ProfScope ps(prof, "tc_make_Y", st);
+      k_tp_make_y<<<dim3((unsigned)cdiv64(rowsY, TY_ROWS), (unsigned)(Kpad / TY_K)), 256, 0, st>>>(
+          rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, wdf, mxW, eY, Ysl, words + 4);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
     CUtensorMap ta, tb;
     if (int r = make_slices_map(&ta, Ysl, rowsY, Kpad, OZ_BM)) return r;
     if (int r = make_slices_map(&tb, Bt, nblp, Kpad, OZ_BN)) return r;
@@ -750,7 +1130,47 @@ int tc_separable_chunk(const SepShape &s, const double *A, const double *q, cons
     if ((e = cudaFuncSetAttribute(k_ozaki_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
         cudaSuccess)
       goto cuda_fail;
+    ProfScope ps(prof, "tc_gemm_triple", st);
     k_ozaki_gemm<1><<<(unsigned)tiles, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+    return MODAL_OK;
+  }
+  {
+    CUtensorMap tb;
+    if (int r = make_slices_map(&tb, Bt, nblp, Kpad, OZ_BN)) return r;
+    FusedParams F{};
+    F.rowsB = nblp;
+    F.Kpad = Kpad;
+    F.K = K;
+    F.nchunks = nch;
+    F.nbp = s.nbp;
+    F.nblp = nblp;
+    F.P2 = P2;
+    F.Mdf = Mdf;
+    F.wdf = wdf;
+    F.mxW = mxW;
+    F.eB = eB;
+    F.emaxB = words + 3;
+    F.emaxW = words + 5;
+    F.G = G;
+    F.g = make_glayout(s.nbl, s.nbp);
+    F.err = words;
+    F.wait_cycles = wait_cycles;
+    int64_t tiles = 0;
+    for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(F.g.rows(b), OZ_BM) * cdiv64(F.g.cols(b), OZ_BN);
+    // split K when the tiles alone cannot fill two waves of one CTA per SM,
+    // keeping at least 4 chunks of 1024 slices per split
+    int ks = (int)cdiv64(2LL * num_sms, tiles);
+    ks = ks < nch / 4 ? ks : nch / 4;
+    if (split_k > 0) ks = split_k < nch ? split_k : nch;
+    if (ks < 1) ks = 1;
+    F.chunks_per_split = (int)cdiv64(nch, ks);
+    F.split_k = (int)cdiv64(nch, F.chunks_per_split);
+    if ((e = cudaFuncSetAttribute(k_ozaki_triple_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
+        cudaSuccess)
+      goto cuda_fail;
+    ProfScope ps(prof, "tc_gemm_triple", st);
+    k_ozaki_triple_fused<<<dim3((unsigned)tiles, (unsigned)F.split_k), OZ_THREADS, OZ_SMEM, st>>>(tb, F);
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   }
   return MODAL_OK;
@@ -759,7 +1179,7 @@ cuda_fail:
   return MODAL_ECUDA;
 }
 
-int *tc_error_word(void *scratch, const SepShape &, int) { return (int *)scratch; }
+int *tc_error_word(void *scratch) { return (int *)scratch; }
 
 void tc_release(int) {}
 

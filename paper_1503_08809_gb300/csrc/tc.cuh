@@ -2,22 +2,29 @@
 #pragma once
 #include "common.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace modal {
-size_t tc_scratch_bytes(const SepShape &s, int nxc);
-size_t tc_triple_scratch_bytes(const SepShape &s, int nxc);
-// l contraction of one radial chunk on the tensor cores: M (FP64) [xl][j][a][p].
-int tc_contract_l(const SepShape &s, const double *A, const double *q, const double *qt, int x0, int nxc,
-                  double *M, void *scratch, long long wait_cycles, cudaStream_t st, char **scratch_end,
-                  bool reset_err);
+// triple-product variants: the Y operand through HBM, or formed in shared memory
+constexpr int TC_TRIPLE_MATERIALISED = 0;
+constexpr int TC_TRIPLE_FUSED = 1;
+size_t tc_scratch_bytes(const SepShape &s, int nxc, int variant);
+size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant);
 // default bound of every device-side wait of the tensor-core kernels (SM clocks)
 constexpr long long TC_DEFAULT_WAIT_CYCLES = 4000000000LL;
+// Split the x-independent A operand of the l contraction (once per call).
+int tc_prepare_l(const SepShape &s, const double *A, const double *q, void *scratch, int nxc_max, cudaStream_t st,
+                 Profiler *prof = nullptr, bool reset_status = true);
+// l contraction of one radial chunk on the tensor cores: M (FP64) [xl][j][a][p].
+int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_max, double *M, void *scratch,
+                  long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
 // One radial chunk: M (FP64 scratch for the chunk) and G (+)= triple product.
-int tc_separable_chunk(const SepShape &s, const double *A, const double *q, const double *qt,
-                       const double *om, const double *xw, int x0, int nxc, double *M, double *G,
-                       bool accumulate, void *scratch, int num_sms, long long wait_cycles, cudaStream_t st);
-// device error word of the tensor-core scratch (bit 0: a bounded wait gave up)
-int *tc_error_word(void *scratch, const SepShape &s, int nxc);
+int tc_separable_chunk(const SepShape &s, const double *qt, const double *om, const double *xw, int x0, int nxc,
+                       int nxc_max, double *M, double *G, bool accumulate, void *scratch, long long wait_cycles,
+                       int num_sms, int variant, int split_k, cudaStream_t st, Profiler *prof = nullptr);
+// device status word of the tensor-core scratch (bit 0: a bounded wait gave up,
+// bit 1: a value outside the FP32 exponent range of the split operands)
+int *tc_error_word(void *scratch);
 const char *tc_last_error();
 void tc_release(int device);
 }  // namespace modal

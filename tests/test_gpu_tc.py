@@ -93,3 +93,20 @@ def test_tc_planck_sampled(mg):
     assert np.abs(g[np.ix_(late_pick, prim_pick)] - ref).max() / np.abs(ref).max() < TOL_MIXED
     g64 = mg.project_separable(dp).cpu().numpy()
     assert normwise(g, g64) < TOL_MIXED
+
+
+@pytest.mark.parametrize("shape,split_k", [((48, 5, 5, 24), 0), ((60, 12, 11, 7), 0),
+                                           ((130, 4, 4, 9), 3), ((300, 10, 10, 6), 0)])
+def test_tc_fused_variant(mg, shape, split_k):
+    """Y formed in shared memory inside the GEMM (MODAL_OPT_TC_TRIPLE_FUSED),
+    with automatic or forced K splits (combined by FP64 atomic adds)."""
+    lmax, nbl, nbp, nx = shape
+    P = syn.make_problem(lmax, nbl, nx, seed=13, nb_prim=nbp)
+    h = mg.Handle()
+    mg.set_option(mg.OPT_TC_TRIPLE_FUSED, 1, handle=h)
+    mg.set_option(mg.OPT_TC_SPLIT_K, split_k, handle=h)
+    g = mg.project_separable(mg.DeviceProblem.from_host(P, handle=h), precision=mg.PREC_OZAKI_BF16,
+                             handle=h)
+    mg.handle_status(handle=h)
+    assert normwise(g, oracle.separable(P)) < TOL_MIXED
+    h.close()
