@@ -310,7 +310,7 @@ int modal_contract_l(modal_handle *h, const modal_problem *p, int32_t n_mu, cons
     return MODAL_OK;
   }
   void *scratch;
-  if (int r = ws_get(h, 0, tc_scratch_bytes(s, p->n_x, TC_TRIPLE_FUSED), &scratch)) return r;
+  if (int r = ws_get(h, 0, tc_scratch_bytes(s, p->n_x, 1, TC_TRIPLE_FUSED), &scratch)) return r;
   {
     PROF(h, "tc_contract_l", st);
     if (int r = tc_prepare_l(s, A, p->q, scratch, p->n_x, st)) return fail(h, r, "%s", tc_last_error());
@@ -330,6 +330,7 @@ struct SepPlan {
   SepShape s;
   int prec;
   int variant;  // tensor-core triple-product variant
+  int nxl;      // radial points per l-contraction chunk (tensor-core form; = nxc otherwise)
   int nxc;      // radial points per chunk
   int ksplit;   // K split of the SIMT triple product
   size_t elem;  // bytes per M element
@@ -370,6 +371,16 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
     pl.nxc = (int)(c < 1 ? 1 : (c > p->n_x ? p->n_x : c));
   }
   if (pl.nxc < 1) pl.nxc = 1;
+  pl.nxl = pl.nxc;
+  if (prec == MODAL_PREC_OZAKI_BF16 && pl.variant == TC_TRIPLE_MATERIALISED) {
+    // the l contraction runs on up to 64 radial points at once (M <= 1 GiB),
+    // a whole number of triple-product chunks
+    int64_t c = ((int64_t)1 << 30) / ((int64_t)n_mu * nblp * 8);
+    if (c > 64) c = 64;
+    if (c > p->n_x) c = p->n_x;
+    c = c / pl.nxc * pl.nxc;
+    pl.nxl = (int)(c < pl.nxc ? pl.nxc : c);
+  }
   GLayout g = make_glayout(p->nb_late, p->nb_prim);
   pl.Gsize = g.size();
   pl.ksplit = triple_ksplit(pl.s, pl.nxc, num_sms);
@@ -378,10 +389,10 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   size_t b = 0;
   b += 2 * align256(sizeof(double) * n_mu);                      // mu, om
   b += align256(sizeof(double) * (size_t)n_mu * pl.s.L);          // A
-  b += align256(pl.elem * (size_t)pl.nxc * n_mu * nblp);          // M chunk
+  b += align256(pl.elem * (size_t)pl.nxl * n_mu * nblp);          // M chunk
   b += align256(sizeof(double) * (size_t)pl.Gsize);               // G
   if (need_part) b += align256(sizeof(double) * (size_t)pl.Gsize * pl.ksplit);
-  if (prec == MODAL_PREC_OZAKI_BF16) b += tc_scratch_bytes(pl.s, pl.nxc, pl.variant);
+  if (prec == MODAL_PREC_OZAKI_BF16) b += tc_scratch_bytes(pl.s, pl.nxl, pl.nxc, pl.variant);
   pl.bytes = b + 1024;
   return MODAL_OK;
 }
@@ -391,14 +402,18 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
                          bool capturing = false) {
   const SepShape &s = pl.s;
   Bump bp{(char *)scratch};
+  // the tensor-core scratch comes first, so that its status words sit at the
+  // same address for every problem of a batch
+  void *tcs = (pl.prec == MODAL_PREC_OZAKI_BF16)
+                  ? bp.take<char>(tc_scratch_bytes(s, pl.nxl, pl.nxc, pl.variant))
+                  : nullptr;
   double *mu = bp.take<double>(s.n_mu), *om = bp.take<double>(s.n_mu);
   double *A = bp.take<double>((size_t)s.n_mu * s.L);
-  void *M = bp.take<char>(pl.elem * (size_t)pl.nxc * s.n_mu * s.nbl * s.nbp);
+  void *M = bp.take<char>(pl.elem * (size_t)pl.nxl * s.n_mu * s.nbl * s.nbp);
   double *G = bp.take<double>((size_t)pl.Gsize);
   const int nchunks = (p->n_x + pl.nxc - 1) / pl.nxc;
   const bool need_part = pl.ksplit > 1 || nchunks > 1;
   double *Gpart = need_part ? bp.take<double>((size_t)pl.Gsize * pl.ksplit) : nullptr;
-  void *tcs = (pl.prec == MODAL_PREC_OZAKI_BF16) ? bp.take<char>(tc_scratch_bytes(s, pl.nxc, pl.variant)) : nullptr;
 
   {
     PROF(h, "gl_nodes", st);
@@ -431,15 +446,25 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
       CK(launch_triple<float>(s, (float *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
                               num_sms, st));
     } else {
+      // tensor-core form: the l contraction over an l-chunk of nxl points,
+      // then the triple product over its chunks of nxc points
+      if (x0 % pl.nxl != 0) continue;
       Profiler *prof = (h && h->prof.on && !capturing) ? &h->prof : nullptr;
       if (c == 0) {
-        int r = tc_prepare_l(s, A, p->q, tcs, pl.nxc, st, prof, first_in_call);
+        int r = tc_prepare_l(s, A, p->q, tcs, pl.nxl, st, prof, first_in_call);
         if (r) return fail(h, r, "tensor-core operand split failed: %s", tc_last_error());
       }
-      int r = tc_separable_chunk(s, p->qt, om, p->x_w, x0, nxc, pl.nxc, (double *)M, G, c > 0, tcs,
-                                 h ? h->wait_cycles : TC_DEFAULT_WAIT_CYCLES, num_sms, pl.variant,
-                                 h ? h->opt_split_k : 0, st, prof);
-      if (r) return fail(h, r, "tensor-core chunk failed: %s", tc_last_error());
+      const int nl = (p->n_x - x0) < pl.nxl ? (p->n_x - x0) : pl.nxl;
+      const long long wc = h ? h->wait_cycles : TC_DEFAULT_WAIT_CYCLES;
+      if (int r = tc_contract_l(s, p->qt, x0, nl, pl.nxl, (double *)M, tcs, wc, st, prof))
+        return fail(h, r, "tensor-core l contraction failed: %s", tc_last_error());
+      for (int xs = x0; xs < x0 + nl; xs += pl.nxc) {
+        const int ns = (x0 + nl - xs) < pl.nxc ? (x0 + nl - xs) : pl.nxc;
+        const double *Ms = (const double *)M + (size_t)(xs - x0) * s.n_mu * s.nbl * s.nbp;
+        int r = tc_triple_chunk(s, Ms, om, p->x_w, xs, ns, pl.nxl, G, xs > 0, tcs, wc, num_sms, pl.variant,
+                                h ? h->opt_split_k : 0, st, prof);
+        if (r) return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
+      }
     }
   }
   if (pl.prec == MODAL_PREC_OZAKI_BF16 && nchunks > 0 && !capturing) {

@@ -7,12 +7,13 @@
 //
 //  * every row of A and B is scaled by a power of two 2^e (per K chunk) so
 //    that |x / 2^e| <= 1, then written as five BF16 slices of 7 bits each:
-//    x / 2^e * 2^7 = q0 + q1 2^-7 + q2 2^-14 + ...,  |q0| <= 128, |qs| <= 64;
+//    x / 2^e * 2^7 = q0 + q1 2^-7 + q2 2^-14 + q3 2^-21 + q4 2^-28 (35 bits),
+//    |q0| <= 128, |qs| <= 64 (up to 72 for the last);
 //  * the 15 slice products with s + t <= 4 are issued as tcgen05.mma into
 //    three TMEM accumulators: level 0 (q0 q0'), level 1 (q0 q1' + q1 q0') and
 //    levels 2-4.  With at most 1024 K terms per chunk the level-0 and level-1
-//    partial sums are integers (in units of 1 and 2^-7) below 2^24, hence
-//    exact in the FP32 accumulator whatever the summation order;
+//    partial sums are integers (in units of 1 and 2^-7) of magnitude at most
+//    2^24, hence exact in the FP32 accumulator whatever the summation order;
 //  * at the end of each chunk the epilogue warps read the accumulators
 //    (tcgen05.ld), apply the row and column scales and add the chunk into a
 //    double-FP32 (hi, lo) running sum held in registers, offset by a global
@@ -40,7 +41,7 @@ const char *tc_last_error() { return g_tc_err; }
 
 constexpr int OZ_BETA = 7;        // bits per slice
 constexpr int OZ_SLICES = 5;      // slices per operand
-constexpr int OZ_MAXLEV = 4;      // products with s + t <= 4
+constexpr int OZ_MAXLEV = 4;      // products with s + t <= 4 (15 of the 25)
 constexpr int OZ_KC = 1024;       // K terms per exact chunk
 constexpr int OZ_BM = 128;        // rows per tile (TMEM lanes)
 constexpr int OZ_BN = 128;        // columns per tile
@@ -78,31 +79,60 @@ __device__ __forceinline__ float pow2f(int k) {
   return __int_as_float((k + 127) << 23);
 }
 
-// Five slices of a double-FP32 value y = (h, l) with |y| <= 2^e: BF16 values
-// q_s 2^(-7 s) with q_s = round-to-nearest of the running residual x 2^7.
-__device__ __forceinline__ void split5_f2(float h, float l, int e, __nv_bfloat16 (&out)[OZ_SLICES]) {
-  if (e < -99999) {
-#pragma unroll
-    for (int s = 0; s < OZ_SLICES; ++s) out[s] = __float2bfloat16_rn(0.f);
-    return;
-  }
-  // scale by 2^(7 - e) in two exact steps (the exponent range of y may be wide)
-  const int k = OZ_BETA - e;
-  const float s1 = pow2f(k / 2), s2 = pow2f(k - k / 2);
-  h = (h * s1) * s2;
-  l = (l * s1) * s2;
-  float w = 1.0f;
+// Scale factors 2^(BETA - e) as two exact float factors (the exponent range of
+// the values may exceed one float exponent).  e < -99999 marks an all-zero row.
+struct SplitScale {
+  float s1, s2;
+  bool zero;
+};
+__device__ __forceinline__ SplitScale split_scale(int e) {
+  SplitScale r;
+  r.zero = e < -99999;
+  const int k = r.zero ? 0 : OZ_BETA - e;
+  r.s1 = pow2f(k / 2);
+  r.s2 = pow2f(k - k / 2);
+  return r;
+}
+
+// Slices of a double-FP32 value scaled so that |H + L| <= 2^BETA (BETA = 7,
+// five slices).  Slice s is the running residual rounded to a multiple of
+// 2^(-BETA s) (round to nearest, by adding and removing 1.5 2^(23 - BETA s)),
+// so each slice carries its own weight.  The first three slices come from H
+// alone, with exact residuals; the residual is then at most 2^-15 and takes
+// the low part L in one FP32 addition whose rounding is below 2^-37; the
+// last two slices come from that sum.  Slices s >= 1 are integer multiples
+// of 2^(-BETA s) of magnitude <= 64, except the fourth: <= 64 + |L| 2^21,
+// which stays below 256 for |L| <= 2^-14 -- so every slice is exact in BF16
+// and the levels 0 and 1 never see L.  |H + L - sum of slices| <= 2^-29 +
+// 2^-37 (2^-36 of the scale 2^7).
+__host__ __device__ constexpr float oz_pow2c(int k) {
+  return k >= 0 ? (float)(1ull << k) : 1.0f / (float)(1ull << -k);
+}
+constexpr int OZ_FOLD = 3;  // slice before which L joins the residual
+static_assert(OZ_BETA == 7 && OZ_SLICES == 5, "the bounds of split_hl are stated for 5 slices of 7 bits");
+__device__ __forceinline__ void split_hl(float H, float L, float (&q)[OZ_SLICES]) {
+  float r = H;
 #pragma unroll
   for (int s = 0; s < OZ_SLICES; ++s) {
-    const float q = rintf(h);
-    const float t = h - q;  // exact: |h - q| <= 1/2
-    const float sum = t + l, bb = sum - t;
-    const float err = (t - (sum - bb)) + (l - bb);
-    out[s] = __float2bfloat16_rn(q * w);
-    h = sum * (float)(1 << OZ_BETA);
-    l = err * (float)(1 << OZ_BETA);
-    w *= 1.0f / (float)(1 << OZ_BETA);
+    const float m = 1.5f * oz_pow2c(23 - OZ_BETA * s);
+    if (s == OZ_FOLD) r = __fadd_rn(r, L);
+    q[s] = __fsub_rn(__fadd_rn(r, m), m);
+    if (s + 1 < OZ_SLICES) r = __fsub_rn(r, q[s]);  // exact
   }
+}
+
+__device__ __forceinline__ void split_scaled(float h, float l, const SplitScale &sc,
+                                              __nv_bfloat16 (&out)[OZ_SLICES]) {
+  float q[OZ_SLICES];
+  const float H = sc.zero ? 0.f : (h * sc.s1) * sc.s2;
+  const float L = sc.zero ? 0.f : (l * sc.s1) * sc.s2;
+  split_hl(H, L, q);
+#pragma unroll
+  for (int s = 0; s < OZ_SLICES; ++s) out[s] = __float2bfloat16_rn(q[s]);
+}
+
+__device__ __forceinline__ void split_f2(float h, float l, int e, __nv_bfloat16 (&out)[OZ_SLICES]) {
+  split_scaled(h, l, split_scale(e), out);
 }
 
 // exponent e with |x| <= 2^e for every |x| <= m (1 + 2^-20): room for the
@@ -155,7 +185,7 @@ __global__ void k_split_lrows(int64_t rows, int L, int Kpad, const double *__res
     const float h = __double2float_rn(v);
     const float lo = __double2float_rn(v - (double)h);
     __nv_bfloat16 o[OZ_SLICES];
-    split5_f2(h, lo, e, o);
+    split_f2(h, lo, e, o);
 #pragma unroll
     for (int s = 0; s < OZ_SLICES; ++s) out[s * sstride + r * Kpad + l] = o[s];
   }
@@ -449,8 +479,10 @@ static EncodeTiledFn get_encode() {
   return fn;
 }
 
-// 3-D map over [slices][rows][Kpad] BF16, box (OZ_BK, box_rows, slices), 64-byte swizzle.
+// 3-D map over [slices][rows][Kpad] BF16, box (OZ_BK, box_rows, slices): rows of
+// 64 bytes with the 64-byte swizzle the tcgen05 descriptors expect.
 static int make_slices_map(CUtensorMap *m, const void *base, int64_t rows, int Kpad, int box_rows) {
+  const int bk = OZ_BK;
   EncodeTiledFn enc = get_encode();
   if (!enc) {
     snprintf(g_tc_err, sizeof g_tc_err, "cuTensorMapEncodeTiled unavailable");
@@ -458,10 +490,11 @@ static int make_slices_map(CUtensorMap *m, const void *base, int64_t rows, int K
   }
   cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)OZ_SLICES};
   cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)rows * Kpad * 2};
-  cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, (cuuint32_t)OZ_SLICES};
+  cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, (cuuint32_t)OZ_SLICES};
   cuuint32_t es[3] = {1, 1, 1};
+  const CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_64B;
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     snprintf(g_tc_err, sizeof g_tc_err, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -495,8 +528,8 @@ static LScratch l_scratch(void *scratch, const SepShape &s, int nxc) {
   return r;
 }
 
-size_t tc_scratch_bytes(const SepShape &s, int nxc, int variant) {
-  LScratch r = l_scratch(nullptr, s, nxc);
+size_t tc_scratch_bytes(const SepShape &s, int nxl, int nxc, int variant) {
+  LScratch r = l_scratch(nullptr, s, nxl);
   return (size_t)(r.end - (char *)nullptr) + tc_triple_scratch_bytes(s, nxc, variant) + 1024;
 }
 
@@ -610,13 +643,16 @@ __device__ __forceinline__ f2 df_addv(f2 a, f2 b) {
   return {h, e - (h - s.h)};
 }
 
-__device__ __forceinline__ void split5_df(f2 y, int e, __nv_bfloat16 (&out)[OZ_SLICES]) {
-  split5_f2(y.h, y.l, e, out);
+__device__ __forceinline__ void split_df(f2 y, int e, __nv_bfloat16 (&out)[OZ_SLICES]) {
+  split_f2(y.h, y.l, e, out);
 }
 
-// Per chunk of OZ_KC slices and block of 64 columns: exact max |M| (B-operand
-// exponent), max sqrt(w)|M| (Y bound), double-FP32 copy of M and of w, and the
-// K-major BF16 slices of M.
+// Per chunk of OZ_KC slices and block of 64 columns of M (FP64, [k][col]):
+//  * B operand: exact max |M| -> exponent, K-major BF16 slices of M;
+//  * Y operand: M~ = sqrt(w_k) M in double-FP32 (so Y = M~ M~ + M~ M~ carries
+//    w_k = om_j W_x) and max |M~| for the per-chunk bound of |Y|;
+//  * also wdf[k] = w_k in double-FP32 (used by the shared-memory-Y variant).
+// sqrt(w_k) is formed once per slice of the chunk in shared memory.
 constexpr int TP_COLS = 64;
 __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int nblp, int n_mu, int x0,
                                                       const double *__restrict__ M, const double *__restrict__ om,
@@ -624,6 +660,7 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
                                                       f2 *__restrict__ wdf, double *__restrict__ mxW,
                                                       int *__restrict__ eB, __nv_bfloat16 *__restrict__ Bt,
                                                       int *__restrict__ emaxB, int *__restrict__ err) {
+  __shared__ double sw[OZ_KC];
   __shared__ double red1[4][TP_COLS], red2[4][TP_COLS];
   __shared__ int esh[TP_COLS];
   __shared__ __nv_bfloat16 tile[OZ_SLICES][TP_COLS][32 + 8];
@@ -632,15 +669,22 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
   const int tc = threadIdx.x % TP_COLS, tk = threadIdx.x / TP_COLS;  // 64 cols x 4 k-lanes
   const int col = c0 + tc;
   const int64_t k0 = (int64_t)ch * OZ_KC, k1 = min(K, k0 + OZ_KC);
+  for (int kk = threadIdx.x; kk < OZ_KC; kk += blockDim.x) {
+    const int64_t k = k0 + kk;
+    double w = 0.0;
+    if (k < k1) w = om[k % n_mu] * xw[x0 + k / n_mu];
+    sw[kk] = sqrt(w);
+    if (blockIdx.x == 0 && k < k1) wdf[k] = df_from_d(w);
+  }
+  __syncthreads();
   double m1 = 0.0, m2 = 0.0;
   if (col < nblp) {
     for (int64_t k = k0 + tk; k < k1; k += 4) {
       const double v = M[k * nblp + col];
-      const double w = om[k % n_mu] * xw[x0 + k / n_mu];
+      const double vt = sw[k - k0] * v;
       m1 = fmax(m1, fabs(v));
-      m2 = fmax(m2, sqrt(w) * fabs(v));
-      Mdf[k * nblp + col] = df_from_d(v);
-      if (col == 0) wdf[k] = df_from_d(w);
+      m2 = fmax(m2, fabs(vt));
+      Mdf[k * nblp + col] = df_from_d(vt);
     }
   }
   red1[tk][tc] = m1;
@@ -651,7 +695,7 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
       m1 = fmax(m1, red1[i][tc]);
       m2 = fmax(m2, red2[i][tc]);
     }
-    // Y = w (M M + M M) must stay inside the FP32 range of the double-FP32 form
+    // Y = M~ M~ + M~ M~ must stay inside the FP32 range of the double-FP32 form
     if (!(m1 < 1e37) || !(m2 < 1e18)) {
       atomicOr(err, ERR_RANGE);
       m1 = 0.0;
@@ -661,28 +705,27 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
     esh[tc] = e;
     if (col < nblp) {
       eB[(int64_t)ch * nblp + col] = e;
-      mxW[(int64_t)ch * nblp + col] = m2 * (1.0 + 1e-12);  // room for the rounding of sqrt(w)
+      mxW[(int64_t)ch * nblp + col] = m2 * (1.0 + 1e-12);  // room for the rounding of M~
       if (e > -99999) atomicMax(emaxB, e);
       const int ew = exp_bound(m2 * (1.0 + 1e-12));
-      if (ew > -99999) atomicMax(emaxB + 2, ew);  // words[5]: bound of max sqrt(w)|M|
+      if (ew > -99999) atomicMax(emaxB + 2, ew);  // words[5]: bound of max |M~|
     }
   }
   __syncthreads();
-  const int e = esh[tc];
+  const SplitScale sc = split_scale(esh[tc]);
   const int64_t kpend = min((int64_t)Kpad, k0 + OZ_KC);
   for (int64_t kt = k0; kt < kpend; kt += 32) {
-    // each thread splits 8 k of its column
     for (int i = 0; i < 8; ++i) {
       const int kk = tk * 8 + i;
       const int64_t k = kt + kk;
       const double v = (col < nblp && k < K) ? M[k * nblp + col] : 0.0;
+      const f2 vd = df_from_d(v);
       __nv_bfloat16 o[OZ_SLICES];
-      split5_df(df_from_d(v), e, o);
+      split_scaled(vd.h, vd.l, sc, o);
 #pragma unroll
       for (int s = 0; s < OZ_SLICES; ++s) tile[s][tc][kk] = o[s];
     }
     __syncthreads();
-    // write: per (slice, column) one 64-byte row of 32 k
     for (int idx = threadIdx.x; idx < OZ_SLICES * TP_COLS * 4; idx += 256) {
       const int part = idx & 3, cc = (idx >> 2) % TP_COLS, s = idx / (4 * TP_COLS);
       if (c0 + cc < nblp && kt + part * 8 < Kpad) {
@@ -707,58 +750,125 @@ __device__ __forceinline__ void y_row_decode(int64_t r, int P2, int &b, int &a, 
   pair_decode((int)(loc % P2), u, v);
 }
 
-constexpr int TY_ROWS = 64, TY_K = 64;
-__global__ void __launch_bounds__(256) k_tp_make_y(int64_t rowsY, int64_t K, int Kpad, int nbp, int nblp, int P2,
-                                                   const f2 *__restrict__ Mdf, const f2 *__restrict__ wdf,
-                                                   const double *__restrict__ mxW, int *__restrict__ eY,
-                                                   __nv_bfloat16 *__restrict__ Ysl, int *__restrict__ emaxY) {
-  __shared__ __nv_bfloat16 tile[OZ_SLICES][TY_ROWS][TY_K + 8];
-  const int64_t r0 = (int64_t)blockIdx.x * TY_ROWS;
+// Per-(row, K chunk) exponents of the Y operand, from the bound
+// |Y| <= m_au m_bv + m_av m_bu (FP64, once per row and chunk), and their
+// maximum.  Rows are ordered by the pair (a <= b), then by {u, v}.
+__global__ void __launch_bounds__(256) k_tp_y_exp(int64_t rowsY, int nbp, int nblp, int P2,
+                                                  const double *__restrict__ mxW, int *__restrict__ eY,
+                                                  int *__restrict__ emaxY) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ch = blockIdx.y;
+  int e = -100000;
+  if (r < rowsY) {
+    int a, b, u, v;
+    pair_decode((int)(r / P2), a, b);
+    pair_decode((int)(r % P2), u, v);
+    const double *mw = mxW + (int64_t)ch * nblp;
+    e = exp_bound(mw[a * nbp + u] * mw[b * nbp + v] + mw[a * nbp + v] * mw[b * nbp + u]);
+    eY[(int64_t)ch * rowsY + r] = e;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0 && e > -99999) atomicMax(emaxY, e);
+}
+
+// Y operand.  A block takes one pair a <= b and TY_K slices k (inside one
+// chunk): it stages M~_a. and M~_b. for those k in shared memory as
+// [column][k], and warp w forms the rows (a, b, {u, v}) for u = w and
+// u = 2W - 1 - w, ... (balanced: rows with u <= v).  Lane i holds k = 2i,
+// 2i + 1 of each 64-slice step: per row it forms both values of
+// Y = M~_au M~_bv + M~_av M~_bu in double-FP32 (w_k is folded into M~),
+// splits them with the row's per-chunk exponent and stores one 32-bit word
+// (two BF16) per slice, i.e. 128 contiguous bytes per warp and slice.
+constexpr int TY_K = 128, TY_WARPS = 10, TY_PAD = 2;
+static_assert(OZ_KC % TY_K == 0, "a Y block stays inside one exact chunk");
+__host__ __device__ inline size_t ty_smem_bytes(int nbp) {
+  return (size_t)2 * nbp * (TY_K + TY_PAD) * sizeof(f2) + (size_t)(nbp * (nbp + 1) / 2) * sizeof(float2);
+}
+__global__ void __launch_bounds__(32 * TY_WARPS) k_tp_make_y(int64_t rowsY, int64_t K, int Kpad, int nbp, int nblp,
+                                                         int P2, const f2 *__restrict__ Mdf,
+                                                         const int *__restrict__ eY, __nv_bfloat16 *__restrict__ Ysl) {
+  extern __shared__ __align__(16) unsigned char ty_sm[];
+  f2 *Ms = reinterpret_cast<f2 *>(ty_sm);  // [2 nbp][TY_K + TY_PAD]: columns a*nbp+c, then b*nbp+c
+  // per row of the pair: the scale 2^(BETA - e) as two exact factors (0 for an all-zero row)
+  float2 *Fs = reinterpret_cast<float2 *>(ty_sm + (size_t)2 * nbp * (TY_K + TY_PAD) * sizeof(f2));
+  constexpr int LD = TY_K + TY_PAD;
+  int a, b;
+  pair_decode(blockIdx.x, a, b);
+  const int64_t row0 = (int64_t)blockIdx.x * P2;
   const int64_t kb = (int64_t)blockIdx.y * TY_K;
   const int ch = (int)(kb / OZ_KC);
-  const int tr = threadIdx.x % TY_ROWS, tk = threadIdx.x / TY_ROWS;  // 64 rows x 4 k-lanes
-  const int64_t r = r0 + tr;
-  int b = 0, a = 0, u = 0, v = 0, e = -100000;
-  if (r < rowsY) {
-    y_row_decode(r, P2, b, a, u, v);
-    const double *mw = mxW + (int64_t)ch * nblp;
-    const double bound = mw[a * nbp + u] * mw[b * nbp + v] + mw[a * nbp + v] * mw[b * nbp + u];
-    e = exp_bound(bound);
-    if (tk == 0 && (kb % OZ_KC) == 0) {
-      eY[(int64_t)ch * rowsY + r] = e;
-      if (e > -99999) atomicMax(emaxY, e);
-    }
-  }
-  for (int i = 0; i < TY_K / 4; ++i) {
-    const int kk = tk * (TY_K / 4) + i;
+  const int nc2 = 2 * nbp;
+  for (int idx = threadIdx.x; idx < TY_K * nc2; idx += blockDim.x) {
+    const int cc = idx % nc2, kk = idx / nc2;
     const int64_t k = kb + kk;
-    __nv_bfloat16 o[OZ_SLICES];
-    f2 y = {0.f, 0.f};
-    if (r < rowsY && k < K) {
-      const f2 *Mk = Mdf + k * nblp;
-      const f2 s = df_addv(df_mul(Mk[a * nbp + u], Mk[b * nbp + v]), df_mul(Mk[a * nbp + v], Mk[b * nbp + u]));
-      y = df_mul(wdf[k], s);
-    }
-    split5_df(y, e, o);
-#pragma unroll
-    for (int s = 0; s < OZ_SLICES; ++s) tile[s][tr][kk] = o[s];
+    const int col = cc < nbp ? a * nbp + cc : b * nbp + (cc - nbp);
+    f2 v = {0.f, 0.f};
+    if (k < K) v = Mdf[k * nblp + col];
+    Ms[cc * LD + kk] = v;
+  }
+  for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+    const SplitScale sc = split_scale(eY[(int64_t)ch * rowsY + row0 + i]);
+    Fs[i] = sc.zero ? make_float2(0.f, 0.f) : make_float2(sc.s1, sc.s2);
   }
   __syncthreads();
-  // write 64-row x 64-k tiles: per (slice, row) 128 bytes = 8 x 16 B
-  for (int idx = threadIdx.x; idx < OZ_SLICES * TY_ROWS * 8; idx += 256) {
-    const int part = idx & 7, rr = (idx >> 3) % TY_ROWS, s = idx / (8 * TY_ROWS);
-    const int64_t kk = kb + part * 8;
-    if (r0 + rr < rowsY && kk < Kpad) {
-      const uint4 *src = reinterpret_cast<const uint4 *>(&tile[s][rr][part * 8]);
-      uint4 *dst = reinterpret_cast<uint4 *>(Ysl + ((int64_t)s * rowsY + r0 + rr) * Kpad + kk);
-      *dst = *src;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t sstride = rowsY * (int64_t)Kpad / 2;  // 32-bit words per slice
+  uint32_t *Yw = reinterpret_cast<uint32_t *>(Ysl);
+  for (int ks = 0; ks < TY_K; ks += 64) {
+    if (kb + ks >= Kpad) break;  // Kpad is a multiple of 64
+    const int kl = ks + 2 * lane;
+    const int tend = (int)cdiv(nbp, TY_WARPS) * TY_WARPS;
+    for (int t = warp; t < tend; t += TY_WARPS) {
+      // balanced pairing of u: w, 2W-1-w, 2W+w, ...
+      const int blk = t / TY_WARPS, wi = t % TY_WARPS;
+      const int u = blk * TY_WARPS + ((blk & 1) ? (TY_WARPS - 1 - wi) : wi);
+      if (u >= nbp) continue;
+      const float4 xau = *reinterpret_cast<const float4 *>(&Ms[u * LD + kl]);
+      const float4 xbu = *reinterpret_cast<const float4 *>(&Ms[(nbp + u) * LD + kl]);
+      for (int v = u; v < nbp; ++v) {
+        const float4 xav = *reinterpret_cast<const float4 *>(&Ms[v * LD + kl]);
+        const float4 xbv = *reinterpret_cast<const float4 *>(&Ms[(nbp + v) * LD + kl]);
+        const int uv = v * (v + 1) / 2 + u;
+        const float2 f = Fs[uv];
+        float q0[OZ_SLICES], q1[OZ_SLICES];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          // (h, l) of the four factors at slice kl + h2
+          const float auh = h2 ? xau.z : xau.x, aul = h2 ? xau.w : xau.y;
+          const float buh = h2 ? xbu.z : xbu.x, bul = h2 ? xbu.w : xbu.y;
+          const float avh = h2 ? xav.z : xav.x, avl = h2 ? xav.w : xav.y;
+          const float bvh = h2 ? xbv.z : xbv.x, bvl = h2 ? xbv.w : xbv.y;
+          const float p1 = auh * bvh;
+          float e1 = fmaf(auh, bvh, -p1);
+          e1 = fmaf(auh, bvl, e1);
+          e1 = fmaf(aul, bvh, e1);
+          const float p2 = avh * buh;
+          float e2 = fmaf(avh, buh, -p2);
+          e2 = fmaf(avh, bul, e2);
+          e2 = fmaf(avl, buh, e2);
+          const float hsum = p1 + p2;
+          const float bb = hsum - p1;
+          const float lsum = ((p1 - (hsum - bb)) + (p2 - bb)) + (e1 + e2);
+          const float H = (hsum * f.x) * f.y;
+          const float L = (lsum * f.x) * f.y;
+          if (h2 == 0) split_hl(H, L, q0);
+          else split_hl(H, L, q1);
+        }
+        uint32_t *dst = Yw + (row0 + uv) * (int64_t)(Kpad / 2) + (kb + kl) / 2;
+#pragma unroll
+        for (int sl = 0; sl < OZ_SLICES; ++sl) {
+          const __nv_bfloat162 pr = __floats2bfloat162_rn(q0[sl], q1[sl]);
+          dst[sl * sstride] = *reinterpret_cast<const uint32_t *>(&pr);
+        }
+      }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Fused triple product: the eight producer/epilogue warps form the Y operand
-// (double-FP32 products of M entries, split into five BF16 slices) directly in
+// (double-FP32 products of M entries, split into BF16 slices) directly in
 // the 64-byte-swizzled shared-memory stage that the tensor core reads, so Y
 // never goes through HBM; the B operand (M slices) comes by TMA.
 //   warp 0: TMA for B;  warp 1: TMEM allocation and MMA issue;
@@ -770,8 +880,8 @@ struct FusedParams {
   int Kpad;
   int64_t K;      // valid slices of this launch
   int nchunks, nbp, nblp, P2;
-  const f2 *Mdf;     // [K][nblp]
-  const f2 *wdf;     // [K]
+  const f2 *Mdf;     // [K][nblp]: sqrt(w_k) M in double-FP32
+  const f2 *wdf;     // [K] (unused: the weight is folded into Mdf)
   const double *mxW; // [nchunks][nblp]
   const int *eB;     // [nchunks][nblp]
   const int *emaxB;  // max of eB
@@ -1004,11 +1114,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             f2 y = {0.f, 0.f};
             if (pvalid && kg < P.K) {
               const f2 *Mk = P.Mdf + kg * P.nblp;
-              const f2 sv = df_addv(df_mul(Mk[o_au], Mk[o_bv]), df_mul(Mk[o_av], Mk[o_bu]));
-              y = df_mul(P.wdf[kg], sv);
+              // M~ = sqrt(w) M already carries the slice weight
+              y = df_addv(df_mul(Mk[o_au], Mk[o_bv]), df_mul(Mk[o_av], Mk[o_bu]));
             }
-            if (h2 == 0) split5_f2(y.h, y.l, e_row, o0);
-            else split5_f2(y.h, y.l, e_row, o1);
+            if (h2 == 0) split_f2(y.h, y.l, e_row, o0);
+            else split_f2(y.h, y.l, e_row, o1);
           }
 #pragma unroll
           for (int sl = 0; sl < OZ_SLICES; ++sl)
@@ -1068,11 +1178,10 @@ size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
   return b;
 }
 
-int tc_separable_chunk(const SepShape &s, const double *qt, const double *om, const double *xw, int x0, int nxc,
-                       int nxc_max, double *M, double *G, bool accumulate, void *scratch, long long wait_cycles,
-                       int num_sms, int variant, int split_k, cudaStream_t st, Profiler *prof) {
-  if (int r = tc_contract_l(s, qt, x0, nxc, nxc_max, M, scratch, wait_cycles, st, prof)) return r;
-  LScratch ls = l_scratch(scratch, s, nxc_max);
+int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
+                    int nxl_max, double *G, bool accumulate, void *scratch, long long wait_cycles, int num_sms,
+                    int variant, int split_k, cudaStream_t st, Profiler *prof) {
+  LScratch ls = l_scratch(scratch, s, nxl_max);
   char *w = ls.end;
   int *words = ls.words;
   cudaError_t e;
@@ -1105,8 +1214,15 @@ int tc_separable_chunk(const SepShape &s, const double *qt, const double *om, co
     __nv_bfloat16 *Ysl = (__nv_bfloat16 *)wy;
     {
       ProfScope ps(prof, "tc_make_Y", st);
-      k_tp_make_y<<<dim3((unsigned)cdiv64(rowsY, TY_ROWS), (unsigned)(Kpad / TY_K)), 256, 0, st>>>(
-          rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, wdf, mxW, eY, Ysl, words + 4);
+      k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(rowsY, s.nbp, nblp, P2, mxW,
+                                                                                  eY, words + 4);
+      const size_t smy = ty_smem_bytes(s.nbp);
+      if ((e = cudaFuncSetAttribute(k_tp_make_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) !=
+          cudaSuccess)
+        goto cuda_fail;
+      const int npairs = s.nbl * (s.nbl + 1) / 2;
+      k_tp_make_y<<<dim3((unsigned)npairs, (unsigned)cdiv64(Kpad, TY_K)), 32 * TY_WARPS, smy, st>>>(
+          rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, eY, Ysl);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
     CUtensorMap ta, tb;
@@ -1159,7 +1275,7 @@ int tc_separable_chunk(const SepShape &s, const double *qt, const double *om, co
     int64_t tiles = 0;
     for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(F.g.rows(b), OZ_BM) * cdiv64(F.g.cols(b), OZ_BN);
     // split K when the tiles alone cannot fill two waves of one CTA per SM,
-    // keeping at least 4 chunks of 1024 slices per split
+    // keeping at least 4 exact chunks per split
     int ks = (int)cdiv64(2LL * num_sms, tiles);
     ks = ks < nch / 4 ? ks : nch / 4;
     if (split_k > 0) ks = split_k < nch ? split_k : nch;

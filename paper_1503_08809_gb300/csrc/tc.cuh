@@ -8,7 +8,9 @@ namespace modal {
 // triple-product variants: the Y operand through HBM, or formed in shared memory
 constexpr int TC_TRIPLE_MATERIALISED = 0;
 constexpr int TC_TRIPLE_FUSED = 1;
-size_t tc_scratch_bytes(const SepShape &s, int nxc, int variant);
+// scratch for l-contraction chunks of nxl radial points and triple-product
+// chunks of nxc points (nxc <= nxl)
+size_t tc_scratch_bytes(const SepShape &s, int nxl, int nxc, int variant);
 size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant);
 // default bound of every device-side wait of the tensor-core kernels (SM clocks)
 constexpr long long TC_DEFAULT_WAIT_CYCLES = 4000000000LL;
@@ -18,10 +20,11 @@ int tc_prepare_l(const SepShape &s, const double *A, const double *q, void *scra
 // l contraction of one radial chunk on the tensor cores: M (FP64) [xl][j][a][p].
 int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_max, double *M, void *scratch,
                   long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
-// One radial chunk: M (FP64 scratch for the chunk) and G (+)= triple product.
-int tc_separable_chunk(const SepShape &s, const double *qt, const double *om, const double *xw, int x0, int nxc,
-                       int nxc_max, double *M, double *G, bool accumulate, void *scratch, long long wait_cycles,
-                       int num_sms, int variant, int split_k, cudaStream_t st, Profiler *prof = nullptr);
+// Triple product of one radial chunk [x0, x0 + nxc) whose M (FP64,
+// [xl][j][a][p]) starts at M: G (+)= sum over its slices.
+int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
+                    int nxl_max, double *G, bool accumulate, void *scratch, long long wait_cycles, int num_sms,
+                    int variant, int split_k, cudaStream_t st, Profiler *prof = nullptr);
 // device status word of the tensor-core scratch (bit 0: a bounded wait gave up,
 // bit 1: a value outside the FP32 exponent range of the split operands)
 int *tc_error_word(void *scratch);
