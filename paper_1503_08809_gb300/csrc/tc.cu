@@ -79,6 +79,12 @@ __device__ __forceinline__ float pow2f(int k) {
   return __int_as_float((k + 127) << 23);
 }
 
+// 2^k for k <= 127, and 0 below the normal range (a scale that small only
+// multiplies contributions far below the FP32 resolution of the result).
+__device__ __forceinline__ float pow2f_or0(int k) {
+  return k < -126 ? 0.f : __int_as_float((min(k, 127) + 127) << 23);
+}
+
 // Scale factors 2^(BETA - e) as two exact float factors (the exponent range of
 // the values may exceed one float exponent).  e < -99999 marks an all-zero row.
 struct SplitScale {
@@ -242,6 +248,14 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float bh, float bl)
   lo = e - (hi - s);
 }
 
+// Width of the column tiles of a G block with `cols` columns: the block is cut
+// into ceil(cols / 128) tiles of equal width, rounded up to a multiple of 16
+// (the MMA N granularity), so narrow blocks do not pay for 128 columns.
+__host__ __device__ inline int g_tile_width(int64_t cols) {
+  const int64_t nct = cdiv64(cols, OZ_BN);
+  return (int)(cdiv64(cdiv64(cols, nct), 16) * 16);
+}
+
 template <int OUT_MODE>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams P) {
@@ -262,6 +276,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   int64_t a_row0, b_row0, R, C;  // operand row origins, valid rows/cols of this tile
   int64_t out_base = 0;
   int bblk = 0;
+  int ntile = OZ_BN;  // MMA N of this tile (a multiple of 16)
   if (OUT_MODE == 0) {
     a_row0 = (int64_t)blockIdx.x * OZ_BM;
     b_row0 = (int64_t)blockIdx.y * OZ_BN;
@@ -281,11 +296,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       rowoff += P.g.rows(bblk);
     }
     if (bblk >= P.g.nbl) return;
+    // the block's columns go to its column tiles in equal widths (multiples of 16)
+    ntile = g_tile_width(P.g.cols(bblk));
     a_row0 = rowoff + (int64_t)rt * OZ_BM;
-    b_row0 = (int64_t)bblk * P.g.nbp + (int64_t)ct * OZ_BN;
+    b_row0 = (int64_t)bblk * P.g.nbp + (int64_t)ct * ntile;
     R = min((int64_t)OZ_BM, P.g.rows(bblk) - (int64_t)rt * OZ_BM);
-    C = min((int64_t)OZ_BN, P.g.cols(bblk) - (int64_t)ct * OZ_BN);
-    out_base = P.g.offset(bblk) + (int64_t)rt * OZ_BM * P.g.cols(bblk) + (int64_t)ct * OZ_BN;
+    C = min((int64_t)ntile, P.g.cols(bblk) - (int64_t)ct * ntile);
+    out_base = P.g.offset(bblk) + (int64_t)rt * OZ_BM * P.g.cols(bblk) + (int64_t)ct * ntile;
   }
 
   if (threadIdx.x == 0) {
@@ -337,7 +354,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   } else if (warp == 1) {
     // ================= MMA issuer =================
     if (lane == 0) {
-      constexpr uint32_t idesc = ptx::idesc_bf16_f32(OZ_BM, OZ_BN);
+      const uint32_t idesc = ptx::idesc_bf16_f32(OZ_BM, ntile);
       const uint32_t sbase = ptx::smem_u32(sm);
       int chunk = 0;
       for (int i = 0; i < ksteps; ++i) {
@@ -390,7 +407,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int chalf = ew >> 2;               // column half
     const int row = quarter * 32 + lane;     // tile row of this thread
     const int col0 = chalf * 64;
-    const int ebias = (*P.emaxA) + (*P.emaxB) + 40;
+    const int emA = *P.emaxA, emB = *P.emaxB;
+    const int ebias = emA + emB + 40;
     float hi[64];  // high halves in registers, low halves in lo_s
 #pragma unroll
     for (int c = 0; c < 64; ++c) {
@@ -399,12 +417,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     bool ok = true;
     for (int ch = 0; ch < P.nchunks; ++ch) {
-      if (!ptx::mbar_wait(acc_full, (uint32_t)(ch & 1), abort_flag, P.wait_cycles)) { ok = false; break; }
+      // the whole warp goes on or gives up together (shuffles below)
+      const bool got = ptx::mbar_wait(acc_full, (uint32_t)(ch & 1), abort_flag, P.wait_cycles);
+      if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
       ptx::tc_fence_after();
+      // the chunk's scale 2^(ea + eb - 2 BETA - ebias) = row factor x column factor;
+      // lane i holds the column factors of columns col0 + i and col0 + 32 + i
       const int ea = (a_row0 + row < P.rowsA) ? P.eA[(int64_t)ch * P.rowsA + a_row0 + row] : -100000;
+      const float fa = pow2f_or0(ea - emA);
+      float fbl[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t bcol = b_row0 + col0 + h * 32 + lane;
+        const int eb = (bcol < P.rowsB) ? __ldg(P.eB + (int64_t)ch * P.rowsB + bcol) : -100000;
+        fbl[h] = pow2f_or0(eb - emB - 2 * OZ_BETA - 40);
+      }
       const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
       for (int cb = 0; cb < 16; ++cb) {
+        if (col0 + cb * 4 >= ntile) break;  // columns beyond the MMA width (warp-uniform)
         float v0[4], v1[4], v2[4];
         const uint32_t cc = (uint32_t)(col0 + cb * 4);
         ptx::tmem_ld4(tl + cc, v0);
@@ -414,18 +445,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int c = cb * 4 + k;
-          const int64_t bcol = b_row0 + col0 + c;
-          const int eb = (bcol < P.rowsB) ? __ldg(P.eB + (int64_t)ch * P.rowsB + bcol) : -100000;
-          if (ea < -99999 || eb < -99999) continue;
+          const float f = fa * __shfl_sync(0xffffffffu, fbl[c >> 5], c & 31);
           // exact level-0 and level-1 sums, then the rest
           float s = v0[k] + v1[k];
           float bb = s - v0[k];
           float e = (v0[k] - (s - bb)) + (v1[k] - bb);
           e += v2[k];
-          const int sh = ea + eb - 2 * OZ_BETA - ebias;  // <= -54 by the bias
-          const float f1 = pow2f(sh / 2), f2 = pow2f(sh - sh / 2);
           float lo = lo_s[(col0 + c) * OZ_BM + row];
-          df_add(hi[c], lo, (s * f1) * f2, (e * f1) * f2);
+          df_add(hi[c], lo, s * f, e * f);
           lo_s[(col0 + c) * OZ_BM + row] = lo;
         }
       }
@@ -647,29 +674,34 @@ __device__ __forceinline__ void split_df(f2 y, int e, __nv_bfloat16 (&out)[OZ_SL
   split_f2(y.h, y.l, e, out);
 }
 
-// Per chunk of OZ_KC slices and block of 64 columns of M (FP64, [k][col]):
-//  * B operand: exact max |M| -> exponent, K-major BF16 slices of M;
-//  * Y operand: M~ = sqrt(w_k) M in double-FP32 (so Y = M~ M~ + M~ M~ carries
-//    w_k = om_j W_x) and max |M~| for the per-chunk bound of |Y|;
+// Per chunk of OZ_KC slices and block of 16 columns of M (FP64, [k][col]):
+//  * B operand: max |M| -> exponent, K-major BF16 slices of M;
+//  * Y operand: M~ = sqrt(w_k) M in double-FP32, K-major and zero-padded to
+//    Kpad (so Y = M~ M~ + M~ M~ carries w_k = om_j W_x), and max |M~| for the
+//    per-chunk bound of |Y|;
 //  * also wdf[k] = w_k in double-FP32 (used by the shared-memory-Y variant).
-// sqrt(w_k) is formed once per slice of the chunk in shared memory.
-constexpr int TP_COLS = 64;
-__global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int nblp, int n_mu, int x0,
+// sqrt(w_k) is formed once per slice of the chunk in shared memory.  A block
+// takes 16 columns x one chunk (16 k-lanes); the maxima are taken over
+// FP32-rounded magnitudes, which can only raise the exponent bound.
+constexpr int TP_COLS = 16, TP_KL = 16;
+__global__ void __launch_bounds__(TP_COLS * TP_KL) k_tp_prep_cols(int64_t K, int Kpad, int nblp, int n_mu, int x0,
                                                       const double *__restrict__ M, const double *__restrict__ om,
                                                       const double *__restrict__ xw, f2 *__restrict__ Mdf,
                                                       f2 *__restrict__ wdf, double *__restrict__ mxW,
                                                       int *__restrict__ eB, __nv_bfloat16 *__restrict__ Bt,
                                                       int *__restrict__ emaxB, int *__restrict__ err) {
+  constexpr int NT = TP_COLS * TP_KL;
   __shared__ double sw[OZ_KC];
-  __shared__ double red1[4][TP_COLS], red2[4][TP_COLS];
+  __shared__ float red1[TP_KL][TP_COLS], red2[TP_KL][TP_COLS];
   __shared__ int esh[TP_COLS];
   __shared__ __nv_bfloat16 tile[OZ_SLICES][TP_COLS][32 + 8];
+  __shared__ f2 mtile[TP_COLS][32 + 1];
   const int ch = blockIdx.y;
   const int c0 = blockIdx.x * TP_COLS;
-  const int tc = threadIdx.x % TP_COLS, tk = threadIdx.x / TP_COLS;  // 64 cols x 4 k-lanes
+  const int tc = threadIdx.x % TP_COLS, tk = threadIdx.x / TP_COLS;
   const int col = c0 + tc;
   const int64_t k0 = (int64_t)ch * OZ_KC, k1 = min(K, k0 + OZ_KC);
-  for (int kk = threadIdx.x; kk < OZ_KC; kk += blockDim.x) {
+  for (int kk = threadIdx.x; kk < OZ_KC; kk += NT) {
     const int64_t k = k0 + kk;
     double w = 0.0;
     if (k < k1) w = om[k % n_mu] * xw[x0 + k / n_mu];
@@ -677,37 +709,39 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
     if (blockIdx.x == 0 && k < k1) wdf[k] = df_from_d(w);
   }
   __syncthreads();
-  double m1 = 0.0, m2 = 0.0;
+  float m1 = 0.f, m2 = 0.f;
   if (col < nblp) {
-    for (int64_t k = k0 + tk; k < k1; k += 4) {
+#pragma unroll 4
+    for (int64_t k = k0 + tk; k < k1; k += TP_KL) {
       const double v = M[k * nblp + col];
       const double vt = sw[k - k0] * v;
-      m1 = fmax(m1, fabs(v));
-      m2 = fmax(m2, fabs(vt));
-      Mdf[k * nblp + col] = df_from_d(vt);
+      m1 = fmaxf(m1, fabsf(__double2float_rn(v)));
+      m2 = fmaxf(m2, fabsf(__double2float_rn(vt)));
     }
   }
   red1[tk][tc] = m1;
   red2[tk][tc] = m2;
   __syncthreads();
   if (tk == 0) {
-    for (int i = 1; i < 4; ++i) {
-      m1 = fmax(m1, red1[i][tc]);
-      m2 = fmax(m2, red2[i][tc]);
+    for (int i = 1; i < TP_KL; ++i) {
+      m1 = fmaxf(m1, red1[i][tc]);
+      m2 = fmaxf(m2, red2[i][tc]);
     }
     // Y = M~ M~ + M~ M~ must stay inside the FP32 range of the double-FP32 form
-    if (!(m1 < 1e37) || !(m2 < 1e18)) {
-      atomicOr(err, ERR_RANGE);
-      m1 = 0.0;
-      m2 = 0.0;
+    if (!(m1 < 1e37f) || !(m2 < 1e18f)) {
+      if (col < nblp) atomicOr(err, ERR_RANGE);
+      m1 = 0.f;
+      m2 = 0.f;
     }
-    const int e = exp_bound(m1);
+    const int e = exp_bound((double)m1);
     esh[tc] = e;
     if (col < nblp) {
+      // room for the FP32 rounding of the maximum and for the low part of M~
+      const double mw = (double)m2 * (1.0 + 1.0 / 1048576.0);
       eB[(int64_t)ch * nblp + col] = e;
-      mxW[(int64_t)ch * nblp + col] = m2 * (1.0 + 1e-12);  // room for the rounding of M~
+      mxW[(int64_t)ch * nblp + col] = mw;
       if (e > -99999) atomicMax(emaxB, e);
-      const int ew = exp_bound(m2 * (1.0 + 1e-12));
+      const int ew = exp_bound(mw);
       if (ew > -99999) atomicMax(emaxB + 2, ew);  // words[5]: bound of max |M~|
     }
   }
@@ -715,8 +749,9 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
   const SplitScale sc = split_scale(esh[tc]);
   const int64_t kpend = min((int64_t)Kpad, k0 + OZ_KC);
   for (int64_t kt = k0; kt < kpend; kt += 32) {
-    for (int i = 0; i < 8; ++i) {
-      const int kk = tk * 8 + i;
+#pragma unroll
+    for (int i = 0; i < 32 / TP_KL; ++i) {
+      const int kk = tk * (32 / TP_KL) + i;
       const int64_t k = kt + kk;
       const double v = (col < nblp && k < K) ? M[k * nblp + col] : 0.0;
       const f2 vd = df_from_d(v);
@@ -724,9 +759,15 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
       split_scaled(vd.h, vd.l, sc, o);
 #pragma unroll
       for (int s = 0; s < OZ_SLICES; ++s) tile[s][tc][kk] = o[s];
+      mtile[tc][kk] = df_from_d((k < K ? sw[k - k0] : 0.0) * v);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < OZ_SLICES * TP_COLS * 4; idx += 256) {
+    // M~ = sqrt(w) M, K-major ([column][Kpad]), zero beyond K
+    for (int idx = threadIdx.x; idx < TP_COLS * 32; idx += NT) {
+      const int kk = idx & 31, cc = idx >> 5;
+      if (c0 + cc < nblp && kt + kk < Kpad) Mdf[(int64_t)(c0 + cc) * Kpad + kt + kk] = mtile[cc][kk];
+    }
+    for (int idx = threadIdx.x; idx < OZ_SLICES * TP_COLS * 4; idx += NT) {
       const int part = idx & 3, cc = (idx >> 2) % TP_COLS, s = idx / (4 * TP_COLS);
       if (c0 + cc < nblp && kt + part * 8 < Kpad) {
         const uint4 *src = reinterpret_cast<const uint4 *>(&tile[s][cc][part * 8]);
@@ -740,14 +781,8 @@ __global__ void __launch_bounds__(256) k_tp_prep_cols(int64_t K, int Kpad, int n
 
 // Y rows: global row r -> (b, a, uv) with rows ordered by b, then a, then uv.
 __device__ __forceinline__ void y_row_decode(int64_t r, int P2, int &b, int &a, int &u, int &v) {
-  // rows before block b: P2 * b (b + 1) / 2
-  int bb = (int)((sqrt(8.0 * (double)(r / P2) + 1.0) - 1.0) * 0.5);
-  while ((int64_t)P2 * bb * (bb + 1) / 2 > r) --bb;
-  while ((int64_t)P2 * (bb + 1) * (bb + 2) / 2 <= r) ++bb;
-  const int64_t loc = r - (int64_t)P2 * bb * (bb + 1) / 2;
-  b = bb;
-  a = (int)(loc / P2);
-  pair_decode((int)(loc % P2), u, v);
+  pair_decode((int)(r / P2), a, b);
+  pair_decode((int)(r % P2), u, v);
 }
 
 // Per-(row, K chunk) exponents of the Y operand, from the bound
@@ -761,8 +796,7 @@ __global__ void __launch_bounds__(256) k_tp_y_exp(int64_t rowsY, int nbp, int nb
   int e = -100000;
   if (r < rowsY) {
     int a, b, u, v;
-    pair_decode((int)(r / P2), a, b);
-    pair_decode((int)(r % P2), u, v);
+    y_row_decode(r, P2, b, a, u, v);
     const double *mw = mxW + (int64_t)ch * nblp;
     e = exp_bound(mw[a * nbp + u] * mw[b * nbp + v] + mw[a * nbp + v] * mw[b * nbp + u]);
     eY[(int64_t)ch * rowsY + r] = e;
@@ -772,95 +806,154 @@ __global__ void __launch_bounds__(256) k_tp_y_exp(int64_t rowsY, int nbp, int nb
   if ((threadIdx.x & 31) == 0 && e > -99999) atomicMax(emaxY, e);
 }
 
-// Y operand.  A block takes one pair a <= b and TY_K slices k (inside one
-// chunk): it stages M~_a. and M~_b. for those k in shared memory as
-// [column][k], and warp w forms the rows (a, b, {u, v}) for u = w and
-// u = 2W - 1 - w, ... (balanced: rows with u <= v).  Lane i holds k = 2i,
-// 2i + 1 of each 64-slice step: per row it forms both values of
-// Y = M~_au M~_bv + M~_av M~_bu in double-FP32 (w_k is folded into M~),
-// splits them with the row's per-chunk exponent and stores one 32-bit word
-// (two BF16) per slice, i.e. 128 contiguous bytes per warp and slice.
-constexpr int TY_K = 128, TY_WARPS = 10, TY_PAD = 2;
+// Y operand.  A block takes one pair a <= b and TY_K = 128 slices k (inside
+// one chunk): it stages M~_a. and M~_b. for those k in shared memory, and
+// warp w forms the rows (a, b, {u, v}) for u = w and u = 2W - 1 - w, ...
+// (balanced: rows with u <= v).  Lane i holds k = 4i .. 4i + 3: per row it
+// forms four values of Y = M~_au M~_bv + M~_av M~_bu in double-FP32 (w_k is
+// folded into M~), splits them with the row's per-chunk scale and stores
+// 8 bytes (four BF16) per slice: 256 contiguous bytes per warp and slice.
+// The arithmetic runs on pairs of slices with the packed FP32x2 operations
+// of sm_100+ (each component rounds exactly as its scalar counterpart).
+// Shared layout per column: [k % 4 >= 2][k / 4][h, h', l, l'] (h, l of two
+// consecutive k), so each 16-byte load of a lane is conflict-free and gives
+// the high and low parts as register pairs.
+constexpr int TY_K = 128, TY_WARPS = 10;
+constexpr int TY_LD = 2 * TY_K + 4;  // floats per staged column (+ pad)
 static_assert(OZ_KC % TY_K == 0, "a Y block stays inside one exact chunk");
 __host__ __device__ inline size_t ty_smem_bytes(int nbp) {
-  return (size_t)2 * nbp * (TY_K + TY_PAD) * sizeof(f2) + (size_t)(nbp * (nbp + 1) / 2) * sizeof(float2);
+  return (size_t)2 * nbp * TY_LD * sizeof(float) + (size_t)(nbp * (nbp + 1) / 2) * sizeof(float2);
 }
+
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, f2neg(b)); }
+
+// double-FP32 values of M~_au M~_bv + M~_av M~_bu for two slices (high parts
+// and unnormalised low parts)
+__device__ __forceinline__ void y_value2(float2 auh, float2 aul, float2 bvh, float2 bvl, float2 avh, float2 avl,
+                                         float2 buh, float2 bul, float2 &hsum, float2 &lsum) {
+  const float2 p1 = __fmul2_rn(auh, bvh);
+  float2 e1 = __ffma2_rn(auh, bvh, f2neg(p1));
+  e1 = __ffma2_rn(auh, bvl, e1);
+  e1 = __ffma2_rn(aul, bvh, e1);
+  const float2 p2 = __fmul2_rn(avh, buh);
+  float2 e2 = __ffma2_rn(avh, buh, f2neg(p2));
+  e2 = __ffma2_rn(avh, bul, e2);
+  e2 = __ffma2_rn(avl, buh, e2);
+  hsum = __fadd2_rn(p1, p2);
+  const float2 bb = f2sub(hsum, p1);
+  const float2 t = __fadd2_rn(f2sub(p1, f2sub(hsum, bb)), f2sub(p2, bb));
+  lsum = __fadd2_rn(t, __fadd2_rn(e1, e2));
+}
+
+// split_hl for two values at once
+__device__ __forceinline__ void split_hl2(float2 H, float2 L, float2 (&q)[OZ_SLICES]) {
+  float2 r = H;
+#pragma unroll
+  for (int s = 0; s < OZ_SLICES; ++s) {
+    const float m = 1.5f * oz_pow2c(23 - OZ_BETA * s);
+    const float2 m2 = make_float2(m, m);
+    if (s == OZ_FOLD) r = __fadd2_rn(r, L);
+    q[s] = f2sub(__fadd2_rn(r, m2), m2);
+    if (s + 1 < OZ_SLICES) r = f2sub(r, q[s]);  // exact
+  }
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float2 v) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(v.x, v.y);
+  return *reinterpret_cast<const uint32_t *>(&p);
+}
+
 __global__ void __launch_bounds__(32 * TY_WARPS) k_tp_make_y(int64_t rowsY, int64_t K, int Kpad, int nbp, int nblp,
                                                          int P2, const f2 *__restrict__ Mdf,
                                                          const int *__restrict__ eY, __nv_bfloat16 *__restrict__ Ysl) {
   extern __shared__ __align__(16) unsigned char ty_sm[];
-  f2 *Ms = reinterpret_cast<f2 *>(ty_sm);  // [2 nbp][TY_K + TY_PAD]: columns a*nbp+c, then b*nbp+c
-  // per row of the pair: the scale 2^(BETA - e) as two exact factors (0 for an all-zero row)
-  float2 *Fs = reinterpret_cast<float2 *>(ty_sm + (size_t)2 * nbp * (TY_K + TY_PAD) * sizeof(f2));
-  constexpr int LD = TY_K + TY_PAD;
+  float *Ms = reinterpret_cast<float *>(ty_sm);  // [2 nbp][TY_LD]: columns a*nbp+c, then b*nbp+c
+  // per row of the pair: the scale 2^(BETA - e) as (2^k, 1) when it is a
+  // normal float, else as two exact factors; (0, 0) for an all-zero row
+  float2 *Fs = reinterpret_cast<float2 *>(ty_sm + (size_t)2 * nbp * TY_LD * sizeof(float));
   int a, b;
   pair_decode(blockIdx.x, a, b);
   const int64_t row0 = (int64_t)blockIdx.x * P2;
   const int64_t kb = (int64_t)blockIdx.y * TY_K;
   const int ch = (int)(kb / OZ_KC);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  (void)K;
+  (void)nblp;
   const int nc2 = 2 * nbp;
-  for (int idx = threadIdx.x; idx < TY_K * nc2; idx += blockDim.x) {
-    const int cc = idx % nc2, kk = idx / nc2;
-    const int64_t k = kb + kk;
+  // staging: thread (column cc, lane group g) moves the four slices 4g .. 4g + 3
+  // (M~ is K-major and zero beyond K up to Kpad)
+  for (int idx = threadIdx.x; idx < nc2 * 32; idx += blockDim.x) {
+    const int g = idx & 31, cc = idx >> 5;
     const int col = cc < nbp ? a * nbp + cc : b * nbp + (cc - nbp);
-    f2 v = {0.f, 0.f};
-    if (k < K) v = Mdf[k * nblp + col];
-    Ms[cc * LD + kk] = v;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (kb + 4 * g < Kpad) {
+      const float4 *src = reinterpret_cast<const float4 *>(Mdf + (int64_t)col * Kpad + kb + 4 * g);
+      lo = src[0];  // (h0, l0, h1, l1)
+      hi = src[1];  // (h2, l2, h3, l3)
+    }
+    *reinterpret_cast<float4 *>(&Ms[cc * TY_LD + 4 * g]) = make_float4(lo.x, lo.z, lo.y, lo.w);
+    *reinterpret_cast<float4 *>(&Ms[cc * TY_LD + TY_K + 4 * g]) = make_float4(hi.x, hi.z, hi.y, hi.w);
   }
   for (int i = threadIdx.x; i < P2; i += blockDim.x) {
-    const SplitScale sc = split_scale(eY[(int64_t)ch * rowsY + row0 + i]);
-    Fs[i] = sc.zero ? make_float2(0.f, 0.f) : make_float2(sc.s1, sc.s2);
+    const int e = eY[(int64_t)ch * rowsY + row0 + i];
+    const int k = OZ_BETA - e;
+    float2 f;
+    if (e < -99999) f = make_float2(0.f, 0.f);
+    else if (k >= -126 && k <= 127) f = make_float2(pow2f(k), 1.f);
+    else f = make_float2(pow2f(k / 2), pow2f(k - k / 2));
+    Fs[i] = f;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t sstride = rowsY * (int64_t)Kpad / 2;  // 32-bit words per slice
-  uint32_t *Yw = reinterpret_cast<uint32_t *>(Ysl);
-  for (int ks = 0; ks < TY_K; ks += 64) {
-    if (kb + ks >= Kpad) break;  // Kpad is a multiple of 64
-    const int kl = ks + 2 * lane;
-    const int tend = (int)cdiv(nbp, TY_WARPS) * TY_WARPS;
-    for (int t = warp; t < tend; t += TY_WARPS) {
-      // balanced pairing of u: w, 2W-1-w, 2W+w, ...
-      const int blk = t / TY_WARPS, wi = t % TY_WARPS;
-      const int u = blk * TY_WARPS + ((blk & 1) ? (TY_WARPS - 1 - wi) : wi);
-      if (u >= nbp) continue;
-      const float4 xau = *reinterpret_cast<const float4 *>(&Ms[u * LD + kl]);
-      const float4 xbu = *reinterpret_cast<const float4 *>(&Ms[(nbp + u) * LD + kl]);
-      for (int v = u; v < nbp; ++v) {
-        const float4 xav = *reinterpret_cast<const float4 *>(&Ms[v * LD + kl]);
-        const float4 xbv = *reinterpret_cast<const float4 *>(&Ms[(nbp + v) * LD + kl]);
-        const int uv = v * (v + 1) / 2 + u;
-        const float2 f = Fs[uv];
-        float q0[OZ_SLICES], q1[OZ_SLICES];
+  const bool kvalid = kb + 4 * lane < Kpad;  // Kpad is a multiple of 64, not of 128
+  const int64_t sstride = rowsY * (int64_t)Kpad / 4;  // 8-byte words per slice
+  uint2 *Yq = reinterpret_cast<uint2 *>(Ysl) + (kb + 4 * lane) / 4;
+  const int64_t rstride = Kpad / 4;
+  const int tend = (int)cdiv(nbp, TY_WARPS) * TY_WARPS;
+  const int o0 = 4 * lane, o1 = TY_K + 4 * lane;
+  for (int t = warp; t < tend; t += TY_WARPS) {
+    // balanced pairing of u: w, 2W-1-w, 2W+w, ...
+    const int blk = t / TY_WARPS, wi = t % TY_WARPS;
+    const int u = blk * TY_WARPS + ((blk & 1) ? (TY_WARPS - 1 - wi) : wi);
+    if (u >= nbp) continue;
+    // (h, h', l, l') of slices (k0, k1) and (k2, k3) of the lane
+    const float4 au0 = *reinterpret_cast<const float4 *>(&Ms[u * TY_LD + o0]);
+    const float4 au1 = *reinterpret_cast<const float4 *>(&Ms[u * TY_LD + o1]);
+    const float4 bu0 = *reinterpret_cast<const float4 *>(&Ms[(nbp + u) * TY_LD + o0]);
+    const float4 bu1 = *reinterpret_cast<const float4 *>(&Ms[(nbp + u) * TY_LD + o1]);
+    for (int v = u; v < nbp; ++v) {
+      const float4 av0 = *reinterpret_cast<const float4 *>(&Ms[v * TY_LD + o0]);
+      const float4 av1 = *reinterpret_cast<const float4 *>(&Ms[v * TY_LD + o1]);
+      const float4 bv0 = *reinterpret_cast<const float4 *>(&Ms[(nbp + v) * TY_LD + o0]);
+      const float4 bv1 = *reinterpret_cast<const float4 *>(&Ms[(nbp + v) * TY_LD + o1]);
+      const int uv = v * (v + 1) / 2 + u;
+      const float2 f = Fs[uv];
+      float2 h01, l01, h23, l23;
+      y_value2(make_float2(au0.x, au0.y), make_float2(au0.z, au0.w), make_float2(bv0.x, bv0.y),
+               make_float2(bv0.z, bv0.w), make_float2(av0.x, av0.y), make_float2(av0.z, av0.w),
+               make_float2(bu0.x, bu0.y), make_float2(bu0.z, bu0.w), h01, l01);
+      y_value2(make_float2(au1.x, au1.y), make_float2(au1.z, au1.w), make_float2(bv1.x, bv1.y),
+               make_float2(bv1.z, bv1.w), make_float2(av1.x, av1.y), make_float2(av1.z, av1.w),
+               make_float2(bu1.x, bu1.y), make_float2(bu1.z, bu1.w), h23, l23);
+      const float2 fx = make_float2(f.x, f.x);
+      h01 = __fmul2_rn(h01, fx);
+      l01 = __fmul2_rn(l01, fx);
+      h23 = __fmul2_rn(h23, fx);
+      l23 = __fmul2_rn(l23, fx);
+      if (f.y != 1.f) {  // second factor (warp-uniform: every lane has the same row)
+        const float2 fy = make_float2(f.y, f.y);
+        h01 = __fmul2_rn(h01, fy);
+        l01 = __fmul2_rn(l01, fy);
+        h23 = __fmul2_rn(h23, fy);
+        l23 = __fmul2_rn(l23, fy);
+      }
+      float2 q01[OZ_SLICES], q23[OZ_SLICES];
+      split_hl2(h01, l01, q01);
+      split_hl2(h23, l23, q23);
+      if (kvalid) {
+        uint2 *dst = Yq + (row0 + uv) * rstride;
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-          // (h, l) of the four factors at slice kl + h2
-          const float auh = h2 ? xau.z : xau.x, aul = h2 ? xau.w : xau.y;
-          const float buh = h2 ? xbu.z : xbu.x, bul = h2 ? xbu.w : xbu.y;
-          const float avh = h2 ? xav.z : xav.x, avl = h2 ? xav.w : xav.y;
-          const float bvh = h2 ? xbv.z : xbv.x, bvl = h2 ? xbv.w : xbv.y;
-          const float p1 = auh * bvh;
-          float e1 = fmaf(auh, bvh, -p1);
-          e1 = fmaf(auh, bvl, e1);
-          e1 = fmaf(aul, bvh, e1);
-          const float p2 = avh * buh;
-          float e2 = fmaf(avh, buh, -p2);
-          e2 = fmaf(avh, bul, e2);
-          e2 = fmaf(avl, buh, e2);
-          const float hsum = p1 + p2;
-          const float bb = hsum - p1;
-          const float lsum = ((p1 - (hsum - bb)) + (p2 - bb)) + (e1 + e2);
-          const float H = (hsum * f.x) * f.y;
-          const float L = (lsum * f.x) * f.y;
-          if (h2 == 0) split_hl(H, L, q0);
-          else split_hl(H, L, q1);
-        }
-        uint32_t *dst = Yw + (row0 + uv) * (int64_t)(Kpad / 2) + (kb + kl) / 2;
-#pragma unroll
-        for (int sl = 0; sl < OZ_SLICES; ++sl) {
-          const __nv_bfloat162 pr = __floats2bfloat162_rn(q0[sl], q1[sl]);
-          dst[sl * sstride] = *reinterpret_cast<const uint32_t *>(&pr);
-        }
+        for (int sl = 0; sl < OZ_SLICES; ++sl) dst[sl * sstride] = make_uint2(bf16x2_bits(q01[sl]), bf16x2_bits(q23[sl]));
       }
     }
   }
@@ -880,7 +973,7 @@ struct FusedParams {
   int Kpad;
   int64_t K;      // valid slices of this launch
   int nchunks, nbp, nblp, P2;
-  const f2 *Mdf;     // [K][nblp]: sqrt(w_k) M in double-FP32
+  const f2 *Mdf;     // [nblp][Kpad]: sqrt(w_k) M in double-FP32, K-major
   const f2 *wdf;     // [K] (unused: the weight is folded into Mdf)
   const double *mxW; // [nchunks][nblp]
   const int *eB;     // [nchunks][nblp]
@@ -1113,9 +1206,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const int64_t kg = (int64_t)i * OZ_BK + khalf * 16 + g * 8 + kk + h2;
             f2 y = {0.f, 0.f};
             if (pvalid && kg < P.K) {
-              const f2 *Mk = P.Mdf + kg * P.nblp;
+              const f2 *Mk = P.Mdf + kg;  // K-major: column o at Mk[o * Kpad]
+              const int64_t ld = P.Kpad;
               // M~ = sqrt(w) M already carries the slice weight
-              y = df_addv(df_mul(Mk[o_au], Mk[o_bv]), df_mul(Mk[o_av], Mk[o_bu]));
+              y = df_addv(df_mul(Mk[o_au * ld], Mk[o_bv * ld]), df_mul(Mk[o_av * ld], Mk[o_bu * ld]));
             }
             if (h2 == 0) split_f2(y.h, y.l, e_row, o0);
             else split_f2(y.h, y.l, e_row, o1);
@@ -1167,7 +1261,7 @@ size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
   const int64_t nblp = (int64_t)s.nbl * s.nbp;
   const int nch = (int)cdiv64(K, OZ_KC);
   size_t b = 0;
-  b += up256((size_t)K * nblp * 8) + up256((size_t)K * 8);            // Mdf, wdf
+  b += up256((size_t)Kpad * nblp * 8) + up256((size_t)K * 8);         // Mdf, wdf
   b += up256((size_t)nch * nblp * 8) + up256((size_t)nch * nblp * 4);  // mxW, eB
   b += up256((size_t)OZ_SLICES * nblp * Kpad * 2);                     // Bt
   if (variant == TC_TRIPLE_MATERIALISED) {
@@ -1190,7 +1284,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
   const int nblp = s.nbl * s.nbp;
   const int nch = (int)cdiv64(K, OZ_KC);
   const int P2 = s.nbp * (s.nbp + 1) / 2;
-  f2 *Mdf = (f2 *)w; w += up256((size_t)K * nblp * 8);
+  f2 *Mdf = (f2 *)w; w += up256((size_t)Kpad * nblp * 8);
   f2 *wdf = (f2 *)w; w += up256((size_t)K * 8);
   double *mxW = (double *)w; w += up256((size_t)nch * nblp * 8);
   int *eB = (int *)w; w += up256((size_t)nch * nblp * 4);
@@ -1201,7 +1295,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
   }
   {
     ProfScope ps(prof, "tc_prep_M", st);
-    k_tp_prep_cols<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)nch), 256, 0, st>>>(
+    k_tp_prep_cols<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)nch), TP_COLS * TP_KL, 0, st>>>(
         K, Kpad, nblp, s.n_mu, x0, M, om, xw, Mdf, wdf, mxW, eB, Bt, words + 3, words);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
