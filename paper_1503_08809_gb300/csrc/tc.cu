@@ -47,6 +47,7 @@ constexpr int OZ_BM = 128;        // rows per tile (TMEM lanes)
 constexpr int OZ_BN = 128;        // columns per tile
 constexpr int OZ_BK = 32;         // K per stage: 64-byte rows, 64-byte swizzle
 constexpr int OZ_STAGES = 2;
+constexpr int OZ_PREFETCH = 4;    // stages of A prefetched into L2 ahead of their loads
 constexpr int OZ_ROWB = OZ_BK * 2;                       // bytes per smem row
 constexpr int OZ_A_BYTES = OZ_SLICES * OZ_BM * OZ_ROWB;  // 40 KB
 constexpr int OZ_B_BYTES = OZ_SLICES * OZ_BN * OZ_ROWB;  // 40 KB
@@ -223,7 +224,12 @@ __global__ void k_init_words(int *w, int mode) {
 // OUT_MODE 1: triple product, add into the G block of b (rows (a,{u,v}),
 //             columns (c,t), c >= b) -- tiles decoded from blockIdx.x.
 // ---------------------------------------------------------------------------
+// MMA schedule of one 16-deep K step for a tile of width w (see mma_plans):
+// plan[0] = number of runs | accumulators used << 8; plan[1 + r] = run r as
+// sa | first sb << 4 | count << 8 | accumulator << 12 | first-touch << 16.
+constexpr int OZ_PLAN_MAX = 11;
 struct OzParams {
+  uint32_t plan[OZ_BN / 16][1 + OZ_PLAN_MAX];  // by w / 16 - 1
   int64_t rowsA, rowsB;   // operand rows (TMA extents)
   int Kpad;               // K extent (multiple of OZ_BK)
   int nchunks;            // K chunks of OZ_KC
@@ -256,9 +262,15 @@ __host__ __device__ inline int g_tile_width(int64_t cols) {
   return (int)(cdiv64(cdiv64(cols, nct), 16) * 16);
 }
 
+// Tensor maps of the B operand with boxes of 16, 32, ..., 128 rows: a tile of
+// MMA width N loads only its N rows of B (slices then lie N * 64 bytes apart).
+struct BMaps {
+  CUtensorMap m[OZ_BN / 16];
+};
+
 template <int OUT_MODE>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams P) {
+    k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ BMaps bmaps, OzParams P) {
   extern __shared__ unsigned char smraw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   float *lo_s = (float *)(sm + OZ_STAGES * OZ_STAGE_BYTES);  // [col][row]
@@ -278,8 +290,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   int bblk = 0;
   int ntile = OZ_BN;  // MMA N of this tile (a multiple of 16)
   if (OUT_MODE == 0) {
-    a_row0 = (int64_t)blockIdx.x * OZ_BM;
-    b_row0 = (int64_t)blockIdx.y * OZ_BN;
+    // column tiles vary fastest, so the CTAs that share a row tile of A run
+    // together and A is read from HBM about once
+    a_row0 = (int64_t)blockIdx.y * OZ_BM;
+    b_row0 = (int64_t)blockIdx.x * OZ_BN;
     R = min((int64_t)OZ_BM, P.rowsA - a_row0);
     C = min((int64_t)OZ_BN, P.rowsB - b_row0);
   } else {
@@ -326,21 +340,27 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t tmem = *tmem_slot;
   const int ksteps = P.Kpad / OZ_BK;
   const int steps_per_chunk = OZ_KC / OZ_BK;
+  const CUtensorMap *tmB = &bmaps.m[ntile / 16 - 1];
+  const uint32_t stage_bytes = (uint32_t)(OZ_A_BYTES + OZ_SLICES * ntile * OZ_ROWB);
 
   if (warp == 0) {
     // ================= TMA producer =================
     if (lane == 0) {
       ptx::prefetch_tmap(&tmA);
-      ptx::prefetch_tmap(&tmB);
+      ptx::prefetch_tmap(tmB);
       int issued = 0;
+      // A tiles are pulled into L2 OZ_PREFETCH stages ahead of their loads,
+      // so that the two-stage ring waits on L2 rather than on HBM latency
+      for (int i = 0; i < OZ_PREFETCH && i < ksteps; ++i) ptx::tma_prefetch_3d(&tmA, i * OZ_BK, (int)a_row0, 0);
       for (int i = 0; i < ksteps; ++i) {
         const int s = i % OZ_STAGES;
         const uint32_t ph = (uint32_t)((i / OZ_STAGES) & 1);
         if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_cycles)) break;
         unsigned char *st = sm + s * OZ_STAGE_BYTES;
-        ptx::mbar_arrive_expect_tx(&full[s], OZ_STAGE_BYTES);
+        ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
         ptx::tma_load_3d(st, &tmA, &full[s], i * OZ_BK, (int)a_row0, 0);
-        ptx::tma_load_3d(st + OZ_A_BYTES, &tmB, &full[s], i * OZ_BK, (int)b_row0, 0);
+        ptx::tma_load_3d(st + OZ_A_BYTES, tmB, &full[s], i * OZ_BK, (int)b_row0, 0);
+        if (i + OZ_PREFETCH < ksteps) ptx::tma_prefetch_3d(&tmA, (i + OZ_PREFETCH) * OZ_BK, (int)a_row0, 0);
         ++issued;
       }
       // on abort: wait (bounded) for the copies in flight before anyone frees smem
@@ -354,7 +374,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   } else if (warp == 1) {
     // ================= MMA issuer =================
     if (lane == 0) {
-      const uint32_t idesc = ptx::idesc_bf16_f32(OZ_BM, ntile);
+      const uint32_t idesc0 = ptx::idesc_bf16_f32(OZ_BM, 0);  // N goes in per run
+      const uint32_t *plan = P.plan[ntile / 16 - 1];
+      const int nruns = (int)(plan[0] & 0xffu);
+      uint32_t run[OZ_PLAN_MAX];
+#pragma unroll
+      for (int r = 0; r < OZ_PLAN_MAX; ++r) run[r] = plan[1 + r];
       const uint32_t sbase = ptx::smem_u32(sm);
       int chunk = 0;
       for (int i = 0; i < ksteps; ++i) {
@@ -372,20 +397,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         // start-address field, by compile-time offsets (>> 4)
         const uint64_t ad0 = ptx::smem_desc(a0, 16, 8 * OZ_ROWB, ptx::SW_64B);
         const uint64_t bd0 = ptx::smem_desc(a0 + OZ_A_BYTES, 16, 8 * OZ_ROWB, ptx::SW_64B);
-        bool fresh[3] = {chunk_start, chunk_start, chunk_start};
 #pragma unroll
         for (int kk = 0; kk < OZ_BK / 16; ++kk) {
 #pragma unroll
-          for (int sa = 0; sa < OZ_SLICES; ++sa) {
-#pragma unroll
-            for (int sb = 0; sb < OZ_SLICES; ++sb) {
-              if (sa + sb > OZ_MAXLEV) continue;
-              const int lev = sa + sb < 2 ? sa + sb : 2;
-              const uint64_t ad = ad0 + (uint64_t)((sa * OZ_BM * OZ_ROWB + kk * 32) >> 4);
-              const uint64_t bd = bd0 + (uint64_t)((sb * OZ_BN * OZ_ROWB + kk * 32) >> 4);
-              ptx::mma_bf16(tmem + lev * OZ_BN, ad, bd, idesc, fresh[lev] ? 0u : 1u);
-              fresh[lev] = false;
-            }
+          for (int r = 0; r < OZ_PLAN_MAX; ++r) {
+            if (r >= nruns) break;
+            const uint32_t e = run[r];
+            const uint32_t sa = e & 15u, sb = (e >> 4) & 15u, n = (e >> 8) & 15u, acc = (e >> 12) & 15u;
+            // the first touch of an accumulator in a chunk overwrites it
+            const bool first = chunk_start && kk == 0 && ((e >> 16) & 1u);
+            const uint32_t N = n * (uint32_t)ntile;
+            const uint64_t ad = ad0 + (uint64_t)((sa * OZ_BM * OZ_ROWB + kk * 32) >> 4);
+            const uint64_t bd = bd0 + (uint64_t)((sb * (uint32_t)ntile * OZ_ROWB + kk * 32) >> 4);
+            ptx::mma_bf16(tmem + acc * (uint32_t)ntile, ad, bd, idesc0 | ((N >> 3) << 17), first ? 0u : 1u);
           }
         }
         ptx::mma_commit(&empty[s]);  // stage s may be refilled once these MMAs retire
@@ -409,6 +433,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int col0 = chalf * 64;
     const int emA = *P.emaxA, emB = *P.emaxB;
     const int ebias = emA + emB + 40;
+    const int nacc = (int)((P.plan[ntile / 16 - 1][0] >> 8) & 0xffu);
     float hi[64];  // high halves in registers, low halves in lo_s
 #pragma unroll
     for (int c = 0; c < 64; ++c) {
@@ -436,12 +461,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
       for (int cb = 0; cb < 16; ++cb) {
         if (col0 + cb * 4 >= ntile) break;  // columns beyond the MMA width (warp-uniform)
-        float v0[4], v1[4], v2[4];
+        // accumulators ntile columns apart: level 0, level 1, then levels >= 2
+        float v0[4], v1[4], v2[4], v3[4], v4[4];
         const uint32_t cc = (uint32_t)(col0 + cb * 4);
+        const uint32_t w = (uint32_t)ntile;
         ptx::tmem_ld4(tl + cc, v0);
-        ptx::tmem_ld4(tl + OZ_BN + cc, v1);
-        ptx::tmem_ld4(tl + 2 * OZ_BN + cc, v2);
+        ptx::tmem_ld4(tl + w + cc, v1);
+        ptx::tmem_ld4(tl + 2 * w + cc, v2);
+        ptx::tmem_ld4(tl + 3 * w + cc, v3);
+        if (nacc > 4) ptx::tmem_ld4(tl + 4 * w + cc, v4);
         ptx::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v2[k] += nacc > 4 ? v3[k] + v4[k] : v3[k];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int c = cb * 4 + k;
@@ -530,6 +561,87 @@ static int make_slices_map(CUtensorMap *m, const void *base, int64_t rows, int K
   return MODAL_OK;
 }
 
+// Schedules of the slice products of one 16-deep K step as runs of MMAs.
+// For A slice sa the B slices sb = 0 .. MAXLEV - sa are needed.  B slices lie
+// w rows apart in shared memory, so a run of n consecutive sb is one MMA with
+// N = n w whose result columns fall on n consecutive accumulators spaced w
+// TMEM columns apart.  Accumulator 0 takes level 0 (sa + sb = 0), 1 takes
+// level 1, and 2, 3, ... take levels >= 2 (summed by the drain).  In a chunk
+// the first MMA on an accumulator overwrites it, so a run touches only fresh
+// or only used accumulators.  Of the schedules that fit in 512 columns the
+// search keeps the one of least issue cost, with an MMA (M = 128, K = 16)
+// costed at max(80, N / 2) clocks -- the rate measured for back-to-back MMAs
+// from one thread, flat up to N = 160.
+struct PlanSearch {
+  int w, nacc, R;
+  double best = 1e30;
+  uint32_t best_plan[OZ_PLAN_MAX];
+  int best_n = 0, best_used = 0;
+  uint32_t cur[OZ_PLAN_MAX];
+  void rec(int sa, int sb, unsigned fresh, double cost, int n, int used) {
+    if (cost >= best || n > OZ_PLAN_MAX) return;
+    if (sa == OZ_SLICES) {
+      best = cost;
+      best_n = n;
+      best_used = used;
+      memcpy(best_plan, cur, sizeof cur);
+      return;
+    }
+    const int nb = OZ_MAXLEV - sa + 1;
+    if (sb >= nb) return rec(sa + 1, 0, fresh, cost, n, used);
+    if (n == OZ_PLAN_MAX) return;
+    for (int len = (R < nb - sb ? R : nb - sb); len >= 1; --len) {
+      const int L = sa + sb;
+      const int lo = L < 2 ? L : 2, hi = L < 2 ? L : nacc - len;
+      for (int a0 = lo; a0 <= hi; ++a0) {
+        if (a0 + len > nacc) continue;
+        bool ok = true, allf = true, nonef = true;
+        for (int t = 0; t < len; ++t) {
+          const int a = a0 + t, lv = L + t;
+          if (!((a >= 2 && lv >= 2) || a == lv)) ok = false;
+          const bool f = (fresh >> a) & 1u;
+          allf = allf && f;
+          nonef = nonef && !f;
+        }
+        if (!ok || !(allf || nonef)) continue;
+        const unsigned mask = ((1u << len) - 1u) << a0;
+        const double c = (len * w / 2.0 > 80.0) ? len * w / 2.0 : 80.0;
+        cur[n] = (uint32_t)sa | (uint32_t)sb << 4 | (uint32_t)len << 8 | (uint32_t)a0 << 12 |
+                 (allf ? 1u << 16 : 0u);
+        rec(sa, sb + len, fresh & ~mask, cost + c, n + 1, used > a0 + len ? used : a0 + len);
+      }
+    }
+  }
+};
+
+static void fill_mma_plans(OzParams &P) {
+  static uint32_t plans[OZ_BN / 16][1 + OZ_PLAN_MAX];
+  static bool done = false;
+  if (!done) {
+    for (int i = 0; i < OZ_BN / 16; ++i) {
+      PlanSearch ps;
+      ps.w = 16 * (i + 1);
+      ps.nacc = 512 / ps.w < 15 ? 512 / ps.w : 15;
+      ps.R = 256 / ps.w < OZ_SLICES ? 256 / ps.w : OZ_SLICES;
+      ps.rec(0, 0, (1u << ps.nacc) - 1u, 0.0, 0, 0);
+      memset(plans[i], 0, sizeof plans[i]);
+      plans[i][0] = (uint32_t)ps.best_n | (uint32_t)ps.best_used << 8;
+      for (int r = 0; r < ps.best_n; ++r) plans[i][1 + r] = ps.best_plan[r];
+    }
+    done = true;
+  }
+  memcpy(P.plan, plans, sizeof plans);
+}
+
+// B maps for the widths in `used` (bit i: 16 (i + 1) rows); the others stay zero
+static int make_bmaps(BMaps *bm, const void *base, int64_t rows, int Kpad, unsigned used) {
+  memset(bm, 0, sizeof *bm);
+  for (int i = 0; i < OZ_BN / 16; ++i)
+    if ((used >> i) & 1u)
+      if (int r = make_slices_map(&bm->m[i], base, rows, Kpad, 16 * (i + 1))) return r;
+  return MODAL_OK;
+}
+
 static size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Scratch layout (fixed order, sized for the largest radial chunk):
@@ -602,9 +714,10 @@ int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_
   }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   {
-    CUtensorMap ta, tb;
+    CUtensorMap ta;
+    BMaps tb;
     if (int rr = make_slices_map(&ta, r.As, rowsA, Kpad, OZ_BM)) return rr;
-    if (int rr = make_slices_map(&tb, r.Bs, rowsB, Kpad, OZ_BN)) return rr;
+    if (int rr = make_bmaps(&tb, r.Bs, rowsB, Kpad, 1u << (OZ_BN / 16 - 1))) return rr;
     OzParams P{};
     P.rowsA = rowsA;
     P.rowsB = rowsB;
@@ -620,10 +733,11 @@ int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_
     P.nbl = s.nbl;
     P.nbp = s.nbp;
     P.wait_cycles = wait_cycles;
+    fill_mma_plans(P);
     if ((e = cudaFuncSetAttribute(k_ozaki_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
         cudaSuccess)
       goto cuda_fail;
-    dim3 grid((unsigned)cdiv64(rowsA, OZ_BM), (unsigned)cdiv64(rowsB, OZ_BN));
+    dim3 grid((unsigned)cdiv64(rowsB, OZ_BN), (unsigned)cdiv64(rowsA, OZ_BM));
     ProfScope ps(prof, "tc_gemm_l", st);
     k_ozaki_gemm<0><<<grid, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
@@ -1319,9 +1433,13 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
           rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, eY, Ysl);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
-    CUtensorMap ta, tb;
+    CUtensorMap ta;
+    BMaps tb;
+    const GLayout gl = make_glayout(s.nbl, s.nbp);
+    unsigned used = 0;
+    for (int b = 0; b < s.nbl; ++b) used |= 1u << (g_tile_width(gl.cols(b)) / 16 - 1);
     if (int r = make_slices_map(&ta, Ysl, rowsY, Kpad, OZ_BM)) return r;
-    if (int r = make_slices_map(&tb, Bt, nblp, Kpad, OZ_BN)) return r;
+    if (int r = make_bmaps(&tb, Bt, nblp, Kpad, used)) return r;
     OzParams P{};
     P.rowsA = rowsY;
     P.rowsB = nblp;
@@ -1335,6 +1453,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     P.err = words;
     P.g = make_glayout(s.nbl, s.nbp);
     P.wait_cycles = wait_cycles;
+    fill_mma_plans(P);
     int64_t tiles = 0;
     for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(P.g.rows(b), OZ_BM) * cdiv64(P.g.cols(b), OZ_BN);
     if ((e = cudaFuncSetAttribute(k_ozaki_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
