@@ -36,7 +36,13 @@ METRIC = "Γ_nm (x,μ)-slices/s and % tensor peak vs plain FP64 GPU at stated er
 PREC = {"fp64": 0, "fp32": 1, "ozaki": 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "ozaki": "bf16x(ozaki)+f64"}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (CUDA cores), nominal figure
+FP32_TFLOPS = 73.3           # GB300 FP32 FMA rate measured on this machine with an FMA-chain kernel
 TC_SLICE_PRODUCTS = 15       # BF16 slice products per useful MAC in the tensor-core form
+# DRAM bytes (read + write) per launch of the workload's size, from one ncu
+# capture (profiles/k_ozaki_gemm_triple_planck.md: n_x = 4 gives one launch
+# with the same K as every launch of the 500-point step).  Kept only while
+# the kernels are unchanged since that capture.
+NCU_TRAFFIC = {"tc_gemm_triple": 5.775e9 + 48.6e6, "tc_make_Y": 44.5e6 + 5.242e9}
 
 
 def parse():
@@ -45,7 +51,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", *PREC])
+    ap.add_argument("--precision", default="auto", choices=["auto", *PREC],
+                    help="auto: the tensor-core form (ozaki) for the headline and batched "
+                         "workloads, fp32 for the gradient workload")
     ap.add_argument("--n-x", type=int, default=500, help="radial points (workload: 500)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -57,6 +65,8 @@ def parse():
                     help="tensor-core triple product: 0 = Y through HBM, 1 = Y in shared memory")
     ap.add_argument("--once", action="store_true",
                     help="run one projection and exit (a small case for profiler captures)")
+    ap.add_argument("--fp64-x", type=int, default=20,
+                    help="radial points of the plain-FP64 comparison run (0: skip)")
     return ap.parse_args()
 
 
@@ -209,7 +219,7 @@ def run_ours(args):
     import paper_1503_08809_gb300 as mg
     import synthetic as syn
 
-    prec_name = "fp64" if args.precision == "auto" else args.precision
+    prec_name = "ozaki" if args.precision == "auto" else args.precision
     prec = PREC[prec_name]
     P = syn.planck_size(seed=1 + rank, n_x=args.n_x)
     h = mg.Handle(dev)
@@ -256,39 +266,14 @@ def run_ours(args):
     ms_max = max_over_ranks(ms, ws, dev)
     value = ws * P.slices / (ms_max * 1e-3)
 
-    # ---- roofline of the dominant kernel -----------------------------------
+    # ---- rooflines: the dominant kernel, and every tensor / HBM kernel ------
     peaks, src = measured_peaks()
+    launches_per_step = {k: max(1, v[0] // args.steps) for k, v in prof.items()}
+    rooflines = {k: kernel_roofline(k, prof[k], launches_per_step[k], P, prec_name, peaks, src, args.steps, ms)
+                 for k in prof}
+    rooflines = {k: v for k, v in rooflines.items() if v is not None}
     dom = max(prof, key=lambda k: prof[k][1]) if prof else None
-    roof = None
-    if dom:
-        nl, tot = prof[dom]
-        avg_s = tot / nl * 1e-3
-        g2 = P.nb_prim * (P.nb_prim + 1) // 2
-        gsize = g2 * P.nb_prim * P.n_late          # useful MACs per slice of the triple product
-        chunk_slices = P.slices / max(1, nl // args.steps)
-        if dom.startswith("triple"):
-            flops = 2.0 * gsize * chunk_slices
-        elif dom.startswith("contract"):
-            flops = 2.0 * P.nb_late * P.nb_prim * P.L * chunk_slices
-        elif dom == "tc_gemm_triple":      # issued: every slice product counts
-            flops = TC_SLICE_PRODUCTS * 2.0 * gsize * chunk_slices
-        elif dom == "tc_gemm_l":
-            flops = TC_SLICE_PRODUCTS * 2.0 * P.nb_late * P.nb_prim * P.L * chunk_slices
-        else:
-            flops = float("nan")
-        achieved = flops / avg_s / 1e12
-        if prec_name == "ozaki":
-            peak, unit, bound, note = peaks["bf16_tflops"], "TFLOP/s", "tensor", f"bf16 {src}"
-        else:
-            peak, unit, bound, note = FP64_NOMINAL_TFLOPS, "TFLOP/s", "alu", "fp64 nominal"
-        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "kernel": dom,
-                "peak_source": note, "kernel_ms_avg": avg_s * 1e3,
-                "kernel_share_of_step": tot / (ms * args.steps)}
-        if dom.startswith("tc_gemm"):
-            nprod = TC_SLICE_PRODUCTS
-            roof["flops_counted"] = f"issued tensor flops ({nprod} BF16 slice products per useful MAC)"
-            roof["useful_achieved"] = achieved / nprod
+    roof = rooflines.get(dom)
     gpu_launches = sum(v[0] for v in prof.values())
 
     # ---- end to end through host buffers -----------------------------------
@@ -326,6 +311,10 @@ def run_ours(args):
 
     if rank != 0:
         return
+    # ---- plain FP64 GPU path and the stated error -------------------------
+    fp64 = err = None
+    if args.fp64_x > 0 and prec_name != "fp64":
+        fp64, err = fp64_comparison(P, args.fp64_x, prec, value, dev, h)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         v, t, desc, cores = cpu_baseline(P, args.cpu_seconds)
@@ -340,8 +329,85 @@ def run_ours(args):
                                                             else "Y through HBM"),
                        "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "fp64_gpu": fp64, "error": err, "kernel_rooflines": rooflines,
             "clocks": clk, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
+
+
+def kernel_roofline(name, rec, per_step, P, prec_name, peaks, src, steps, ms):
+    """Achieved algorithmic work per launch / mean launch time against the
+    measured peak of the unit that bounds the kernel (None if not modelled)."""
+    nl, tot = rec
+    avg_s = tot / nl * 1e-3
+    g2 = P.nb_prim * (P.nb_prim + 1) // 2
+    gsize = g2 * P.nb_prim * P.n_late          # useful MACs per slice of the triple product
+    k = P.slices / per_step                     # slices per launch
+    kpad = math.ceil(k / 64) * 64
+    extra = {}
+    if name.startswith("triple_") or name.startswith("contract_l_"):
+        macs = gsize if name.startswith("triple_") else P.nb_late * P.nb_prim * P.L
+        work, unit, bound = 2.0 * macs * k, "TFLOP/s", "alu"
+        peak, note = (FP64_NOMINAL_TFLOPS, "fp64 nominal") if name.endswith("f64") else \
+            (FP32_TFLOPS, "fp32 measured (FMA chain)")
+    elif name in ("tc_gemm_triple", "tc_gemm_l"):
+        macs = gsize if name == "tc_gemm_triple" else P.nb_late * P.nb_prim * P.L
+        work, unit, bound = TC_SLICE_PRODUCTS * 2.0 * macs * k, "TFLOP/s", "tensor"
+        peak, note = peaks["bf16_tflops"], f"bf16 {src}"
+        extra = {"flops_counted": f"issued tensor flops ({TC_SLICE_PRODUCTS} BF16 slice products "
+                                  "per useful MAC)",
+                 "useful_achieved": 2.0 * macs * k / avg_s / 1e12}
+    elif name == "tc_make_Y":
+        rows = g2 * P.nb_late * (P.nb_late + 1) // 2
+        work = 10.0 * rows * kpad + 8.0 * P.nb_late * P.nb_prim * kpad   # Y slices out, M~ in
+        unit, bound, peak, note = "GB/s", "hbm", peaks["hbm_gbs"], f"hbm copy {src}"
+    else:
+        return None
+    scale = 1e9 if bound == "hbm" else 1e12
+    achieved = work / avg_s / scale
+    r = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+         "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name) if P.n_x == 500 else None,
+         "peak_source": note, "kernel_ms_avg": avg_s * 1e3, "launches_per_step": per_step,
+         "kernel_share_of_step": tot / (ms * steps)}
+    r.update(extra)
+    return r
+
+
+def entry_errors(g, ref):
+    """Normwise max|dG| / max|G_ref|, and entrywise relative errors with a
+    floor of 1e-12 max|G_ref| (max and RMS)."""
+    d = np.abs(g - ref)
+    scale = np.abs(ref).max()
+    rel = d / np.maximum(np.abs(ref), 1e-12 * scale)
+    return {"normwise": float(d.max() / scale), "max_rel": float(rel.max()),
+            "rms_rel": float(np.sqrt(np.mean(rel ** 2)))}
+
+
+def fp64_comparison(P, n_x, prec, value, dev, h):
+    """The plain FP64 GPU path on the `n_x` radial points of the workload
+    nearest the last-scattering peak (its time is linear in the slice count),
+    timed once after a warm-up, and the error of the timed precision against
+    it on those inputs."""
+    import torch
+    import paper_1503_08809_gb300 as mg
+    import synthetic as syn
+    idx = np.sort(np.argsort(np.abs(P.x - syn.X_PEAK))[:n_x])  # the radial points nearest the peak
+    Ps = syn.Problem(**{**P.__dict__, "qt": P.qt[idx].copy(), "x": P.x[idx], "n_x": n_x})
+    dp = mg.DeviceProblem.from_host(Ps, device=dev, handle=h)
+    st = torch.cuda.current_stream(dev)
+    ref = mg.project_separable(dp, precision=PREC["fp64"], handle=h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    ref = mg.project_separable(dp, precision=PREC["fp64"], handle=h)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    v64 = Ps.slices / (e0.elapsed_time(e1) * 1e-3)
+    g = mg.project_separable(dp, precision=prec, handle=h)
+    mg.handle_status(handle=h)
+    fp64 = {"value": v64, "unit": "slices/s", "sample": f"{n_x} of {P.n_x} radial points (nearest the peak), "
+            f"all {P.n_mu} GL nodes and {P.n_late}x{P.n_prim} modes", "speedup": value / v64}
+    err = {"vs": "plain FP64 GPU path (itself within 1e-10 of the oracle) on the same sample",
+           **entry_errors(g.cpu().numpy(), ref.cpu().numpy())}
+    return fp64, err
 
 
 def run_once(args):
@@ -349,7 +415,7 @@ def run_once(args):
     import torch
     import paper_1503_08809_gb300 as mg
     import synthetic as syn
-    prec = PREC["fp64" if args.precision == "auto" else args.precision]
+    prec = PREC["ozaki" if args.precision == "auto" else args.precision]
     P = syn.planck_size(n_x=args.n_x)
     mg.set_option(mg.OPT_TC_TRIPLE_FUSED, args.tc_fused)
     g = mg.project_separable(mg.DeviceProblem.from_host(P), precision=prec)
@@ -366,7 +432,10 @@ def run_extra(args):
     import paper_1503_08809_gb300 as mg
     import synthetic as syn
     dev = torch.device("cuda", 0)
-    prec_name = "fp32" if args.precision == "auto" else args.precision
+    # auto: FP32 forward and adjoint for the gradient workload, the
+    # tensor-core form for the batched one
+    prec_name = args.precision if args.precision != "auto" else (
+        "fp32" if args.workload == "grad" else "ozaki")
     prec = PREC[prec_name]
     h = mg.Handle(dev)
     st = torch.cuda.current_stream(dev)

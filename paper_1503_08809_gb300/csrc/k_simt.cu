@@ -312,6 +312,16 @@ int triple_ksplit(const SepShape &s, int nxc, int num_sms) {
   return (int)ks;
 }
 
+// kernels launch_triple launches: the tile kernel, plus the reduction of the
+// K-split partial tables unless one split writes G directly
+int triple_launches(const SepShape &s, int nxc, int ksplit, bool accumulate) {
+  using C = SimtCfg<double>;
+  const int64_t S = (int64_t)nxc * s.n_mu;
+  const int64_t kps = cdiv64(cdiv64(S, ksplit), C::BK) * C::BK;
+  const int nks = (int)cdiv64(S, kps);
+  return (nks == 1 && !accumulate) ? 1 : 2;
+}
+
 template <typename T>
 cudaError_t launch_triple(const SepShape &s, const T *M, const double *om, const double *xw, int x0,
                           int nxc, int ksplit, double *G, double *Gpart, bool accumulate,

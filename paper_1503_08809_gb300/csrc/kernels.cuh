@@ -20,6 +20,7 @@ template <typename T>
 cudaError_t launch_contract_l(const SepShape &s, const double *A, const double *q, const double *qt,
                               int x0, int nxc, T *M, cudaStream_t st);
 // G (+)= sum over the chunk's slices (see GLayout); Gpart = [ksplit][Gsize] scratch
+int triple_launches(const SepShape &s, int nxc, int ksplit, bool accumulate);
 template <typename T>
 cudaError_t launch_triple(const SepShape &s, const T *M, const double *om, const double *xw, int x0,
                           int nxc, int ksplit, double *G, double *Gpart, bool accumulate,

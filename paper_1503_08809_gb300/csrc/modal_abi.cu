@@ -44,6 +44,7 @@ struct modal_handle {
 
 // time the launch(es) of the enclosing block when profiling is on
 #define PROF(h, name, st) ProfScope _prof_scope(((h) && (h)->prof.on) ? &(h)->prof : nullptr, name, st)
+#define PROFN(h, name, st, n) ProfScope _prof_scope(((h) && (h)->prof.on) ? &(h)->prof : nullptr, name, st, n)
 
 static thread_local std::string g_err_nohandle;
 
@@ -424,6 +425,7 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
     CK(launch_legendre_table(s.n_mu, mu, s.l_min, s.l_max, p->w_l, A, st));      // a2
   }
   if (p->n_x == 0) {
+    PROF(h, "zero_G", st);
     CK(launch_zero(G, (size_t)pl.Gsize, st));
   }
   for (int c = 0; c < nchunks; ++c) {
@@ -434,7 +436,7 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
         PROF(h, "contract_l_f64", st);
         CK(launch_contract_l<double>(s, A, p->q, p->qt, x0, nxc, (double *)M, st));         // a4+a5
       }
-      PROF(h, "triple_f64", st);
+      PROFN(h, "triple_f64", st, triple_launches(s, nxc, pl.ksplit, c > 0));
       CK(launch_triple<double>(s, (double *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
                                num_sms, st));                                               // a6
     } else if (pl.prec == MODAL_PREC_FP32) {
@@ -442,7 +444,7 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
         PROF(h, "contract_l_f32", st);
         CK(launch_contract_l<float>(s, A, p->q, p->qt, x0, nxc, (float *)M, st));
       }
-      PROF(h, "triple_f32", st);
+      PROFN(h, "triple_f32", st, triple_launches(s, nxc, pl.ksplit, c > 0));
       CK(launch_triple<float>(s, (float *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
                               num_sms, st));
     } else {

@@ -13,6 +13,7 @@ struct Profiler {
   struct Rec {
     const char *name;
     cudaEvent_t a, b;
+    int kernels;  // kernel launches inside the scope
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -26,9 +27,9 @@ struct Profiler {
     cudaEventCreate(&e);
     return e;
   }
-  void begin(const char *name, cudaStream_t st) {
+  void begin(const char *name, cudaStream_t st, int kernels) {
     if (!on) return;
-    Rec r{name, get(), get()};
+    Rec r{name, get(), get(), kernels};
     cudaEventRecord(r.a, st);
     recs.push_back(r);
   }
@@ -36,7 +37,7 @@ struct Profiler {
     if (!on || recs.empty()) return;
     cudaEventRecord(recs.back().b, st);
   }
-  // name -> (launches, ms)
+  // name -> (kernel launches, ms)
   std::map<std::string, std::pair<long long, double>> drain() {
     std::map<std::string, std::pair<long long, double>> out;
     for (auto &r : recs) {
@@ -44,7 +45,7 @@ struct Profiler {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, r.a, r.b);
       auto &e = out[r.name];
-      e.first += 1;
+      e.first += r.kernels;
       e.second += ms;
       pool.push_back(r.a);
       pool.push_back(r.b);
@@ -61,12 +62,12 @@ struct Profiler {
   }
 };
 
-// RAII scope around one launch
+// RAII scope around `kernels` launches (timed together)
 struct ProfScope {
   Profiler *p;
   cudaStream_t st;
-  ProfScope(Profiler *p_, const char *name, cudaStream_t s) : p(p_), st(s) {
-    if (p) p->begin(name, st);
+  ProfScope(Profiler *p_, const char *name, cudaStream_t s, int kernels = 1) : p(p_), st(s) {
+    if (p) p->begin(name, st, kernels);
   }
   ~ProfScope() {
     if (p) p->end(st);

@@ -681,7 +681,10 @@ int tc_prepare_l(const SepShape &s, const double *A, const double *q, void *scra
   const int nch = cdiv(s.L, OZ_KC);
   const int64_t rowsA = (int64_t)s.n_mu * s.nbl;
   cudaError_t e;
-  k_init_words<<<1, 32, 0, st>>>(r.words, reset_status ? 1 : 2);
+  {
+    ProfScope ps(prof, "tc_init", st);
+    k_init_words<<<1, 32, 0, st>>>(r.words, reset_status ? 1 : 2);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   {
     ProfScope ps(prof, "tc_split_lA", st);
@@ -704,7 +707,10 @@ int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_
   const int nch = cdiv(s.L, OZ_KC);
   const int64_t rowsA = (int64_t)s.n_mu * s.nbl, rowsB = (int64_t)nxc * s.nbp;
   cudaError_t e;
-  k_init_words<<<1, 32, 0, st>>>(r.words, 0);
+  {
+    ProfScope ps(prof, "tc_init", st);
+    k_init_words<<<1, 32, 0, st>>>(r.words, 0);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   {
     ProfScope ps(prof, "tc_split_lB", st);
@@ -1404,6 +1410,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
   int *eB = (int *)w; w += up256((size_t)nch * nblp * 4);
   __nv_bfloat16 *Bt = (__nv_bfloat16 *)w;
   if (!accumulate) {
+    ProfScope ps(prof, "zero_G", st);
     GLayout g = make_glayout(s.nbl, s.nbp);
     if ((e = launch_zero(G, (size_t)g.size(), st)) != cudaSuccess) goto cuda_fail;
   }
@@ -1421,7 +1428,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     wy += up256((size_t)nch * rowsY * 4);
     __nv_bfloat16 *Ysl = (__nv_bfloat16 *)wy;
     {
-      ProfScope ps(prof, "tc_make_Y", st);
+      ProfScope ps(prof, "tc_make_Y", st, 2);  // exponents + slices
       k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(rowsY, s.nbp, nblp, P2, mxW,
                                                                                   eY, words + 4);
       const size_t smy = ty_smem_bytes(s.nbp);
