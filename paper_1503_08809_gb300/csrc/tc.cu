@@ -794,108 +794,122 @@ __device__ __forceinline__ void split_df(f2 y, int e, __nv_bfloat16 (&out)[OZ_SL
   split_f2(y.h, y.l, e, out);
 }
 
-// Per chunk of OZ_KC slices and block of 16 columns of M (FP64, [k][col]):
-//  * B operand: max |M| -> exponent, K-major BF16 slices of M;
-//  * Y operand: M~ = sqrt(w_k) M in double-FP32, K-major and zero-padded to
-//    Kpad (so Y = M~ M~ + M~ M~ carries w_k = om_j W_x), and max |M~| for the
-//    per-chunk bound of |Y|;
-//  * also wdf[k] = w_k in double-FP32 (used by the shared-memory-Y variant).
-// sqrt(w_k) is formed once per slice of the chunk in shared memory.  A block
-// takes 16 columns x one chunk (16 k-lanes); the maxima are taken over
-// FP32-rounded magnitudes, which can only raise the exponent bound.
-constexpr int TP_COLS = 16, TP_KL = 16;
-__global__ void __launch_bounds__(TP_COLS * TP_KL) k_tp_prep_cols(int64_t K, int Kpad, int nblp, int n_mu, int x0,
-                                                      const double *__restrict__ M, const double *__restrict__ om,
-                                                      const double *__restrict__ xw, f2 *__restrict__ Mdf,
-                                                      f2 *__restrict__ wdf, double *__restrict__ mxW,
-                                                      int *__restrict__ eB, __nv_bfloat16 *__restrict__ Bt,
-                                                      int *__restrict__ emaxB, int *__restrict__ err) {
-  constexpr int NT = TP_COLS * TP_KL;
-  __shared__ double sw[OZ_KC];
-  __shared__ float red1[TP_KL][TP_COLS], red2[TP_KL][TP_COLS];
-  __shared__ int esh[TP_COLS];
-  __shared__ __nv_bfloat16 tile[OZ_SLICES][TP_COLS][32 + 8];
-  __shared__ f2 mtile[TP_COLS][32 + 1];
-  const int ch = blockIdx.y;
+// Column statistics of one chunk of M (FP64, [k][col]) for the triple product,
+// in two passes over blocks of 32 columns:
+//  * k_tp_col_max, 128 slices per block: max |M| and max |M~| (M~ = sqrt(w_k) M),
+//    both from FP32-rounded values, combined by atomicMax on their bit patterns
+//    (non-negative floats order like their bits) into colmax[2][nch][nblp];
+//  * k_tp_split_cols, 32 slices per block: the per-(chunk, column) exponents
+//    and bounds, M~ in double-FP32 (K-major, zero up to Kpad) for the Y
+//    operand, and the five BF16 slices of M (K-major) for the B operand.
+// w_k = om_j W_x for slice k = (x - x0) n_mu + j.
+constexpr int TP_COLS = 32;
+__global__ void __launch_bounds__(256) k_tp_col_max(int64_t K, int nblp, int n_mu, int x0,
+                                                    const double *__restrict__ M, const double *__restrict__ om,
+                                                    const double *__restrict__ xw, unsigned *__restrict__ colmax) {
+  __shared__ float sw[128];
+  __shared__ float red[2][8][TP_COLS];
   const int c0 = blockIdx.x * TP_COLS;
-  const int tc = threadIdx.x % TP_COLS, tk = threadIdx.x / TP_COLS;
-  const int col = c0 + tc;
-  const int64_t k0 = (int64_t)ch * OZ_KC, k1 = min(K, k0 + OZ_KC);
-  for (int kk = threadIdx.x; kk < OZ_KC; kk += NT) {
-    const int64_t k = k0 + kk;
-    double w = 0.0;
-    if (k < k1) w = om[k % n_mu] * xw[x0 + k / n_mu];
-    sw[kk] = sqrt(w);
-    if (blockIdx.x == 0 && k < k1) wdf[k] = df_from_d(w);
+  const int64_t k0 = (int64_t)blockIdx.y * 128;
+  const int tc = threadIdx.x & 31, tk = threadIdx.x >> 5;
+  if (threadIdx.x < 128) {
+    const int64_t k = k0 + threadIdx.x;
+    sw[threadIdx.x] = k < K ? sqrtf((float)(om[k % n_mu] * xw[x0 + k / n_mu])) : 0.f;
   }
   __syncthreads();
+  const int col = c0 + tc;
   float m1 = 0.f, m2 = 0.f;
   if (col < nblp) {
 #pragma unroll 4
-    for (int64_t k = k0 + tk; k < k1; k += TP_KL) {
-      const double v = M[k * nblp + col];
-      const double vt = sw[k - k0] * v;
-      m1 = fmaxf(m1, fabsf(__double2float_rn(v)));
-      m2 = fmaxf(m2, fabsf(__double2float_rn(vt)));
+    for (int i = tk; i < 128; i += 8) {
+      const int64_t k = k0 + i;
+      if (k >= K) break;
+      const float v = fabsf(__double2float_rn(M[k * nblp + col]));
+      m1 = fmaxf(m1, v);
+      m2 = fmaxf(m2, sw[i] * v);
     }
   }
-  red1[tk][tc] = m1;
-  red2[tk][tc] = m2;
+  red[0][tk][tc] = m1;
+  red[1][tk][tc] = m2;
   __syncthreads();
-  if (tk == 0) {
-    for (int i = 1; i < TP_KL; ++i) {
-      m1 = fmaxf(m1, red1[i][tc]);
-      m2 = fmaxf(m2, red2[i][tc]);
+  if (tk == 0 && col < nblp) {
+    for (int i = 1; i < 8; ++i) {
+      m1 = fmaxf(m1, red[0][i][tc]);
+      m2 = fmaxf(m2, red[1][i][tc]);
     }
-    // Y = M~ M~ + M~ M~ must stay inside the FP32 range of the double-FP32 form
-    if (!(m1 < 1e37f) || !(m2 < 1e18f)) {
-      if (col < nblp) atomicOr(err, ERR_RANGE);
-      m1 = 0.f;
-      m2 = 0.f;
-    }
-    const int e = exp_bound((double)m1);
-    esh[tc] = e;
-    if (col < nblp) {
-      // room for the FP32 rounding of the maximum and for the low part of M~
-      const double mw = (double)m2 * (1.0 + 1.0 / 1048576.0);
-      eB[(int64_t)ch * nblp + col] = e;
-      mxW[(int64_t)ch * nblp + col] = mw;
-      if (e > -99999) atomicMax(emaxB, e);
-      const int ew = exp_bound(mw);
-      if (ew > -99999) atomicMax(emaxB + 2, ew);  // words[5]: bound of max |M~|
-    }
+    const int ch = (int)(k0 / OZ_KC), nch = (int)((K + OZ_KC - 1) / OZ_KC);
+    // a NaN becomes +inf, which the range check of the next pass rejects
+    atomicMax(colmax + (int64_t)ch * nblp + col, __float_as_uint(m1 == m1 ? m1 : INFINITY));
+    atomicMax(colmax + ((int64_t)nch + ch) * nblp + col, __float_as_uint(m2 == m2 ? m2 : INFINITY));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_tp_split_cols(int64_t K, int Kpad, int nblp, int n_mu, int x0,
+                                                       const double *__restrict__ M, const double *__restrict__ om,
+                                                       const double *__restrict__ xw,
+                                                       const unsigned *__restrict__ colmax, f2 *__restrict__ Mdf,
+                                                       double *__restrict__ mxW, int *__restrict__ eB,
+                                                       __nv_bfloat16 *__restrict__ Bt, int *__restrict__ emaxB,
+                                                       int *__restrict__ err) {
+  __shared__ double sw[32];
+  __shared__ __nv_bfloat16 tile[OZ_SLICES][TP_COLS][32 + 8];
+  __shared__ f2 mtile[TP_COLS][32 + 1];
+  const int c0 = blockIdx.x * TP_COLS;
+  const int64_t k0 = (int64_t)blockIdx.y * 32;
+  const int ch = (int)(k0 / OZ_KC), nch = (int)((K + OZ_KC - 1) / OZ_KC);
+  const int tc = threadIdx.x & 31, tk = threadIdx.x >> 5;  // 32 columns x 8 k-lanes (4 slices each)
+  const int col = c0 + tc;
+  if (threadIdx.x < 32) {
+    const int64_t k = k0 + threadIdx.x;
+    sw[threadIdx.x] = k < K ? sqrt(om[k % n_mu] * xw[x0 + k / n_mu]) : 0.0;
+  }
+  // the column's exponent for this chunk
+  float m1 = 0.f, m2 = 0.f;
+  if (col < nblp) {
+    m1 = __uint_as_float(colmax[(int64_t)ch * nblp + col]);
+    m2 = __uint_as_float(colmax[((int64_t)nch + ch) * nblp + col]);
+  }
+  // Y = M~ M~ + M~ M~ must stay inside the FP32 range of the double-FP32 form
+  const bool bad = !(m1 < 1e37f) || !(m2 < 1e18f);
+  if (bad) m1 = m2 = 0.f;
+  const int e = exp_bound((double)m1);
+  if ((k0 % OZ_KC) == 0 && tk == 0 && col < nblp) {
+    if (bad) atomicOr(err, ERR_RANGE);
+    // room for the FP32 roundings of the maxima (sqrt, product) and the low part of M~
+    const double mw = (double)m2 * (1.0 + 1.0 / 262144.0);
+    eB[(int64_t)ch * nblp + col] = e;
+    mxW[(int64_t)ch * nblp + col] = mw;
+    if (e > -99999) atomicMax(emaxB, e);
+    const int ew = exp_bound(mw);
+    if (ew > -99999) atomicMax(emaxB + 2, ew);  // words[5]: bound of max |M~|
   }
   __syncthreads();
-  const SplitScale sc = split_scale(esh[tc]);
-  const int64_t kpend = min((int64_t)Kpad, k0 + OZ_KC);
-  for (int64_t kt = k0; kt < kpend; kt += 32) {
+  const SplitScale sc = split_scale(e);
 #pragma unroll
-    for (int i = 0; i < 32 / TP_KL; ++i) {
-      const int kk = tk * (32 / TP_KL) + i;
-      const int64_t k = kt + kk;
-      const double v = (col < nblp && k < K) ? M[k * nblp + col] : 0.0;
-      const f2 vd = df_from_d(v);
-      __nv_bfloat16 o[OZ_SLICES];
-      split_scaled(vd.h, vd.l, sc, o);
+  for (int i = 0; i < 4; ++i) {
+    const int kk = tk * 4 + i;
+    const int64_t k = k0 + kk;
+    const double v = (col < nblp && k < K) ? M[k * nblp + col] : 0.0;
+    const f2 vd = df_from_d(v);
+    __nv_bfloat16 o[OZ_SLICES];
+    split_scaled(vd.h, vd.l, sc, o);
 #pragma unroll
-      for (int s = 0; s < OZ_SLICES; ++s) tile[s][tc][kk] = o[s];
-      mtile[tc][kk] = df_from_d((k < K ? sw[k - k0] : 0.0) * v);
+    for (int s = 0; s < OZ_SLICES; ++s) tile[s][tc][kk] = o[s];
+    mtile[tc][kk] = df_from_d(sw[kk] * v);
+  }
+  __syncthreads();
+  // B slices: per (slice, column) 64 contiguous bytes; M~: per column 256 bytes
+  for (int idx = threadIdx.x; idx < OZ_SLICES * TP_COLS * 4; idx += 256) {
+    const int part = idx & 3, cc = (idx >> 2) % TP_COLS, s = idx / (4 * TP_COLS);
+    if (c0 + cc < nblp && k0 + part * 8 < Kpad) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(&tile[s][cc][part * 8]);
+      uint4 *dst = reinterpret_cast<uint4 *>(Bt + ((int64_t)s * nblp + c0 + cc) * Kpad + k0 + part * 8);
+      *dst = *src;
     }
-    __syncthreads();
-    // M~ = sqrt(w) M, K-major ([column][Kpad]), zero beyond K
-    for (int idx = threadIdx.x; idx < TP_COLS * 32; idx += NT) {
-      const int kk = idx & 31, cc = idx >> 5;
-      if (c0 + cc < nblp && kt + kk < Kpad) Mdf[(int64_t)(c0 + cc) * Kpad + kt + kk] = mtile[cc][kk];
-    }
-    for (int idx = threadIdx.x; idx < OZ_SLICES * TP_COLS * 4; idx += NT) {
-      const int part = idx & 3, cc = (idx >> 2) % TP_COLS, s = idx / (4 * TP_COLS);
-      if (c0 + cc < nblp && kt + part * 8 < Kpad) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(&tile[s][cc][part * 8]);
-        uint4 *dst = reinterpret_cast<uint4 *>(Bt + ((int64_t)s * nblp + c0 + cc) * Kpad + kt + part * 8);
-        *dst = *src;
-      }
-    }
-    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < TP_COLS * 32; idx += 256) {
+    const int kk = idx & 31, cc = idx >> 5;
+    if (c0 + cc < nblp && k0 + kk < Kpad) Mdf[(int64_t)(c0 + cc) * Kpad + k0 + kk] = mtile[cc][kk];
   }
 }
 
@@ -1094,7 +1108,6 @@ struct FusedParams {
   int64_t K;      // valid slices of this launch
   int nchunks, nbp, nblp, P2;
   const f2 *Mdf;     // [nblp][Kpad]: sqrt(w_k) M in double-FP32, K-major
-  const f2 *wdf;     // [K] (unused: the weight is folded into Mdf)
   const double *mxW; // [nchunks][nblp]
   const int *eB;     // [nchunks][nblp]
   const int *emaxB;  // max of eB
@@ -1381,7 +1394,7 @@ size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
   const int64_t nblp = (int64_t)s.nbl * s.nbp;
   const int nch = (int)cdiv64(K, OZ_KC);
   size_t b = 0;
-  b += up256((size_t)Kpad * nblp * 8) + up256((size_t)K * 8);         // Mdf, wdf
+  b += up256((size_t)Kpad * nblp * 8) + up256((size_t)nch * nblp * 8); // Mdf, column maxima
   b += up256((size_t)nch * nblp * 8) + up256((size_t)nch * nblp * 4);  // mxW, eB
   b += up256((size_t)OZ_SLICES * nblp * Kpad * 2);                     // Bt
   if (variant == TC_TRIPLE_MATERIALISED) {
@@ -1405,7 +1418,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
   const int nch = (int)cdiv64(K, OZ_KC);
   const int P2 = s.nbp * (s.nbp + 1) / 2;
   f2 *Mdf = (f2 *)w; w += up256((size_t)Kpad * nblp * 8);
-  f2 *wdf = (f2 *)w; w += up256((size_t)K * 8);
+  unsigned *colmax = (unsigned *)w; w += up256((size_t)nch * nblp * 8);
   double *mxW = (double *)w; w += up256((size_t)nch * nblp * 8);
   int *eB = (int *)w; w += up256((size_t)nch * nblp * 4);
   __nv_bfloat16 *Bt = (__nv_bfloat16 *)w;
@@ -1415,9 +1428,12 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     if ((e = launch_zero(G, (size_t)g.size(), st)) != cudaSuccess) goto cuda_fail;
   }
   {
-    ProfScope ps(prof, "tc_prep_M", st);
-    k_tp_prep_cols<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)nch), TP_COLS * TP_KL, 0, st>>>(
-        K, Kpad, nblp, s.n_mu, x0, M, om, xw, Mdf, wdf, mxW, eB, Bt, words + 3, words);
+    ProfScope ps(prof, "tc_prep_M", st, 2);
+    if ((e = cudaMemsetAsync(colmax, 0, (size_t)nch * nblp * 8, st)) != cudaSuccess) goto cuda_fail;
+    k_tp_col_max<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)cdiv64(K, 128)), 256, 0, st>>>(
+        K, nblp, s.n_mu, x0, M, om, xw, colmax);
+    k_tp_split_cols<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)(Kpad / 32)), 256, 0, st>>>(
+        K, Kpad, nblp, s.n_mu, x0, M, om, xw, colmax, Mdf, mxW, eB, Bt, words + 3, words);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   if (variant == TC_TRIPLE_MATERIALISED) {
@@ -1483,7 +1499,6 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     F.nblp = nblp;
     F.P2 = P2;
     F.Mdf = Mdf;
-    F.wdf = wdf;
     F.mxW = mxW;
     F.eB = eB;
     F.emaxB = words + 3;
