@@ -114,9 +114,14 @@ int modal_handle_status(modal_handle *h);
  *   operand of the triple product to device memory and runs a TMA-fed GEMM;
  *   1 forms Y in shared memory inside the GEMM (no Y traffic through HBM).
  *   Both give the same results to rounding.
- * MODAL_OPT_TC_SPLIT_K: K splits of the shared-memory variant (0 = automatic). */
+ * MODAL_OPT_TC_SPLIT_K: K splits of the shared-memory variant (0 = automatic).
+ * MODAL_OPT_BATCH_STREAMS: concurrent streams of modal_project_separable_batched
+ *   (1 .. 8), or 0 (default): the first call for a problem set captures one
+ *   graph each for 1, 2, 4 and 8 streams (as far as their scratch fits),
+ *   replays each twice, keeps the fastest and blocks until that is done. */
 #define MODAL_OPT_TC_TRIPLE_FUSED 1
 #define MODAL_OPT_TC_SPLIT_K 2
+#define MODAL_OPT_BATCH_STREAMS 3
 int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value);
 
 /* Bound (in SM clock cycles) of those device-side waits for later calls on
@@ -206,11 +211,16 @@ int modal_project_backward(modal_handle *h, const modal_problem *prob, const mod
 /* Many independent problems of uneven size in one call (host array `probs`
  * of n problem descriptors, host array `gammas` of n device outputs).  Each
  * result equals modal_project_separable on that problem with these opts.
- * The launches of the whole batch are captured once into a CUDA graph,
- * cached on the handle under the problem set (descriptors, pointers, opts,
- * tunables) and replayed on `stream` by later calls with the same set; the
- * data may change between calls, the pointers and sizes may not.  Scratch
- * growth on the handle drops the cached graphs. */
+ * The problems are spread over S concurrent streams (largest first, each to
+ * the least loaded stream; each stream has its own scratch) so that small
+ * problems fill the GPU side by side, and the launches of the whole batch
+ * are captured once into one CUDA graph, cached on the handle under the
+ * problem set (descriptors, pointers, opts, tunables) and replayed on
+ * `stream` by later calls with the same set; the data may change between
+ * calls, the pointers and sizes may not.  S comes from
+ * MODAL_OPT_BATCH_STREAMS; by default the first call for a set times the
+ * candidates and blocks until done.  Scratch growth on the handle drops the
+ * cached graphs. */
 int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_problem *probs,
                                     const modal_opts *opts, double *const *gammas,
                                     modal_stream_t stream);

@@ -8,7 +8,7 @@ fails loudly if it has not been built.
 """
 from __future__ import annotations
 
-from ._lib import (OPT_TC_SPLIT_K, OPT_TC_TRIPLE_FUSED, ModalError, PREC_FP32, PREC_FP64,
+from ._lib import (OPT_BATCH_STREAMS, OPT_TC_SPLIT_K, OPT_TC_TRIPLE_FUSED, ModalError, PREC_FP32, PREC_FP64,
                    PREC_OZAKI_BF16, W_EXACT_3J, W_SMOOTH_GOSPER, XW_HERMITE, XW_TRAPEZOID, lib,
                    lib_path)
 from .api import (DeviceProblem, Handle, contract_l, default_handle, gl_nodes, handle_status,

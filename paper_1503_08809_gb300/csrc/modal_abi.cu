@@ -2,6 +2,7 @@
 // argument validation and the drivers that chain the kernels of the
 // separable path (rows a1-a7), the direct path (a8), the adjoint (a9) and
 // the batched form (a10).
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,8 @@
 
 using namespace modal;
 
+constexpr int MAX_BATCH_STREAMS = 8;
+
 struct modal_handle {
   int device = 0;
   int num_sms = 0;
@@ -26,18 +29,27 @@ struct modal_handle {
   void *slot_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t slot_bytes[4] = {0, 0, 0, 0};
   int64_t *pinned_i64 = nullptr;  // host-pinned word for the direct path's triple count
-  int *pinned_err = nullptr;      // host-pinned copy of the tensor path's device error word
+  int *pinned_err = nullptr;      // host-pinned copies of the tensor path's device error words
+  int n_err_words = 1;            // how many of them the last call filled
   cudaEvent_t err_event = nullptr;
   bool err_pending = false;
   long long wait_cycles = TC_DEFAULT_WAIT_CYCLES;
   int opt_triple_variant = TC_TRIPLE_MATERIALISED;
   int opt_split_k = 0;
+  int opt_batch_streams = 0;      // 0: chosen by timing on the first call for a problem set
   Profiler prof;
-  // batched calls: graphs of all launches, keyed by the problem set
+  // batched calls: graphs of all launches, keyed by the problem set; the
+  // capture forks onto side streams so that small problems run side by side
   cudaStream_t cap_stream = nullptr;
-  std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
+  cudaStream_t side[MAX_BATCH_STREAMS] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[MAX_BATCH_STREAMS] = {};
+  struct BatchGraph {
+    cudaGraphExec_t exec;
+    int streams;
+  };
+  std::unordered_map<uint64_t, BatchGraph> graphs;
   void clear_graphs() {
-    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second.exec);
     graphs.clear();
   }
 };
@@ -160,13 +172,13 @@ int modal_handle_create(modal_handle **out) {
   modal_handle *h = new modal_handle();
   h->device = dev;
   h->num_sms = prop.multiProcessorCount;
-  e = cudaMallocHost((void **)&h->pinned_i64, 2 * sizeof(int64_t));
+  e = cudaMallocHost((void **)&h->pinned_i64, sizeof(int64_t) + MAX_BATCH_STREAMS * sizeof(int));
   if (e != cudaSuccess) {
     delete h;
     return fail(nullptr, MODAL_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
   }
   h->pinned_err = (int *)(h->pinned_i64 + 1);
-  *h->pinned_err = 0;
+  for (int i = 0; i < MAX_BATCH_STREAMS; ++i) h->pinned_err[i] = 0;
   e = cudaEventCreateWithFlags(&h->err_event, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaFreeHost(h->pinned_i64);
@@ -183,6 +195,11 @@ int modal_handle_destroy(modal_handle *h) {
     if (h->slot_ptr[s]) cudaFree(h->slot_ptr[s]);
   h->clear_graphs();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int i = 0; i < MAX_BATCH_STREAMS; ++i) {
+    if (h->side[i]) cudaStreamDestroy(h->side[i]);
+    if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->err_event) cudaEventDestroy(h->err_event);
   if (h->pinned_i64) cudaFreeHost(h->pinned_i64);
   tc_release(h->device);
@@ -226,8 +243,11 @@ int modal_handle_status(modal_handle *h) {
   cudaError_t e = cudaEventSynchronize(h->err_event);
   if (e != cudaSuccess) return fail(h, MODAL_ECUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
   h->err_pending = false;
-  const int word = *h->pinned_err;
-  *h->pinned_err = 0;
+  int word = 0;
+  for (int i = 0; i < h->n_err_words; ++i) {
+    word |= h->pinned_err[i];
+    h->pinned_err[i] = 0;
+  }
   if (word & 1) return fail(h, MODAL_ETIMEOUT, "a bounded device-side wait of the tensor-core kernels gave up");
   if (word & 2)
     return fail(h, MODAL_EUNSUPPORTED,
@@ -246,6 +266,11 @@ int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value) {
     case MODAL_OPT_TC_SPLIT_K:
       if (value < 0 || value > 4096) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_SPLIT_K out of range");
       h->opt_split_k = (int)value;
+      return MODAL_OK;
+    case MODAL_OPT_BATCH_STREAMS:
+      if (value < 0 || value > MAX_BATCH_STREAMS)
+        return fail(h, MODAL_EINVAL, "MODAL_OPT_BATCH_STREAMS takes 0 .. %d", MAX_BATCH_STREAMS);
+      h->opt_batch_streams = (int)value;
       return MODAL_OK;
     default:
       return fail(h, MODAL_EINVAL, "unknown option %d", option);
@@ -320,6 +345,7 @@ int modal_contract_l(modal_handle *h, const modal_problem *p, int32_t n_mu, cons
   }
   CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(scratch), sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(h->err_event, st));
+  h->n_err_words = 1;
   h->err_pending = true;
   return MODAL_OK;
 }
@@ -473,6 +499,7 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
     // surface a bounded-wait give-up through modal_handle_status (no sync here)
     CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(tcs), sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(h->err_event, st));
+    h->n_err_words = 1;
     h->err_pending = true;
   }
   PROF(h, "gather", st);
@@ -520,6 +547,94 @@ static uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
   return h;
 }
 
+// Work estimate of one problem (for spreading a batch over streams): the
+// triple product's MACs plus the l contraction's, per slice, times slices.
+static double problem_cost(const modal_problem *p, int n_mu) {
+  const GLayout g = make_glayout(p->nb_late, p->nb_prim);
+  const double L = (double)(p->l_max - p->l_min + 1);
+  return ((double)g.size() + L * p->nb_late * p->nb_prim) * (double)p->n_x * (double)n_mu;
+}
+
+// A batch spread over `ns` streams: problems in decreasing cost, each to the
+// least loaded stream (longest processing time first); each stream owns a
+// scratch block of its largest plan.
+struct BatchLayout {
+  int ns;
+  std::vector<int> stream_of;
+  size_t off[MAX_BATCH_STREAMS + 1];
+};
+static BatchLayout batch_layout(int n, const modal_problem *probs, const std::vector<SepPlan> &plans, int ns) {
+  BatchLayout bl;
+  bl.ns = ns;
+  bl.stream_of.assign(n, 0);
+  std::vector<int> order(n);
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) {
+    order[i] = i;
+    cost[i] = problem_cost(&probs[i], plans[i].s.n_mu);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  double load[MAX_BATCH_STREAMS] = {};
+  size_t need[MAX_BATCH_STREAMS] = {};
+  for (int i : order) {
+    int best = 0;
+    for (int k = 1; k < ns; ++k)
+      if (load[k] < load[best]) best = k;
+    bl.stream_of[i] = best;
+    load[best] += cost[i];
+    need[best] = plans[i].bytes > need[best] ? plans[i].bytes : need[best];
+  }
+  bl.off[0] = 0;
+  for (int k = 0; k < ns; ++k) bl.off[k + 1] = bl.off[k] + align256(need[k] ? need[k] : 256);
+  return bl;
+}
+
+// Capture every launch of the batch into one graph, the problems of stream k
+// on side stream k (forked from and joined back into the capture stream).
+static int capture_batch(modal_handle *h, int n, const modal_problem *probs, const std::vector<SepPlan> &plans,
+                         double *const *gammas, const BatchLayout &bl, char *scratch, cudaGraphExec_t *out) {
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+  for (int k = 1; k < bl.ns; ++k) {
+    if (!h->side[k]) CK(cudaStreamCreateWithFlags(&h->side[k], cudaStreamNonBlocking));
+    if (!h->join_ev[k]) CK(cudaEventCreateWithFlags(&h->join_ev[k], cudaEventDisableTiming));
+  }
+  const bool prof_on = h->prof.on;
+  h->prof.on = false;  // no event records inside the capture
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+  int rr = MODAL_OK;
+  cudaError_t ce = cudaSuccess;
+  if (bl.ns > 1) {
+    ce = cudaEventRecord(h->fork_ev, h->cap_stream);
+    for (int k = 1; k < bl.ns && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(h->side[k], h->fork_ev, 0);
+  }
+  bool first[MAX_BATCH_STREAMS];
+  for (int k = 0; k < MAX_BATCH_STREAMS; ++k) first[k] = true;
+  for (int i = 0; i < n && rr == MODAL_OK && ce == cudaSuccess; ++i) {
+    if ((int64_t)probs[i].n_late * probs[i].n_prim == 0) continue;
+    const int k = bl.stream_of[i];
+    cudaStream_t sk = k == 0 ? h->cap_stream : h->side[k];
+    rr = run_separable(h, h->num_sms, &probs[i], plans[i], gammas[i], sk, scratch + bl.off[k], first[k], true);
+    first[k] = false;
+  }
+  for (int k = 1; k < bl.ns && ce == cudaSuccess; ++k) {
+    ce = cudaEventRecord(h->join_ev[k], h->side[k]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->cap_stream, h->join_ev[k], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+  h->prof.on = prof_on;
+  if (rr != MODAL_OK || ce != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (rr != MODAL_OK) return rr;
+    return fail(h, MODAL_ECUDA, "graph capture: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+  }
+  ce = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return fail(h, MODAL_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+  return MODAL_OK;
+}
+
 int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_problem *probs,
                                     const modal_opts *o, double *const *gammas, modal_stream_t stream) {
   if (int r = check_handle(h)) return r;
@@ -528,7 +643,6 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
   if (!probs || !gammas) return fail(h, MODAL_EINVAL, "null probs/gammas");
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<SepPlan> plans(n);
-  size_t need = 0;
   bool any_tc = false;
   for (int i = 0; i < n; ++i) {
     if (int r = validate_problem(h, &probs[i], true, true)) return fail(h, r, "problem %d: %s", i, h->err.c_str());
@@ -536,9 +650,27 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
       return fail(h, r, "problem %d: %s", i, h->err.c_str());
     if ((int64_t)probs[i].n_late * probs[i].n_prim > 0 && !gammas[i])
       return fail(h, MODAL_EINVAL, "null gamma for problem %d", i);
-    need = plans[i].bytes > need ? plans[i].bytes : need;
     any_tc = any_tc || plans[i].prec == MODAL_PREC_OZAKI_BF16;
   }
+  // stream counts to consider: the fixed option, or 1, 2, 4, 8 (at most n)
+  // while their scratch fits in half of the free device memory
+  std::vector<BatchLayout> cands;
+  size_t freeb = 0, totb = 0;
+  if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) freeb = 0;
+  for (int ns = 1; ns <= MAX_BATCH_STREAMS; ns *= 2) {
+    if (h->opt_batch_streams > 0 && ns != h->opt_batch_streams) continue;
+    if (ns > 1 && ns > n) break;
+    BatchLayout bl = batch_layout(n, probs, plans, ns);
+    const size_t cap = freeb / 2 < ((size_t)64 << 30) ? freeb / 2 : ((size_t)64 << 30);
+    if (ns > 1 && h->opt_batch_streams == 0 && bl.off[ns] > h->slot_bytes[0] && bl.off[ns] > cap) break;
+    cands.push_back(bl);
+  }
+  if (h->opt_batch_streams > 0 && cands.empty()) {
+    const int ns = h->opt_batch_streams < n ? h->opt_batch_streams : n;
+    cands.push_back(batch_layout(n, probs, plans, ns));
+  }
+  size_t need = 0;
+  for (auto &bl : cands) need = bl.off[bl.ns] > need ? bl.off[bl.ns] : need;
   void *scratch;
   if (int r = ws_get(h, 0, need, &scratch)) return r;  // before capture: no allocation inside
   uint64_t key = 1469598103934665603ULL;
@@ -549,39 +681,62 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
   key = fnv1a(key, &scratch, sizeof scratch);
   key = fnv1a(key, &h->opt_triple_variant, sizeof(int));
   key = fnv1a(key, &h->opt_split_k, sizeof(int));
+  key = fnv1a(key, &h->opt_batch_streams, sizeof(int));
   key = fnv1a(key, &h->wait_cycles, sizeof(long long));
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
-    // capture every launch of the batch once, on a private stream
-    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    const bool prof_on = h->prof.on;
-    h->prof.on = false;  // no event records inside the capture
-    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
-    int rr = MODAL_OK;
-    bool first = true;
-    for (int i = 0; i < n && rr == MODAL_OK; ++i) {
-      if ((int64_t)probs[i].n_late * probs[i].n_prim == 0) continue;
-      rr = run_separable(h, h->num_sms, &probs[i], plans[i], gammas[i], h->cap_stream, scratch, first, true);
-      first = false;
+    // capture one graph per candidate; with several, replay each twice and
+    // keep the one whose second replay is fastest (blocks this first call)
+    std::vector<cudaGraphExec_t> execs;
+    for (auto &bl : cands) {
+      cudaGraphExec_t ex = nullptr;
+      if (int r = capture_batch(h, n, probs, plans, gammas, bl, (char *)scratch, &ex)) {
+        for (auto x : execs) cudaGraphExecDestroy(x);
+        return r;
+      }
+      execs.push_back(ex);
     }
-    cudaGraph_t graph = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
-    h->prof.on = prof_on;
-    if (rr != MODAL_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return rr;
+    int best = 0;
+    if (execs.size() > 1) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      float best_ms = 1e30f;
+      for (size_t c = 0; c < execs.size(); ++c) {
+        cudaError_t ce = cudaGraphLaunch(execs[c], st);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
+        if (ce == cudaSuccess) ce = cudaGraphLaunch(execs[c], st);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          for (auto x : execs) cudaGraphExecDestroy(x);
+          return fail(h, MODAL_ECUDA, "timing the batched graphs: %s", cudaGetErrorString(ce));
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = (int)c;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
     }
-    if (ce != cudaSuccess) return fail(h, MODAL_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
-    cudaGraphExec_t exec = nullptr;
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return fail(h, MODAL_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
-    it = h->graphs.emplace(key, exec).first;
+    for (size_t c = 0; c < execs.size(); ++c)
+      if ((int)c != best) cudaGraphExecDestroy(execs[c]);
+    it = h->graphs.emplace(key, modal_handle::BatchGraph{execs[best], cands[best].ns}).first;
   }
-  CK(cudaGraphLaunch(it->second, st));
+  CK(cudaGraphLaunch(it->second.exec, st));
   if (any_tc) {
-    CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(scratch), sizeof(int), cudaMemcpyDeviceToHost, st));
+    const int ns = it->second.streams;
+    const BatchLayout bl = batch_layout(n, probs, plans, ns);
+    for (int k = 0; k < ns; ++k)
+      CK(cudaMemcpyAsync(h->pinned_err + k, tc_error_word((char *)scratch + bl.off[k]), sizeof(int),
+                         cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(h->err_event, st));
+    h->n_err_words = ns;
     h->err_pending = true;
   }
   return MODAL_OK;

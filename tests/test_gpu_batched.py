@@ -46,3 +46,48 @@ def test_batched_uneven_models(mg, precision, tol):
     for g, ref in zip(gs2, refs):      # Gamma' is cubic in q~: factor (-1/2)^3
         assert normwise(g, -0.125 * ref) < tol
     h.close()
+
+
+@pytest.mark.parametrize("streams", [0, 1, 3, 8])
+def test_batched_streams(mg, streams):
+    """The batch spread over concurrent streams (MODAL_OPT_BATCH_STREAMS; 0 =
+    chosen by timing on the first call): each result equals the single-problem
+    entry point on the same inputs, and the replayed graph reads new data."""
+    probs = syn.batched_models(n=7, scale=0.03, base_seed=2000)
+    h = mg.Handle()
+    mg.set_option(mg.OPT_BATCH_STREAMS, streams, handle=h)
+    dps = [mg.DeviceProblem.from_host(P, handle=h) for P in probs]
+    gs = mg.project_separable_batched(dps, precision=2, handle=h)
+    mg.handle_status(handle=h)
+    singles = [mg.project_separable(dp, precision=2, handle=h).cpu().numpy() for dp in dps]
+    mg.handle_status(handle=h)
+    for g, ref in zip(gs, singles):
+        assert normwise(g, ref) < 1e-12
+    for dp in dps:
+        dp.qt.mul_(2.0)
+    gs2 = mg.project_separable_batched(dps, precision=2, outs=gs, handle=h)
+    mg.handle_status(handle=h)
+    for g, ref in zip(gs2, singles):   # cubic in q~: factor 8
+        assert normwise(g, 8.0 * ref) < 1e-12
+    h.close()
+
+
+def test_batched_bounded_wait_status_from_every_stream(mg):
+    """A wait bound of one clock makes the tensor-core kernels give up on every
+    stream of a batched call; the status word of each stream reaches
+    modal_handle_status, and the next call with the default bound is right."""
+    probs = syn.batched_models(n=4, scale=0.03, base_seed=3000)
+    h = mg.Handle()
+    mg.set_option(mg.OPT_BATCH_STREAMS, 4, handle=h)
+    dps = [mg.DeviceProblem.from_host(P, handle=h) for P in probs]
+    mg.set_wait_limit(1, handle=h)
+    mg.project_separable_batched(dps, precision=2, handle=h)
+    with pytest.raises(mg.ModalError) as ei:
+        mg.handle_status(handle=h)
+    assert ei.value.code == 4        # MODAL_ETIMEOUT
+    mg.set_wait_limit(0, handle=h)
+    gs = mg.project_separable_batched(dps, precision=2, handle=h)
+    mg.handle_status(handle=h)
+    for g, P in zip(gs, probs):
+        assert normwise(g, oracle.separable(P)) < 1e-8
+    h.close()
