@@ -83,6 +83,15 @@ typedef struct modal_opts {
   int32_t precision;         /* MODAL_PREC_* */
   int32_t allow_inexact_gl;  /* nonzero: accept n_mu below that bound */
   int32_t x_chunk;           /* radial points per streamed chunk; 0 = automatic */
+  double *error_estimate;    /* optional, modal_project_separable only: device
+                                [n_late][n_prim] output (overwritten) of the
+                                same projection with every M replaced by |M|
+                                and every weight by its magnitude, i.e.
+                                1/(48 pi) sum_x |W_x| sum_j om_j sum of the six
+                                |products| -- the scale of the rounding error
+                                of each entry; |error| <= tol * estimate is
+                                the conditioned entrywise check.  Costs one
+                                more triple product.  NULL: not computed. */
 } modal_opts;
 
 /* ---- handle ------------------------------------------------------------ */

@@ -52,6 +52,8 @@ def _load():
     common = [ctypes.c_int] * 5 + [_d, _d, _d, _d]
     lib.oracle_separable.argtypes = common + [ctypes.c_int, _d, _d, ctypes.c_int, _i,
                                               ctypes.c_int, _i, _d]
+    lib.oracle_separable_abs.argtypes = common + [ctypes.c_int, _d, _d, ctypes.c_int, _i,
+                                              ctypes.c_int, _i, _d]
     lib.oracle_direct.argtypes = common + [ctypes.c_int, _i, _d, ctypes.c_int,
                                            ctypes.c_int, _i, ctypes.c_int, _i, _d]
     lib.oracle_backward.argtypes = common + [ctypes.c_int, _d, _d, ctypes.c_int, _i,
@@ -130,9 +132,11 @@ def M_table(P, mu) -> np.ndarray:
 
 
 def separable(P, n_mu: int | None = None, xw=None, mu=None, om=None,
-              late=None, prim=None) -> np.ndarray:
+              late=None, prim=None, magnitudes: bool = False) -> np.ndarray:
     """Gamma' by Eq. 2D (Section 2.2) with GL mu and trapezium x weights.
-    ``late``/``prim`` restrict the mode lists (rows/columns)."""
+    ``late``/``prim`` restrict the mode lists (rows/columns).  With
+    ``magnitudes`` every weight and each of the six products is taken in
+    magnitude: the scale of the rounding error of each entry."""
     n_mu = P.n_mu if n_mu is None else int(n_mu)
     if mu is None:
         mu, om = gl_nodes(n_mu)
@@ -143,9 +147,9 @@ def separable(P, n_mu: int | None = None, xw=None, mu=None, om=None,
     l0, l1, nbl, nbp, nx, q, qt, wl, xw = _common(P, xw)
     mu, om = _f64(mu), _f64(om)
     g = np.zeros((late.shape[0], prim.shape[0]))
-    _load().oracle_separable(l0, l1, nbl, nbp, nx, _pd(q), _pd(qt), _pd(wl), _pd(xw),
-                             int(mu.size), _pd(mu), _pd(om), int(late.shape[0]), _pi(late),
-                             int(prim.shape[0]), _pi(prim), _pd(g))
+    fn = _load().oracle_separable_abs if magnitudes else _load().oracle_separable
+    fn(l0, l1, nbl, nbp, nx, _pd(q), _pd(qt), _pd(wl), _pd(xw), int(mu.size), _pd(mu), _pd(om),
+       int(late.shape[0]), _pi(late), int(prim.shape[0]), _pi(prim), _pd(g))
     return g
 
 

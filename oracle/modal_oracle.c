@@ -216,6 +216,15 @@ static double perm3(const double *M, int nbp, const int *r, const int *c) {
   return s1 + s2 + s3 + s4 + s5 + s6;
 }
 
+/* The same six products in magnitude: the summation-error scale of perm3. */
+static double perm3_abs(const double *M, int nbp, const int *r, const int *c) {
+  double m[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) m[i][j] = fabs(M[r[i] * nbp + c[j]]);
+  return m[0][0] * m[1][1] * m[2][2] + m[0][0] * m[1][2] * m[2][1] + m[0][1] * m[1][0] * m[2][2] +
+         m[0][1] * m[1][2] * m[2][0] + m[0][2] * m[1][0] * m[2][1] + m[0][2] * m[1][1] * m[2][0];
+}
+
 /* P_{ii'}(x, mu) of Eq. legendre for every (a, p) flagged in need_a x need_p:
  *   M[a][p] = sum_l wl[l] P_l(mu) q_a(l) q~_p(l, x). */
 static void legendre_table_M(int l_min, int L, int nbl, int nbp, const double *q,
@@ -244,11 +253,11 @@ static void legendre_table_M(int l_min, int L, int nbl, int nbp, const double *q
 /* Only the (a, p) pairs used by the given mode lists are formed, so a       */
 /* caller may ask for a few rows/columns of a large problem.                  */
 /* ------------------------------------------------------------------------ */
-void oracle_separable(int l_min, int l_max, int nbl, int nbp, int nx,
-                      const double *q, const double *qt, const double *wl,
-                      const double *xw, int nmu, const double *mu, const double *om,
-                      int nlate, const int *late, int nprim, const int *prim,
-                      double *gamma) {
+static void separable_impl(int l_min, int l_max, int nbl, int nbp, int nx,
+                           const double *q, const double *qt, const double *wl,
+                           const double *xw, int nmu, const double *mu, const double *om,
+                           int nlate, const int *late, int nprim, const int *prim,
+                           double *gamma, int magnitudes) {
   int L = l_max - l_min + 1;
   unsigned char *need_a = (unsigned char *)calloc((size_t)nbl, 1);
   unsigned char *need_p = (unsigned char *)calloc((size_t)nbp, 1);
@@ -271,15 +280,36 @@ void oracle_separable(int l_min, int l_max, int nbl, int nbp, int nx,
       for (int m = 0; m < nprim; ++m) {
         double s = 0.0;
         for (int j = 0; j < nmu; ++j)
-          s += om[j] * perm3(Mall + (size_t)j * nbl * nbp, nbp, late + 3 * n, prim + 3 * m);
+          s += magnitudes ? fabs(om[j]) * perm3_abs(Mall + (size_t)j * nbl * nbp, nbp, late + 3 * n, prim + 3 * m)
+                          : om[j] * perm3(Mall + (size_t)j * nbl * nbp, nbp, late + 3 * n, prim + 3 * m);
         inner[(size_t)n * nprim + m] = s;
       }
     }
-    for (size_t i = 0; i < (size_t)nlate * nprim; ++i) gamma[i] += xw[x] * inner[i];
+    const double wx = magnitudes ? fabs(xw[x]) : xw[x];
+    for (size_t i = 0; i < (size_t)nlate * nprim; ++i) gamma[i] += wx * inner[i];
   }
   const double pref = 1.0 / (48.0 * ORACLE_PI);
   for (size_t i = 0; i < (size_t)nlate * nprim; ++i) gamma[i] *= pref;
   free(need_a); free(need_p); free(inner); free(Mall); free(Pall);
+}
+
+void oracle_separable(int l_min, int l_max, int nbl, int nbp, int nx,
+                      const double *q, const double *qt, const double *wl,
+                      const double *xw, int nmu, const double *mu, const double *om,
+                      int nlate, const int *late, int nprim, const int *prim,
+                      double *gamma) {
+  separable_impl(l_min, l_max, nbl, nbp, nx, q, qt, wl, xw, nmu, mu, om, nlate, late, nprim, prim, gamma, 0);
+}
+
+/* The same sum with every term in magnitude -- |om_j|, |W_x| and the six   */
+/* |products| of P_{ii'} entries -- the scale of the rounding error of each */
+/* entry of Gamma' (the conditioned entrywise check).                        */
+void oracle_separable_abs(int l_min, int l_max, int nbl, int nbp, int nx,
+                          const double *q, const double *qt, const double *wl,
+                          const double *xw, int nmu, const double *mu, const double *om,
+                          int nlate, const int *late, int nprim, const int *prim,
+                          double *gamma) {
+  separable_impl(l_min, l_max, nbl, nbp, nx, q, qt, wl, xw, nmu, mu, om, nlate, late, nprim, prim, gamma, 1);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -45,7 +45,8 @@ class Problem(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("n_mu", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("allow_inexact_gl", ctypes.c_int32), ("x_chunk", ctypes.c_int32)]
+                ("allow_inexact_gl", ctypes.c_int32), ("x_chunk", ctypes.c_int32),
+                ("error_estimate", ctypes.c_void_p)]
 
 
 def lib_path() -> Path:

@@ -133,8 +133,10 @@ class DeviceProblem:
                        self.prim_modes.data_ptr())
 
 
-def _opts(precision=_lib.PREC_FP64, n_mu=0, allow_inexact_gl=False, x_chunk=0) -> Opts:
-    return Opts(int(n_mu), int(precision), int(bool(allow_inexact_gl)), int(x_chunk))
+def _opts(precision=_lib.PREC_FP64, n_mu=0, allow_inexact_gl=False, x_chunk=0,
+          error_estimate: Optional[torch.Tensor] = None) -> Opts:
+    return Opts(int(n_mu), int(precision), int(bool(allow_inexact_gl)), int(x_chunk),
+                None if error_estimate is None else error_estimate.data_ptr())
 
 
 def _h(handle, device):
@@ -205,13 +207,17 @@ def set_wait_limit(cycles: int, handle=None, device=None):
 
 def project_separable(dp: DeviceProblem, precision: int = _lib.PREC_FP64, n_mu: int = 0,
                       allow_inexact_gl: bool = False, x_chunk: int = 0, out=None, handle=None,
-                      qt: Optional[torch.Tensor] = None, q: Optional[torch.Tensor] = None):
-    """modal_project_separable: Gamma' [n_late][n_prim] (FP64)."""
+                      qt: Optional[torch.Tensor] = None, q: Optional[torch.Tensor] = None,
+                      error_estimate: Optional[torch.Tensor] = None):
+    """modal_project_separable: Gamma' [n_late][n_prim] (FP64).  If
+    ``error_estimate`` (a [n_late][n_prim] FP64 device tensor) is given, it
+    receives the same projection of |M| with |weights| (the per-entry error
+    scale)."""
     h = _h(handle, dp.device)
     gamma = out if out is not None else torch.empty(dp.n_late, dp.n_prim, dtype=_f64,
                                                     device=dp.device)
     s = dp.struct(qt, q)
-    o = _opts(precision, n_mu, allow_inexact_gl, x_chunk)
+    o = _opts(precision, n_mu, allow_inexact_gl, x_chunk, error_estimate)
     check(lib().modal_project_separable(h.ptr, ctypes.byref(s), ctypes.byref(o), _ptr(gamma),
                                         _stream(dp.device)), h.ptr)
     return gamma

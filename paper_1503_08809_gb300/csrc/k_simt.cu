@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) k_triple(SepShape s, GLayout g, const T *
                                                 const double *__restrict__ om,
                                                 const double *__restrict__ xw, int x0, int64_t S,
                                                 int64_t k_per_split, double *__restrict__ out,
-                                                int64_t out_stride) {
+                                                int64_t out_stride, int absM) {
   using C = SimtCfg<T>;
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
   constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
@@ -259,17 +259,23 @@ __global__ void __launch_bounds__(256) k_triple(SepShape s, GLayout g, const T *
     if (kok) {
       int xl = (int)(k / n_mu), j = (int)(k % n_mu);
       w = (T)(om[j] * xw[x0 + xl]);
+      if (absM && w < 0) w = -w;
     }
+    // absM: the error-scale projection (every M and weight by its magnitude)
+    auto ld = [&](int i) -> T {
+      const T m = Mk[i];
+      return (absM && m < 0) ? -m : m;
+    };
 #pragma unroll
     for (int it = 0; it < AIT; ++it) {
       T v = 0;
-      if (kok && rok[it]) v = w * (Mk[ro1[it]] * Mk[ro2[it]] + Mk[ro3[it]] * Mk[ro4[it]]);
+      if (kok && rok[it]) v = w * (ld(ro1[it]) * ld(ro2[it]) + ld(ro3[it]) * ld(ro4[it]));
       As[kk_ld][r_ld + it * (NT / BK)] = v;
     }
 #pragma unroll
     for (int it = 0; it < BIT; ++it) {
       T v = 0;
-      if (kok && cok[it]) v = Mk[co[it]];
+      if (kok && cok[it]) v = ld(co[it]);
       Bs[kk_ld][r_ld + it * (NT / BK)] = v;
     }
     __syncthreads();
@@ -325,7 +331,7 @@ int triple_launches(const SepShape &s, int nxc, int ksplit, bool accumulate) {
 template <typename T>
 cudaError_t launch_triple(const SepShape &s, const T *M, const double *om, const double *xw, int x0,
                           int nxc, int ksplit, double *G, double *Gpart, bool accumulate,
-                          int num_sms, cudaStream_t st) {
+                          int num_sms, cudaStream_t st, bool absM) {
   (void)num_sms;
   using C = SimtCfg<T>;
   GLayout g = make_glayout(s.nbl, s.nbp);
@@ -336,7 +342,7 @@ cudaError_t launch_triple(const SepShape &s, const T *M, const double *om, const
   dim3 grid((unsigned)tiles, (unsigned)nks);
   const bool direct = (nks == 1 && !accumulate);
   double *out = direct ? G : Gpart;
-  k_triple<T><<<grid, 256, 0, st>>>(s, g, M, om, xw, x0, S, kps, out, g.size());
+  k_triple<T><<<grid, 256, 0, st>>>(s, g, M, om, xw, x0, S, kps, out, g.size(), absM ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || direct) return e;
   int64_t n = g.size();
@@ -345,10 +351,10 @@ cudaError_t launch_triple(const SepShape &s, const T *M, const double *om, const
 }
 template cudaError_t launch_triple<double>(const SepShape &, const double *, const double *,
                                            const double *, int, int, int, double *, double *, bool,
-                                           int, cudaStream_t);
+                                           int, cudaStream_t, bool);
 template cudaError_t launch_triple<float>(const SepShape &, const float *, const double *,
                                           const double *, int, int, int, double *, double *, bool,
-                                          int, cudaStream_t);
+                                          int, cudaStream_t, bool);
 
 // ---------------------------------------------------------------------------
 // a7: Gamma'[n][n'] = scale * (G[ab{pr}, c s] + G[ab{ps}, c r] + G[ab{rs}, c p])

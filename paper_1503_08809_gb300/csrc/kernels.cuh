@@ -24,7 +24,7 @@ int triple_launches(const SepShape &s, int nxc, int ksplit, bool accumulate);
 template <typename T>
 cudaError_t launch_triple(const SepShape &s, const T *M, const double *om, const double *xw, int x0,
                           int nxc, int ksplit, double *G, double *Gpart, bool accumulate,
-                          int num_sms, cudaStream_t st);
+                          int num_sms, cudaStream_t st, bool absM = false);
 int triple_ksplit(const SepShape &s, int nxc, int num_sms);
 cudaError_t launch_gather(const SepShape &s, const double *G, const int *late, const int *prim,
                           int n_late, int n_prim, double scale, double *gamma, cudaStream_t st);

@@ -362,6 +362,7 @@ struct SepPlan {
   int ksplit;   // K split of the SIMT triple product
   size_t elem;  // bytes per M element
   int64_t Gsize;
+  double *est;  // error-scale output (opts->error_estimate) or NULL
   size_t bytes;
 };
 
@@ -410,6 +411,7 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   }
   GLayout g = make_glayout(p->nb_late, p->nb_prim);
   pl.Gsize = g.size();
+  pl.est = o ? o->error_estimate : nullptr;
   pl.ksplit = triple_ksplit(pl.s, pl.nxc, num_sms);
   const int nchunks = p->n_x > 0 ? (p->n_x + pl.nxc - 1) / pl.nxc : 0;
   const bool need_part = pl.ksplit > 1 || nchunks > 1;
@@ -418,6 +420,7 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   b += align256(sizeof(double) * (size_t)n_mu * pl.s.L);          // A
   b += align256(pl.elem * (size_t)pl.nxl * n_mu * nblp);          // M chunk
   b += align256(sizeof(double) * (size_t)pl.Gsize);               // G
+  if (pl.est) b += align256(sizeof(double) * (size_t)pl.Gsize);   // G of |M| (error scale)
   if (need_part) b += align256(sizeof(double) * (size_t)pl.Gsize * pl.ksplit);
   if (prec == MODAL_PREC_OZAKI_BF16) b += tc_scratch_bytes(pl.s, pl.nxl, pl.nxc, pl.variant);
   pl.bytes = b + 1024;
@@ -438,6 +441,7 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
   double *A = bp.take<double>((size_t)s.n_mu * s.L);
   void *M = bp.take<char>(pl.elem * (size_t)pl.nxl * s.n_mu * s.nbl * s.nbp);
   double *G = bp.take<double>((size_t)pl.Gsize);
+  double *Gabs = pl.est ? bp.take<double>((size_t)pl.Gsize) : nullptr;
   const int nchunks = (p->n_x + pl.nxc - 1) / pl.nxc;
   const bool need_part = pl.ksplit > 1 || nchunks > 1;
   double *Gpart = need_part ? bp.take<double>((size_t)pl.Gsize * pl.ksplit) : nullptr;
@@ -451,8 +455,9 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
     CK(launch_legendre_table(s.n_mu, mu, s.l_min, s.l_max, p->w_l, A, st));      // a2
   }
   if (p->n_x == 0) {
-    PROF(h, "zero_G", st);
+    PROFN(h, "zero_G", st, Gabs ? 2 : 1);
     CK(launch_zero(G, (size_t)pl.Gsize, st));
+    if (Gabs) CK(launch_zero(Gabs, (size_t)pl.Gsize, st));
   }
   for (int c = 0; c < nchunks; ++c) {
     const int x0 = c * pl.nxc;
@@ -462,17 +467,31 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
         PROF(h, "contract_l_f64", st);
         CK(launch_contract_l<double>(s, A, p->q, p->qt, x0, nxc, (double *)M, st));         // a4+a5
       }
-      PROFN(h, "triple_f64", st, triple_launches(s, nxc, pl.ksplit, c > 0));
-      CK(launch_triple<double>(s, (double *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
-                               num_sms, st));                                               // a6
+      {
+        PROFN(h, "triple_f64", st, triple_launches(s, nxc, pl.ksplit, c > 0));
+        CK(launch_triple<double>(s, (double *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
+                                 num_sms, st));                                             // a6
+      }
+      if (Gabs) {
+        PROFN(h, "triple_abs_f64", st, triple_launches(s, nxc, pl.ksplit, c > 0));
+        CK(launch_triple<double>(s, (double *)M, om, p->x_w, x0, nxc, pl.ksplit, Gabs, Gpart, c > 0,
+                                 num_sms, st, true));
+      }
     } else if (pl.prec == MODAL_PREC_FP32) {
       {
         PROF(h, "contract_l_f32", st);
         CK(launch_contract_l<float>(s, A, p->q, p->qt, x0, nxc, (float *)M, st));
       }
-      PROFN(h, "triple_f32", st, triple_launches(s, nxc, pl.ksplit, c > 0));
-      CK(launch_triple<float>(s, (float *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
-                              num_sms, st));
+      {
+        PROFN(h, "triple_f32", st, triple_launches(s, nxc, pl.ksplit, c > 0));
+        CK(launch_triple<float>(s, (float *)M, om, p->x_w, x0, nxc, pl.ksplit, G, Gpart, c > 0,
+                                num_sms, st));
+      }
+      if (Gabs) {
+        PROFN(h, "triple_abs_f32", st, triple_launches(s, nxc, pl.ksplit, c > 0));
+        CK(launch_triple<float>(s, (float *)M, om, p->x_w, x0, nxc, pl.ksplit, Gabs, Gpart, c > 0,
+                                num_sms, st, true));
+      }
     } else {
       // tensor-core form: the l contraction over an l-chunk of nxl points,
       // then the triple product over its chunks of nxc points
@@ -492,6 +511,11 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
         int r = tc_triple_chunk(s, Ms, om, p->x_w, xs, ns, pl.nxl, G, xs > 0, tcs, wc, num_sms, pl.variant,
                                 h ? h->opt_split_k : 0, st, prof);
         if (r) return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
+        if (Gabs) {
+          r = tc_triple_chunk(s, Ms, om, p->x_w, xs, ns, pl.nxl, Gabs, xs > 0, tcs, wc, num_sms, pl.variant,
+                              h ? h->opt_split_k : 0, st, prof, true);
+          if (r) return fail(h, r, "tensor-core triple product (error scale) failed: %s", tc_last_error());
+        }
       }
     }
   }
@@ -502,9 +526,12 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
     h->n_err_words = 1;
     h->err_pending = true;
   }
-  PROF(h, "gather", st);
+  PROFN(h, "gather", st, Gabs ? 2 : 1);
   CK(launch_gather(s, G, p->late_modes, p->prim_modes, p->n_late, p->n_prim, 1.0 / (48.0 * MODAL_PI), gamma,
                    st));                                                                    // a7
+  if (Gabs)
+    CK(launch_gather(s, Gabs, p->late_modes, p->prim_modes, p->n_late, p->n_prim, 1.0 / (48.0 * MODAL_PI),
+                     pl.est, st));
   return MODAL_OK;
 }
 
@@ -641,6 +668,7 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
   if (n < 0) return fail(h, MODAL_EINVAL, "n < 0");
   if (n == 0) return MODAL_OK;
   if (!probs || !gammas) return fail(h, MODAL_EINVAL, "null probs/gammas");
+  if (o && o->error_estimate) return fail(h, MODAL_EINVAL, "error_estimate is for single-problem calls");
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<SepPlan> plans(n);
   bool any_tc = false;

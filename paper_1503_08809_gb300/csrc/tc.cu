@@ -807,6 +807,7 @@ constexpr int TP_COLS = 32;
 __global__ void __launch_bounds__(256) k_tp_col_max(int64_t K, int nblp, int n_mu, int x0,
                                                     const double *__restrict__ M, const double *__restrict__ om,
                                                     const double *__restrict__ xw, unsigned *__restrict__ colmax) {
+  // |M| bounds serve both the projection and its |M| error-scale variant
   __shared__ float sw[128];
   __shared__ float red[2][8][TP_COLS];
   const int c0 = blockIdx.x * TP_COLS;
@@ -814,7 +815,7 @@ __global__ void __launch_bounds__(256) k_tp_col_max(int64_t K, int nblp, int n_m
   const int tc = threadIdx.x & 31, tk = threadIdx.x >> 5;
   if (threadIdx.x < 128) {
     const int64_t k = k0 + threadIdx.x;
-    sw[threadIdx.x] = k < K ? sqrtf((float)(om[k % n_mu] * xw[x0 + k / n_mu])) : 0.f;
+    sw[threadIdx.x] = k < K ? sqrtf(fabsf((float)(om[k % n_mu] * xw[x0 + k / n_mu]))) : 0.f;
   }
   __syncthreads();
   const int col = c0 + tc;
@@ -850,8 +851,9 @@ __global__ void __launch_bounds__(256) k_tp_split_cols(int64_t K, int Kpad, int 
                                                        const unsigned *__restrict__ colmax, f2 *__restrict__ Mdf,
                                                        double *__restrict__ mxW, int *__restrict__ eB,
                                                        __nv_bfloat16 *__restrict__ Bt, int *__restrict__ emaxB,
-                                                       int *__restrict__ err) {
+                                                       int *__restrict__ err, int absM) {
   __shared__ double sw[32];
+  __shared__ float sgn[32];
   __shared__ __nv_bfloat16 tile[OZ_SLICES][TP_COLS][32 + 8];
   __shared__ f2 mtile[TP_COLS][32 + 1];
   const int c0 = blockIdx.x * TP_COLS;
@@ -860,8 +862,12 @@ __global__ void __launch_bounds__(256) k_tp_split_cols(int64_t K, int Kpad, int 
   const int tc = threadIdx.x & 31, tk = threadIdx.x >> 5;  // 32 columns x 8 k-lanes (4 slices each)
   const int col = c0 + tc;
   if (threadIdx.x < 32) {
+    // M~ = sqrt(|w_k|) M; the sign of w_k goes with the B slices of M, so that
+    // Y B = |w| M M M sign(w) (absM: every M and weight by its magnitude)
     const int64_t k = k0 + threadIdx.x;
-    sw[threadIdx.x] = k < K ? sqrt(om[k % n_mu] * xw[x0 + k / n_mu]) : 0.0;
+    const double w = k < K ? om[k % n_mu] * xw[x0 + k / n_mu] : 0.0;
+    sw[threadIdx.x] = sqrt(fabs(w));
+    sgn[threadIdx.x] = (w < 0.0 && !absM) ? -1.f : 1.f;
   }
   // the column's exponent for this chunk
   float m1 = 0.f, m2 = 0.f;
@@ -889,10 +895,11 @@ __global__ void __launch_bounds__(256) k_tp_split_cols(int64_t K, int Kpad, int 
   for (int i = 0; i < 4; ++i) {
     const int kk = tk * 4 + i;
     const int64_t k = k0 + kk;
-    const double v = (col < nblp && k < K) ? M[k * nblp + col] : 0.0;
+    double v = (col < nblp && k < K) ? M[k * nblp + col] : 0.0;
+    if (absM) v = fabs(v);
     const f2 vd = df_from_d(v);
     __nv_bfloat16 o[OZ_SLICES];
-    split_scaled(vd.h, vd.l, sc, o);
+    split_scaled(sgn[kk] * vd.h, sgn[kk] * vd.l, sc, o);
 #pragma unroll
     for (int s = 0; s < OZ_SLICES; ++s) tile[s][tc][kk] = o[s];
     mtile[tc][kk] = df_from_d(sw[kk] * v);
@@ -1407,7 +1414,7 @@ size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
 
 int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
                     int nxl_max, double *G, bool accumulate, void *scratch, long long wait_cycles, int num_sms,
-                    int variant, int split_k, cudaStream_t st, Profiler *prof) {
+                    int variant, int split_k, cudaStream_t st, Profiler *prof, bool absM) {
   LScratch ls = l_scratch(scratch, s, nxl_max);
   char *w = ls.end;
   int *words = ls.words;
@@ -1433,7 +1440,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     k_tp_col_max<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)cdiv64(K, 128)), 256, 0, st>>>(
         K, nblp, s.n_mu, x0, M, om, xw, colmax);
     k_tp_split_cols<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)(Kpad / 32)), 256, 0, st>>>(
-        K, Kpad, nblp, s.n_mu, x0, M, om, xw, colmax, Mdf, mxW, eB, Bt, words + 3, words);
+        K, Kpad, nblp, s.n_mu, x0, M, om, xw, colmax, Mdf, mxW, eB, Bt, words + 3, words, absM ? 1 : 0);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   if (variant == TC_TRIPLE_MATERIALISED) {

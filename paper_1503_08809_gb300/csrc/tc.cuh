@@ -24,7 +24,7 @@ int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_
 // [xl][j][a][p]) starts at M: G (+)= sum over its slices.
 int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
                     int nxl_max, double *G, bool accumulate, void *scratch, long long wait_cycles, int num_sms,
-                    int variant, int split_k, cudaStream_t st, Profiler *prof = nullptr);
+                    int variant, int split_k, cudaStream_t st, Profiler *prof = nullptr, bool absM = false);
 // device status word of the tensor-core scratch (bit 0: a bounded wait gave up,
 // bit 1: a value outside the FP32 exponent range of the split operands)
 int *tc_error_word(void *scratch);

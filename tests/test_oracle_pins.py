@@ -383,3 +383,37 @@ def test_M_table_matches_library_legendre():
     Pl = np.array([[npleg.legval(m, np.eye(P.l_max + 1)[l]) for l in ls] for m in mu])
     ref = np.einsum("jl,l,al,xpl->xjap", Pl, P.w_l, P.q, P.qt)
     assert np.abs(M - ref).max() / np.abs(ref).max() < 1e-13
+
+
+def _magnitude_sum_numpy(P, mu, om, xw):
+    """The error-scale projection by plain numpy loops, independent of the
+    oracle's C code: 1/(48 pi) sum_x |W_x| sum_j |om_j| sum over the six
+    assignments sigma of |M_a sigma(p) M_b sigma(r) M_c sigma(s)|."""
+    ls = np.arange(P.l_min, P.l_max + 1)
+    Pl = npleg.legvander(mu, P.l_max)[:, ls]                  # [j][l]
+    M = np.einsum("l,jl,al,xpl->xjap", P.w_l, Pl, P.q, P.qt)    # [x][j][a][p]
+    g = np.zeros((P.n_late, P.n_prim))
+    for n, (a, b, c) in enumerate(P.late_modes):
+        for m, prs in enumerate(P.prim_modes):
+            t = 0.0
+            for s in itertools.permutations(prs):
+                t = t + np.abs(M[:, :, a, s[0]] * M[:, :, b, s[1]] * M[:, :, c, s[2]])
+            g[n, m] = np.sum(np.abs(xw)[:, None] * np.abs(om)[None, :] * t)
+    return g / (48.0 * math.pi)
+
+
+def test_error_scale_matches_brute_force():
+    """The magnitude form of the separable sum (the per-entry rounding-error
+    scale) equals a plain numpy evaluation on a tiny problem, bounds |Gamma'|
+    entrywise, ignores a sign flip of q~ and is cubic in its scale."""
+    P = syn.make_problem(10, 3, 3, seed=17)
+    mu, om = oracle.gl_nodes(P.n_mu)
+    xw = oracle.x_weights(P.x)
+    ga = oracle.separable(P, magnitudes=True)
+    ref = _magnitude_sum_numpy(P, mu, om, xw)
+    assert np.allclose(ga, ref, rtol=1e-12, atol=0)
+    g = oracle.separable(P)
+    assert np.all(np.abs(g) <= ga * (1 + 1e-12))
+    assert np.abs(g).max() < ga.max()            # cancellation happens somewhere
+    Pn = syn.Problem(**{**P.__dict__, "qt": -2.0 * P.qt})
+    assert np.allclose(oracle.separable(Pn, magnitudes=True), 8.0 * ga, rtol=1e-13, atol=0)
