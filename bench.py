@@ -61,8 +61,9 @@ def parse():
     ap.add_argument("--workload", default="planck", choices=["planck", "grad", "batched"],
                     help="planck: the headline line; grad: forward + adjoint at l_max 1000 / "
                          "16 functions / 300 x; batched: 64 uneven models in one call")
-    ap.add_argument("--tc-fused", type=int, default=0, choices=[0, 1],
-                    help="tensor-core triple product: 0 = Y through HBM, 1 = Y in shared memory")
+    ap.add_argument("--tc-fused", type=int, default=0, choices=[0, 1, 2],
+                    help="tensor-core triple product: 0 = Y through HBM, 1 and 2 = Y formed in "
+                         "shared memory (two forms)")
     ap.add_argument("--once", action="store_true",
                     help="run one projection and exit (a small case for profiler captures)")
     ap.add_argument("--fp64-x", type=int, default=20,
@@ -325,8 +326,8 @@ def run_ours(args):
             "dtype": DTYPE[prec_name], "data": "synthetic",
             "config": {"workload": P.name, "l_max": P.l_max, "nb": P.nb_late, "n_x": P.n_x,
                        "n_mu": P.n_mu, "slices": P.slices, "precision": prec_name,
-                       "n_modes": P.n_late, "tc_triple": ("shared-memory Y" if args.tc_fused
-                                                            else "Y through HBM"),
+                       "n_modes": P.n_late, "tc_triple": ["Y through HBM", "shared-memory Y",
+                                                          "shared-memory Y (16 warps)"][args.tc_fused],
                        "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "fp64_gpu": fp64, "error": err, "kernel_rooflines": rooflines,

@@ -121,8 +121,10 @@ int modal_handle_status(modal_handle *h);
 /* Tunables of the tensor-core form for later calls on this handle.
  * MODAL_OPT_TC_TRIPLE_FUSED: 0 (default) writes the BF16 slices of the Y
  *   operand of the triple product to device memory and runs a TMA-fed GEMM;
- *   1 forms Y in shared memory inside the GEMM (no Y traffic through HBM).
- *   Both give the same results to rounding.
+ *   1 forms Y in shared memory inside the GEMM (no Y traffic through HBM);
+ *   2 does so with sixteen warps from a TMA-staged tile of M~ rows (bases of
+ *   up to ~21 functions; larger ones use 0).  All give the same results to
+ *   rounding; 0 is the fastest at the sizes measured.
  * MODAL_OPT_TC_SPLIT_K: K splits of the shared-memory variant (0 = automatic).
  * MODAL_OPT_BATCH_STREAMS: concurrent streams of modal_project_separable_batched
  *   (1 .. 8), or 0 (default): the first call for a problem set captures one

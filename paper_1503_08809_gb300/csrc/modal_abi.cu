@@ -260,8 +260,8 @@ int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value) {
   if (int r = check_handle(h)) return r;
   switch (option) {
     case MODAL_OPT_TC_TRIPLE_FUSED:
-      if (value != 0 && value != 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_TRIPLE_FUSED takes 0 or 1");
-      h->opt_triple_variant = value ? TC_TRIPLE_FUSED : TC_TRIPLE_MATERIALISED;
+      if (value < 0 || value > 2) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_TRIPLE_FUSED takes 0, 1 or 2");
+      h->opt_triple_variant = value == 2 ? TC_TRIPLE_FUSED2 : value ? TC_TRIPLE_FUSED : TC_TRIPLE_MATERIALISED;
       return MODAL_OK;
     case MODAL_OPT_TC_SPLIT_K:
       if (value < 0 || value > 4096) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_SPLIT_K out of range");
@@ -369,6 +369,7 @@ struct SepPlan {
 static int plan_separable(modal_handle *h, const modal_problem *p, const modal_opts *o, SepPlan &pl,
                           int num_sms) {
   pl.variant = h ? h->opt_triple_variant : TC_TRIPLE_MATERIALISED;
+  if (pl.variant == TC_TRIPLE_FUSED2 && !tc_fused2_fits(p->nb_late, p->nb_prim)) pl.variant = TC_TRIPLE_MATERIALISED;
   int n_mu, prec, xch;
   if (int r = resolve_opts(h, p, o, n_mu, prec, xch)) return r;
   pl.s = SepShape{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};

@@ -227,7 +227,7 @@ __global__ void k_init_words(int *w, int mode) {
 // MMA schedule of one 16-deep K step for a tile of width w (see mma_plans):
 // plan[0] = number of runs | accumulators used << 8; plan[1 + r] = run r as
 // sa | first sb << 4 | count << 8 | accumulator << 12 | first-touch << 16.
-constexpr int OZ_PLAN_MAX = 11;
+constexpr int OZ_PLAN_MAX = 16;  // >= 15: the all-singles schedule always fits
 struct OzParams {
   uint32_t plan[OZ_BN / 16][1 + OZ_PLAN_MAX];  // by w / 16 - 1
   int64_t rowsA, rowsB;   // operand rows (TMA extents)
@@ -614,7 +614,7 @@ struct PlanSearch {
   }
 };
 
-static void fill_mma_plans(OzParams &P) {
+static void fill_mma_plans(uint32_t (&dst)[OZ_BN / 16][1 + OZ_PLAN_MAX]) {
   static uint32_t plans[OZ_BN / 16][1 + OZ_PLAN_MAX];
   static bool done = false;
   if (!done) {
@@ -624,13 +624,23 @@ static void fill_mma_plans(OzParams &P) {
       ps.nacc = 512 / ps.w < 15 ? 512 / ps.w : 15;
       ps.R = 256 / ps.w < OZ_SLICES ? 256 / ps.w : OZ_SLICES;
       ps.rec(0, 0, (1u << ps.nacc) - 1u, 0.0, 0, 0);
+      if (ps.best_n == 0) {  // not reached for nacc >= 3; the singles schedule is always valid
+        ps.best_n = 0;
+        for (int sa = 0; sa < OZ_SLICES; ++sa)
+          for (int sb = 0; sa + sb <= OZ_MAXLEV; ++sb) {
+            const int L = sa + sb, acc = L < 2 ? L : 2;
+            ps.best_plan[ps.best_n++] = (uint32_t)sa | (uint32_t)sb << 4 | 1u << 8 | (uint32_t)acc << 12 |
+                                        ((sa == 0 && sb <= 2) ? 1u << 16 : 0u);
+          }
+        ps.best_used = 3;
+      }
       memset(plans[i], 0, sizeof plans[i]);
       plans[i][0] = (uint32_t)ps.best_n | (uint32_t)ps.best_used << 8;
       for (int r = 0; r < ps.best_n; ++r) plans[i][1 + r] = ps.best_plan[r];
     }
     done = true;
   }
-  memcpy(P.plan, plans, sizeof plans);
+  memcpy(dst, plans, sizeof plans);
 }
 
 // B maps for the widths in `used` (bit i: 16 (i + 1) rows); the others stay zero
@@ -739,7 +749,7 @@ int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_
     P.nbl = s.nbl;
     P.nbp = s.nbp;
     P.wait_cycles = wait_cycles;
-    fill_mma_plans(P);
+    fill_mma_plans(P.plan);
     if ((e = cudaFuncSetAttribute(k_ozaki_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
         cudaSuccess)
       goto cuda_fail;
@@ -1390,6 +1400,338 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused triple product, second form.  Sixteen warps form the Y operand of
+// each K step in the GEMM's own shared-memory stage, from a TMA-staged tile of
+// the M~ rows the tile needs (groups a_first..a_last and b, K-major), and
+// drain the accumulators with their double-FP32 running sums in registers
+// (32 columns per thread), which leaves room for two 96 KB stages.
+//   warp 0: TMA (B slices of M, M~ groups);  warp 1: TMEM and MMA issue;
+//   warps 2-17: Y production (4 (row, slice pair) tasks per thread and K
+//   step, packed FP32x2 arithmetic) and the chunk drains.
+// Y rows of the tile whose pair lies outside the block are written as zero.
+// ---------------------------------------------------------------------------
+constexpr int F2_WARPS = 16;
+constexpr int F2_THREADS = 64 + 32 * F2_WARPS;
+constexpr int F2_MT_BYTES = 16 * 1024;            // M~ groups of one stage: <= 64 columns x 32 slices x 8 B
+constexpr int F2_MAX_COLS = F2_MT_BYTES / 256;
+constexpr int F2_STAGE = OZ_A_BYTES + OZ_B_BYTES + F2_MT_BYTES;
+constexpr int F2_SMEM = OZ_STAGES * F2_STAGE + 1024 /*align*/ + 256 /*barriers*/;
+static_assert(F2_SMEM <= 232448, "shared memory per CTA");
+static_assert(OZ_BK == 32, "one K step = 32 slices = 16 slice pairs");
+
+struct Fused2Params {
+  uint32_t plan[OZ_BN / 16][1 + OZ_PLAN_MAX];
+  int64_t rowsB;      // nb_late * nb_prim (columns of M)
+  int64_t rowsY;      // rows of the full Y operand (for eY)
+  int Kpad, nchunks, nbp;
+  const int *eY;      // [nchunks][rowsY] row exponents of Y
+  const int *eB;      // [nchunks][rowsB]
+  const int *emaxY, *emaxB;
+  double *G;
+  GLayout g;
+  int *err;
+  long long wait_cycles;
+};
+
+// Number of M~ groups of the tile (distinct a of its rows, plus b).
+__host__ __device__ inline int f2_groups(const GLayout &g, int b, int rt) {
+  const int64_t r0 = (int64_t)rt * OZ_BM;
+  const int64_t r1 = min(g.rows(b), r0 + OZ_BM) - 1;
+  return (int)(r1 / g.P2 - r0 / g.P2) + 2;
+}
+
+__global__ void __launch_bounds__(F2_THREADS, 1)
+    k_ozaki_triple_fused2(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ BMaps bmaps,
+                          Fused2Params P) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(sm + OZ_STAGES * F2_STAGE);  // TMA: B and M~ landed
+  uint64_t *fullA = full + OZ_STAGES;                         // producers: Y written
+  uint64_t *empty = fullA + OZ_STAGES;                        // MMAs of the stage retired
+  uint64_t *acc_full = empty + OZ_STAGES;
+  uint64_t *acc_empty = acc_full + 1;
+  uint64_t *mma_done = acc_empty + 1;
+  uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NPROD = 32 * F2_WARPS;
+
+  // ---- tile of the G block (as in k_ozaki_gemm<1>) ----
+  int t = blockIdx.x, rt = 0, ct = 0, bblk;
+  int64_t rowoff = 0;
+  for (bblk = 0; bblk < P.g.nbl; ++bblk) {
+    const int nrt = (int)cdiv64(P.g.rows(bblk), OZ_BM), nct = (int)cdiv64(P.g.cols(bblk), OZ_BN);
+    if (t < nrt * nct) {
+      rt = t / nct;
+      ct = t % nct;
+      break;
+    }
+    t -= nrt * nct;
+    rowoff += P.g.rows(bblk);
+  }
+  if (bblk >= P.g.nbl) return;
+  const int ntile = g_tile_width(P.g.cols(bblk));
+  const int64_t lrow0 = (int64_t)rt * OZ_BM;       // first row of the tile inside block b
+  const int64_t a_row0 = rowoff + lrow0;           // ... in the full Y row order
+  const int64_t b_row0 = (int64_t)bblk * P.g.nbp + (int64_t)ct * ntile;
+  const int64_t R = min((int64_t)OZ_BM, P.g.rows(bblk) - lrow0);
+  const int64_t C = min((int64_t)ntile, P.g.cols(bblk) - (int64_t)ct * ntile);
+  const int64_t out_base = P.g.offset(bblk) + lrow0 * P.g.cols(bblk) + (int64_t)ct * ntile;
+  const int nbp = P.nbp, P2 = P.g.P2;
+  const int a_first = (int)(lrow0 / P2);
+  const int ngrp = f2_groups(P.g, bblk, rt);     // groups a_first .. a_first + ngrp - 2, then b
+  const CUtensorMap *tmB = &bmaps.m[ntile / 16 - 1];
+  const uint32_t stage_bytes = (uint32_t)(OZ_SLICES * ntile * OZ_ROWB + ngrp * nbp * 256);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&fullA[s], NPROD);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(acc_full, 1);
+    ptx::mbar_init(acc_empty, NPROD);
+    ptx::mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_slot, 512);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ksteps = P.Kpad / OZ_BK;
+  const int steps_per_chunk = OZ_KC / OZ_BK;
+
+  if (warp == 0) {
+    // ================= TMA: B slices and the M~ groups =================
+    if (lane == 0) {
+      ptx::prefetch_tmap(tmB);
+      ptx::prefetch_tmap(&tmM);
+      int issued = 0;
+      for (int i = 0; i < ksteps; ++i) {
+        const int s = i % OZ_STAGES;
+        const uint32_t ph = (uint32_t)((i / OZ_STAGES) & 1);
+        if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_cycles)) break;
+        unsigned char *st = sm + s * F2_STAGE;
+        ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
+        ptx::tma_load_3d(st + OZ_A_BYTES, tmB, &full[s], i * OZ_BK, (int)b_row0, 0);
+        unsigned char *mt = st + OZ_A_BYTES + OZ_B_BYTES;
+        for (int gidx = 0; gidx < ngrp; ++gidx) {
+          const int grow = (gidx == ngrp - 1 ? bblk : a_first + gidx) * nbp;
+          ptx::tma_load_2d(mt + gidx * nbp * 256, &tmM, &full[s], i * OZ_BK, grow);
+        }
+        ++issued;
+      }
+      if (*abort_flag) {  // let the copies in flight land before the CTA ends
+        for (int j = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); j < issued; ++j) {
+          volatile int dummy = 0;
+          ptx::mbar_wait(&full[j % OZ_STAGES], (uint32_t)((j / OZ_STAGES) & 1), &dummy, OZ_WAIT_CYCLES);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ================= MMA issue (runs of slice products, see mma_plans) =================
+    if (lane == 0) {
+      const uint32_t idesc0 = ptx::idesc_bf16_f32(OZ_BM, 0);
+      const uint32_t *plan = P.plan[ntile / 16 - 1];  // read from the parameter space per MMA
+      const int nruns = (int)(plan[0] & 0xffu);
+      const uint32_t sbase = ptx::smem_u32(sm);
+      int chunk = 0;
+      for (int i = 0; i < ksteps; ++i) {
+        const int s = i % OZ_STAGES;
+        const uint32_t ph = (uint32_t)((i / OZ_STAGES) & 1);
+        const bool chunk_start = (i % steps_per_chunk) == 0;
+        if (chunk_start && chunk > 0) {
+          if (!ptx::mbar_wait(acc_empty, (uint32_t)((chunk - 1) & 1), abort_flag, P.wait_cycles)) break;
+        }
+        if (!ptx::mbar_wait(&full[s], ph, abort_flag, P.wait_cycles)) break;
+        if (!ptx::mbar_wait(&fullA[s], ph, abort_flag, P.wait_cycles)) break;
+        ptx::tc_fence_after();
+        const uint32_t a0 = sbase + s * F2_STAGE;
+        const uint64_t ad0 = ptx::smem_desc(a0, 16, 8 * OZ_ROWB, ptx::SW_64B);
+        const uint64_t bd0 = ptx::smem_desc(a0 + OZ_A_BYTES, 16, 8 * OZ_ROWB, ptx::SW_64B);
+#pragma unroll
+        for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+          for (int r = 0; r < nruns; ++r) {
+            const uint32_t e = plan[1 + r];
+            const uint32_t sa = e & 15u, sb = (e >> 4) & 15u, n = (e >> 8) & 15u, acc = (e >> 12) & 15u;
+            const bool first = chunk_start && kk == 0 && ((e >> 16) & 1u);
+            const uint32_t N = n * (uint32_t)ntile;
+            const uint64_t ad = ad0 + (uint64_t)((sa * OZ_BM * OZ_ROWB + kk * 32) >> 4);
+            const uint64_t bd = bd0 + (uint64_t)((sb * (uint32_t)ntile * OZ_ROWB + kk * 32) >> 4);
+            ptx::mma_bf16(tmem + acc * (uint32_t)ntile, ad, bd, idesc0 | ((N >> 3) << 17), first ? 0u : 1u);
+          }
+        }
+        ptx::mma_commit(&empty[s]);
+        const bool chunk_end = ((i + 1) % steps_per_chunk) == 0 || i + 1 == ksteps;
+        if (chunk_end) {
+          ptx::mma_commit(acc_full);
+          ++chunk;
+        }
+      }
+      ptx::mma_commit(mma_done);
+      volatile int dummy = 0;
+      ptx::mbar_wait(mma_done, 0, &dummy, OZ_WAIT_CYCLES);
+    }
+  } else {
+    // ================= Y production and drains =================
+    const int pw = warp - 2;                    // producer warp 0..15
+    const int kp = lane & 15;                   // slice pair of the K step (slices 2kp, 2kp+1)
+    // rows of this thread: 32 j + 2 pw + (lane >> 4), j = 0..3; per row the
+    // M~ tile columns of (a,u), (b,v), (a,v), (b,u), one byte each
+    uint32_t cols4[4];
+    unsigned rmask = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = 32 * j + 2 * pw + (lane >> 4);
+      const int64_t lr = lrow0 + r;
+      int a = a_first, u = 0, v = 0;
+      if (r < R) {
+        rmask |= 1u << j;
+        a = (int)(lr / P2);
+        pair_decode((int)(lr % P2), u, v);
+      }
+      const int ga = (a - a_first) * nbp, gb = (ngrp - 1) * nbp;
+      cols4[j] = (uint32_t)(ga + u) | (uint32_t)(gb + v) << 8 | (uint32_t)(ga + v) << 16 | (uint32_t)(gb + u) << 24;
+    }
+    // drain role: TMEM lane quarter of this warp, one quarter of the columns
+    const int quarter = warp & 3, cq = pw >> 2;
+    const int erow = quarter * 32 + lane, col0 = cq * 32;
+    const int emA = *P.emaxY, emB = *P.emaxB;
+    const int ebias = emA + emB + 40;
+    const int nacc = (int)((P.plan[ntile / 16 - 1][0] >> 8) & 0xffu);
+    float hi[32], lo[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0.f;
+    int rexp[4];  // per-row exponent of the current chunk
+    const uint32_t sbase = ptx::smem_u32(sm);
+    int drained = 0;
+    bool ok = true;
+
+    auto drain = [&](int ch) -> bool {
+      const bool got = ptx::mbar_wait(acc_full, (uint32_t)(ch & 1), abort_flag, P.wait_cycles);
+      if (!__all_sync(0xffffffffu, got)) return false;
+      ptx::tc_fence_after();
+      const int ea = (erow < R) ? P.eY[(int64_t)ch * P.rowsY + a_row0 + erow] : -100000;
+      const float fa = pow2f_or0(ea - emA);
+      const int64_t bcol = b_row0 + col0 + lane;
+      const int eb = (col0 + lane < ntile && bcol < P.rowsB) ? __ldg(P.eB + (int64_t)ch * P.rowsB + bcol)
+                                                             : -100000;
+      const float fbl = pow2f_or0(eb - emB - 2 * OZ_BETA - 40);
+      const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+      for (int cb = 0; cb < 8; ++cb) {
+        if (col0 + cb * 4 >= ntile) break;  // warp-uniform
+        float v0[4], v1[4], v2[4], v3[4], v4[4];
+        const uint32_t cc = (uint32_t)(col0 + cb * 4);
+        const uint32_t w = (uint32_t)ntile;
+        ptx::tmem_ld4(tl + cc, v0);
+        ptx::tmem_ld4(tl + w + cc, v1);
+        ptx::tmem_ld4(tl + 2 * w + cc, v2);
+        if (nacc > 3) ptx::tmem_ld4(tl + 3 * w + cc, v3);
+        if (nacc > 4) ptx::tmem_ld4(tl + 4 * w + cc, v4);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = cb * 4 + k;
+          float rest = v2[k];
+          if (nacc > 3) rest += v3[k];
+          if (nacc > 4) rest += v4[k];
+          const float f = fa * __shfl_sync(0xffffffffu, fbl, c);
+          float s = v0[k] + v1[k];
+          float bb = s - v0[k];
+          float e = (v0[k] - (s - bb)) + (v1[k] - bb);
+          e += rest;
+          df_add(hi[c], lo[c], s * f, e * f);
+        }
+      }
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(acc_empty);
+      return true;
+    };
+
+    for (int i = 0; i < ksteps && ok; ++i) {
+      const int ch = i / steps_per_chunk, ic = i % steps_per_chunk;
+      if (ch >= 1 && ic == OZ_STAGES && drained == ch - 1) {
+        if (!drain(ch - 1)) { ok = false; break; }
+        drained = ch;
+      }
+      if (ic == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int r = 32 * j + 2 * pw + (lane >> 4);
+          rexp[j] = ((rmask >> j) & 1u) ? P.eY[(int64_t)ch * P.rowsY + a_row0 + r] : -100000;
+        }
+      }
+      const int s = i % OZ_STAGES;
+      const uint32_t ph = (uint32_t)((i / OZ_STAGES) & 1);
+      bool got = ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_cycles);
+      if (got) got = ptx::mbar_wait(&full[s], ph, abort_flag, P.wait_cycles);
+      if (!__all_sync(0xffffffffu, got)) { ok = false; break; }  // the warp goes on or stops together
+      const float4 *mt = reinterpret_cast<const float4 *>(sm + s * F2_STAGE + OZ_A_BYTES + OZ_B_BYTES);
+      const uint32_t abase = sbase + s * F2_STAGE;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 32 * j + 2 * pw + (lane >> 4);
+        float2 q[OZ_SLICES];
+        if ((rmask >> j) & 1u) {
+          // (h, l, h', l') of slices 2kp and 2kp+1 of each factor
+          const uint32_t cj = cols4[j];
+          const float4 au = mt[(cj & 255u) * 16 + kp], bv = mt[((cj >> 8) & 255u) * 16 + kp];
+          const float4 av = mt[((cj >> 16) & 255u) * 16 + kp], bu = mt[(cj >> 24) * 16 + kp];
+          float2 hy, ly;
+          y_value2(make_float2(au.x, au.z), make_float2(au.y, au.w), make_float2(bv.x, bv.z),
+                   make_float2(bv.y, bv.w), make_float2(av.x, av.z), make_float2(av.y, av.w),
+                   make_float2(bu.x, bu.z), make_float2(bu.y, bu.w), hy, ly);
+          // scale 2^(BETA - e) as two exact factors (0 for an all-zero row)
+          const int e = rexp[j], k = OZ_BETA - e;
+          const float f1 = e < -99999 ? 0.f : pow2f(k / 2), f2v = e < -99999 ? 0.f : pow2f(k - k / 2);
+          const float2 fx = make_float2(f1, f1), fy = make_float2(f2v, f2v);
+          hy = __fmul2_rn(__fmul2_rn(hy, fx), fy);
+          ly = __fmul2_rn(__fmul2_rn(ly, fx), fy);
+          split_hl2(hy, ly, q);
+        } else {
+#pragma unroll
+          for (int sl = 0; sl < OZ_SLICES; ++sl) q[sl] = make_float2(0.f, 0.f);
+        }
+        // 64-byte swizzled row of each slice: granule kp/4 ^ ((r >> 1) & 3)
+        const uint32_t gran = (uint32_t)((kp >> 2) ^ ((r >> 1) & 3));
+        const uint32_t addr = abase + (uint32_t)r * OZ_ROWB + (gran << 4) + (uint32_t)(kp & 3) * 4;
+#pragma unroll
+        for (int sl = 0; sl < OZ_SLICES; ++sl)
+          asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr + sl * OZ_BM * OZ_ROWB), "r"(bf16x2_bits(q[sl]))
+                       : "memory");
+      }
+      ptx::fence_proxy_async_smem();
+      ptx::mbar_arrive(&fullA[s]);
+    }
+    const int nch = P.nchunks;
+    for (int c = drained; ok && c < nch; ++c) {
+      if (!drain(c)) { ok = false; break; }
+    }
+    if (ok && !*abort_flag && erow < R) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int col = col0 + c;
+        if (col >= C) continue;
+        double *d = P.G + out_base + (int64_t)erow * P.g.cols(bblk) + col;
+        *d += ldexp((double)hi[c] + (double)lo[c], ebias);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(P.err, ERR_TIMEOUT);
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 512);
+  }
+}
+
 static int64_t y_rows(const SepShape &s) {
   const int64_t P2 = (int64_t)s.nbp * (s.nbp + 1) / 2;
   return P2 * s.nbl * (s.nbl + 1) / 2;
@@ -1404,12 +1746,41 @@ size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
   b += up256((size_t)Kpad * nblp * 8) + up256((size_t)nch * nblp * 8); // Mdf, column maxima
   b += up256((size_t)nch * nblp * 8) + up256((size_t)nch * nblp * 4);  // mxW, eB
   b += up256((size_t)OZ_SLICES * nblp * Kpad * 2);                     // Bt
-  if (variant == TC_TRIPLE_MATERIALISED) {
-    const int64_t rowsY = y_rows(s);
-    b += up256((size_t)nch * rowsY * 4);                                // eY
-    b += up256((size_t)OZ_SLICES * rowsY * Kpad * 2);                   // Y slices
-  }
+  if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_FUSED2)
+    b += up256((size_t)nch * y_rows(s) * 4);                            // eY
+  if (variant == TC_TRIPLE_MATERIALISED)
+    b += up256((size_t)OZ_SLICES * y_rows(s) * Kpad * 2);               // Y slices
   return b;
+}
+
+bool tc_fused2_fits(int nbl, int nbp) {
+  const GLayout g = make_glayout(nbl, nbp);
+  for (int b = 0; b < nbl; ++b)
+    for (int rt = 0; rt < (int)cdiv64(g.rows(b), OZ_BM); ++rt)
+      if (f2_groups(g, b, rt) * nbp > F2_MAX_COLS) return false;
+  return true;
+}
+
+// 2-D map over M~ ([nblp][Kpad] double-FP32 pairs as 8-byte elements), box of
+// 32 slices x nbp columns: one group of columns (a, 0..nbp-1) per load.
+static int make_mt_map(CUtensorMap *m, const void *base, int64_t rows, int Kpad, int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) {
+    snprintf(g_tc_err, sizeof g_tc_err, "cuTensorMapEncodeTiled unavailable");
+    return MODAL_EUNSUPPORTED;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kpad * 8};
+  cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    snprintf(g_tc_err, sizeof g_tc_err, "cuTensorMapEncodeTiled (M~) failed (%d)", (int)r);
+    return MODAL_EINVAL;
+  }
+  return MODAL_OK;
 }
 
 int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
@@ -1443,6 +1814,48 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
         K, Kpad, nblp, s.n_mu, x0, M, om, xw, colmax, Mdf, mxW, eB, Bt, words + 3, words, absM ? 1 : 0);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  if (variant == TC_TRIPLE_FUSED2) {
+    // Y formed in the GEMM's shared-memory stages; only the row exponents first
+    const int64_t rowsY = y_rows(s);
+    int *eY = (int *)((char *)Bt + up256((size_t)OZ_SLICES * nblp * Kpad * 2));
+    {
+      ProfScope ps(prof, "tc_y_exp", st);
+      k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(rowsY, s.nbp, nblp, P2, mxW,
+                                                                                  eY, words + 4);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+    CUtensorMap tm;
+    BMaps tb;
+    const GLayout gl = make_glayout(s.nbl, s.nbp);
+    unsigned used = 0;
+    for (int b = 0; b < s.nbl; ++b) used |= 1u << (g_tile_width(gl.cols(b)) / 16 - 1);
+    if (int r = make_mt_map(&tm, Mdf, nblp, Kpad, s.nbp)) return r;
+    if (int r = make_bmaps(&tb, Bt, nblp, Kpad, used)) return r;
+    Fused2Params F{};
+    fill_mma_plans(F.plan);
+    F.rowsB = nblp;
+    F.rowsY = rowsY;
+    F.Kpad = Kpad;
+    F.nchunks = nch;
+    F.nbp = s.nbp;
+    F.eY = eY;
+    F.eB = eB;
+    F.emaxY = words + 4;
+    F.emaxB = words + 3;
+    F.G = G;
+    F.g = gl;
+    F.err = words;
+    F.wait_cycles = wait_cycles;
+    int64_t tiles = 0;
+    for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(gl.rows(b), OZ_BM) * cdiv64(gl.cols(b), OZ_BN);
+    if ((e = cudaFuncSetAttribute(k_ozaki_triple_fused2, cudaFuncAttributeMaxDynamicSharedMemorySize, F2_SMEM)) !=
+        cudaSuccess)
+      goto cuda_fail;
+    ProfScope ps(prof, "tc_gemm_triple", st);
+    k_ozaki_triple_fused2<<<(unsigned)tiles, F2_THREADS, F2_SMEM, st>>>(tm, tb, F);
+    if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+    return MODAL_OK;
+  }
   if (variant == TC_TRIPLE_MATERIALISED) {
     // Y slices through HBM, then the TMA-fed GEMM for both operands
     const int64_t rowsY = y_rows(s);
@@ -1483,7 +1896,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     P.err = words;
     P.g = make_glayout(s.nbl, s.nbp);
     P.wait_cycles = wait_cycles;
-    fill_mma_plans(P);
+    fill_mma_plans(P.plan);
     int64_t tiles = 0;
     for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(P.g.rows(b), OZ_BM) * cdiv64(P.g.cols(b), OZ_BN);
     if ((e = cudaFuncSetAttribute(k_ozaki_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=

@@ -8,6 +8,9 @@ namespace modal {
 // triple-product variants: the Y operand through HBM, or formed in shared memory
 constexpr int TC_TRIPLE_MATERIALISED = 0;
 constexpr int TC_TRIPLE_FUSED = 1;
+constexpr int TC_TRIPLE_FUSED2 = 2;
+// whether the second fused form can serve a basis (its M~ tile per stage)
+bool tc_fused2_fits(int nbl, int nbp);
 // scratch for l-contraction chunks of nxl radial points and triple-product
 // chunks of nxc points (nxc <= nxl)
 size_t tc_scratch_bytes(const SepShape &s, int nxl, int nxc, int variant);

@@ -110,3 +110,19 @@ def test_tc_fused_variant(mg, shape, split_k):
     mg.handle_status(handle=h)
     assert normwise(g, oracle.separable(P)) < TOL_MIXED
     h.close()
+
+
+@pytest.mark.parametrize("shape", [(48, 5, 5, 24), (60, 12, 11, 7), (130, 4, 4, 9), (300, 10, 10, 6),
+                                   (37, 21, 21, 3)])
+def test_tc_fused2_variant(mg, shape):
+    """Y formed by sixteen warps in the GEMM's shared-memory stages from a
+    TMA-staged M~ tile (MODAL_OPT_TC_TRIPLE_FUSED = 2), against the oracle."""
+    lmax, nbl, nbp, nx = shape
+    P = syn.make_problem(lmax, nbl, nx, seed=19, nb_prim=nbp)
+    h = mg.Handle()
+    mg.set_option(mg.OPT_TC_TRIPLE_FUSED, 2, handle=h)
+    g = mg.project_separable(mg.DeviceProblem.from_host(P, handle=h), precision=mg.PREC_OZAKI_BF16,
+                             handle=h)
+    mg.handle_status(handle=h)
+    assert normwise(g, oracle.separable(P)) < TOL_MIXED
+    h.close()
