@@ -6,50 +6,86 @@
 namespace modal {
 
 // ---------------------------------------------------------------------------
-// a1: Gauss-Legendre nodes/weights (Section 2.2).  One thread per root pair
-// (+-mu).  Newton in FP64 from the usual cosine guess, then two Newton steps
-// with P_n, P_{n-1} evaluated in double-double by the three-term recurrence
-//   (k+1) P_{k+1} = (2k+1) mu P_k - k P_{k-1},
-// then w = 2 / ((1 - mu^2) P_n'(mu)^2), P_n' = n (mu P_n - P_{n-1})/(mu^2-1),
-// in double-double, each rounded once to FP64.  Output ascending.
+// a1: Gauss-Legendre nodes/weights (Section 2.2).  One warp per root pair
+// (+-mu).  The three-term recurrence
+//   (k+1) P_{k+1} = (2k+1) mu P_k - k P_{k-1},   i.e.
+//   [P_{k+1}, P_k]^T = M_k [P_k, P_{k-1}]^T,  M_k = [[a_k mu, -b_k], [1, 0]],
+// with a_k = (2k+1)/(k+1), b_k = k/(k+1), is evaluated as the ordered product
+// of the M_k: each lane multiplies the matrices of its segment of k, and a
+// shuffle tree multiplies the 32 segment products in order, so the latency
+// of one evaluation is ~n/32 steps instead of n.  Newton in FP64 from the
+// usual cosine guess, then one evaluation of P_n, P_{n-1} in double-double
+// at the FP64 root x0 gives the last correction d = P_n / P_n' (node
+// x0 - d) and P_n'(x0); the derivative at the node follows from the Legendre
+// equation, P_n'' = (2 x P_n' - n(n+1) P_n)/(1 - x^2), as P_n'(x0) - d P_n''.
+// The weight 2 / ((1 - x^2) P_n'(x)^2) is formed from these in double-double
+// and rounded once.  The a_k, b_k are tabulated per block in shared memory in
+// double-double.  Output ascending.
 // ---------------------------------------------------------------------------
-// Recurrence coefficients a_k = (2k+1)/(k+1), b_k = k/(k+1) (k >= 1) are
-// tabulated once per block in shared memory in double-double, so the inner
-// loops carry no division:  P_{k+1} = a_k mu P_k - b_k P_{k-1}.
-constexpr int GL_TPB = 8;  // few threads per block: spread the roots over all SMs
+constexpr int GL_WARPS = 4;  // roots per block
 
-__device__ __forceinline__ void leg_pair_tab_d(int n, double x, const dd *ca, const dd *cb, double &pn,
-                                               double &pm) {
-  double p0 = 1.0, p1 = x;
-  for (int k = 1; k < n; ++k) {
-    double p2 = fma(ca[k].hi * x, p1, -cb[k].hi * p0);
-    p0 = p1;
-    p1 = p2;
-  }
-  pn = p1;
-  pm = p0;
+struct M2 {
+  double a, b, c, d;  // [[a, b], [c, d]]
+};
+struct M2dd {
+  dd a, b, c, d;
+};
+__device__ __forceinline__ M2 m2_mul(const M2 &x, const M2 &y) {  // x y
+  return {fma(x.a, y.a, x.b * y.c), fma(x.a, y.b, x.b * y.d), fma(x.c, y.a, x.d * y.c), fma(x.c, y.b, x.d * y.d)};
+}
+__device__ __forceinline__ M2dd m2dd_mul(const M2dd &x, const M2dd &y) {
+  return {dd_add(dd_mul(x.a, y.a), dd_mul(x.b, y.c)), dd_add(dd_mul(x.a, y.b), dd_mul(x.b, y.d)),
+          dd_add(dd_mul(x.c, y.a), dd_mul(x.d, y.c)), dd_add(dd_mul(x.c, y.b), dd_mul(x.d, y.d))};
+}
+__device__ __forceinline__ double shfl_up_d(double v, int off) { return __shfl_up_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ dd shfl_up_dd(dd v, int off) { return {shfl_up_d(v.hi, off), shfl_up_d(v.lo, off)}; }
+
+// k range of this lane's segment of 1 .. n-1
+__device__ __forceinline__ void gl_segment(int n, int lane, int &k0, int &k1) {
+  const int len = (n - 1 + 31) / 32;
+  k0 = 1 + lane * len;
+  k1 = min(n, k0 + len);
 }
 
-// P_n and P_{n-1} at a double x in double-double: the products are
-// double-double x double (cheaper than full double-double products).
-__device__ __forceinline__ void leg_pair_tab_dd_at(int n, double x, const dd *ca, const dd *cb, dd &pn, dd &pm) {
-  dd p0 = {1.0, 0.0}, p1 = {x, 0.0};
-  for (int k = 1; k < n; ++k) {
-    dd p2 = dd_sub(dd_mul(ca[k], dd_mul_d(p1, x)), dd_mul(cb[k], p0));
-    p0 = p1;
-    p1 = p2;
+// [P_n, P_{n-1}] at x (FP64): lane 31 returns them
+__device__ __forceinline__ void leg_pair_warp_d(int n, double x, const dd *ca, const dd *cb, int lane, double &pn,
+                                                double &pm) {
+  int k0, k1;
+  gl_segment(n, lane, k0, k1);
+  M2 t = {1.0, 0.0, 0.0, 1.0};
+  for (int k = k0; k < k1; ++k) {  // t = M_k t
+    const double ax = ca[k].hi * x, bk = cb[k].hi;
+    t = {fma(ax, t.a, -bk * t.c), fma(ax, t.b, -bk * t.d), t.a, t.b};
   }
-  pn = p1;
-  pm = p0;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {  // ordered product: higher k on the left
+    M2 lo = {shfl_up_d(t.a, off), shfl_up_d(t.b, off), shfl_up_d(t.c, off), shfl_up_d(t.d, off)};
+    if (lane >= off && ((lane + 1) & (2 * off - 1)) == 0) t = m2_mul(t, lo);
+  }
+  pn = fma(t.a, x, t.b);  // applied to [P_1, P_0] = [x, 1]
+  pm = fma(t.c, x, t.d);
 }
 
-// Each root: Tricomi's asymptotic start, FP64 Newton to ~1 ulp at x0, then
-// P_n(x0), P_{n-1}(x0) in double-double give the last Newton correction
-// d = P_n/P_n' (so the node is x0 - d to ~1e-30) and P_n'(x0); the
-// derivative at the node follows from the Legendre equation,
-// P_n'' = (2 x P_n' - n(n+1) P_n)/(1 - x^2), as P_n'(x) ~ P_n'(x0) - d P_n''(x0).
-// The weight 2 / ((1 - x^2) P_n'(x)^2) is formed from these and rounded once.
-__global__ void __launch_bounds__(GL_TPB) k_gl_nodes(int n, double *__restrict__ mu, double *__restrict__ om) {
+__device__ __forceinline__ void leg_pair_warp_dd(int n, double x, const dd *ca, const dd *cb, int lane, dd &pn,
+                                                 dd &pm) {
+  int k0, k1;
+  gl_segment(n, lane, k0, k1);
+  const dd one = {1.0, 0.0}, zero = {0.0, 0.0};
+  M2dd t = {one, zero, zero, one};
+  for (int k = k0; k < k1; ++k) {
+    const dd ax = dd_mul_d(ca[k], x);
+    t = {dd_sub(dd_mul(ax, t.a), dd_mul(cb[k], t.c)), dd_sub(dd_mul(ax, t.b), dd_mul(cb[k], t.d)), t.a, t.b};
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    M2dd lo = {shfl_up_dd(t.a, off), shfl_up_dd(t.b, off), shfl_up_dd(t.c, off), shfl_up_dd(t.d, off)};
+    if (lane >= off && ((lane + 1) & (2 * off - 1)) == 0) t = m2dd_mul(t, lo);
+  }
+  pn = dd_add(dd_mul_d(t.a, x), t.b);
+  pm = dd_add(dd_mul_d(t.c, x), t.d);
+}
+
+__global__ void __launch_bounds__(32 * GL_WARPS) k_gl_nodes(int n, double *__restrict__ mu, double *__restrict__ om) {
   extern __shared__ dd coef[];
   dd *ca = coef, *cb = coef + n;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -57,27 +93,35 @@ __global__ void __launch_bounds__(GL_TPB) k_gl_nodes(int n, double *__restrict__
     cb[k] = dd_div_d({(double)k, 0.0}, (double)(k + 1));
   }
   __syncthreads();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int half = (n + 1) / 2;
-  if (i >= half) return;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * GL_WARPS + (threadIdx.x >> 5);  // root pair of this warp
+  const int half = (n + 1) / 2;
+  if (i >= half) return;  // warp-uniform
   if (n == 1) {
-    mu[0] = 0.0;
-    om[0] = 2.0;
+    if (lane == 0) {
+      mu[0] = 0.0;
+      om[0] = 2.0;
+    }
     return;
   }
   const double nn = (double)n;
   double x = (1.0 - (nn - 1.0) / (8.0 * nn * nn * nn)) * cos(MODAL_PI * (4.0 * i + 3.0) / (4.0 * nn + 2.0));
   for (int it = 0; it < 12; ++it) {
     double pn, pm;
-    leg_pair_tab_d(n, x, ca, cb, pn, pm);
-    double dp = nn * (x * pn - pm) / (x * x - 1.0);
-    double dx = pn / dp;
+    leg_pair_warp_d(n, x, ca, cb, lane, pn, pm);
+    double dx = 0.0;
+    if (lane == 31) {
+      const double dp = nn * (x * pn - pm) / (x * x - 1.0);
+      dx = pn / dp;
+    }
+    dx = __shfl_sync(0xffffffffu, dx, 31);
     x -= dx;
-    if (fabs(dx) <= 1e-15 * fabs(x)) break;
+    if (fabs(dx) <= 1e-15 * fabs(x)) break;  // warp-uniform
   }
   if ((n & 1) && i == n / 2) x = 0.0;  // exact centre node of an odd rule
   dd pn, pm;
-  leg_pair_tab_dd_at(n, x, ca, cb, pn, pm);
+  leg_pair_warp_dd(n, x, ca, cb, lane, pn, pm);
+  if (lane != 31) return;
   const dd one = {1.0, 0.0};
   const dd X0 = {x, 0.0};
   const dd x2m1 = dd_sub(dd_mul_d(X0, x), one);                             // x0^2 - 1 (exact-ish)
@@ -203,7 +247,7 @@ cudaError_t launch_gl_nodes(int n, double *mu, double *om, cudaStream_t st) {
   if (smem > 200 * 1024) return cudaErrorInvalidValue;  // n > 6400: not supported
   cudaError_t e = cudaFuncSetAttribute(k_gl_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gl_nodes<<<cdiv(half, GL_TPB), GL_TPB, smem, st>>>(n, mu, om);
+  k_gl_nodes<<<cdiv(half, GL_WARPS), 32 * GL_WARPS, smem, st>>>(n, mu, om);
   return cudaGetLastError();
 }
 cudaError_t launch_legendre_table(int n_mu, const double *mu, int l_min, int l_max,

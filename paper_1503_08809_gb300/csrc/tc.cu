@@ -28,6 +28,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -525,15 +526,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static const EncodeTiledFn fn = [] {  // resolved once (thread-safe static initialisation)
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    return (EncodeTiledFn) nullptr;
+  }();
   return fn;
 }
 
@@ -616,8 +617,8 @@ struct PlanSearch {
 
 static void fill_mma_plans(uint32_t (&dst)[OZ_BN / 16][1 + OZ_PLAN_MAX]) {
   static uint32_t plans[OZ_BN / 16][1 + OZ_PLAN_MAX];
-  static bool done = false;
-  if (!done) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     for (int i = 0; i < OZ_BN / 16; ++i) {
       PlanSearch ps;
       ps.w = 16 * (i + 1);
@@ -638,8 +639,7 @@ static void fill_mma_plans(uint32_t (&dst)[OZ_BN / 16][1 + OZ_PLAN_MAX]) {
       plans[i][0] = (uint32_t)ps.best_n | (uint32_t)ps.best_used << 8;
       for (int r = 0; r < ps.best_n; ++r) plans[i][1 + r] = ps.best_plan[r];
     }
-    done = true;
-  }
+  });
   memcpy(dst, plans, sizeof plans);
 }
 
