@@ -241,6 +241,7 @@ struct OzParams {
   int *err;
   // OUT_MODE 0
   int n_mu, nbl, nbp;
+  int rows_per_cta;       // row tiles each CTA runs one after another (OUT_MODE 0)
   // OUT_MODE 1
   GLayout g;
   long long wait_cycles;
@@ -290,10 +291,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   int64_t out_base = 0;
   int bblk = 0;
   int ntile = OZ_BN;  // MMA N of this tile (a multiple of 16)
+  int ntt = 1;  // tiles of this CTA (OUT_MODE 0: row tiles of one column tile)
   if (OUT_MODE == 0) {
     // column tiles vary fastest, so the CTAs that share a row tile of A run
-    // together and A is read from HBM about once
-    a_row0 = (int64_t)blockIdx.y * OZ_BM;
+    // together and A is read from HBM about once; each CTA then moves on to
+    // the next row tile, so its set-up, pipeline fill and last drain are
+    // shared by several tiles and overlap the neighbouring tile's work
+    const int64_t rt0 = (int64_t)blockIdx.y * P.rows_per_cta;
+    ntt = (int)min((int64_t)P.rows_per_cta, cdiv64(P.rowsA, OZ_BM) - rt0);
+    a_row0 = rt0 * OZ_BM;
     b_row0 = (int64_t)blockIdx.x * OZ_BN;
     R = min((int64_t)OZ_BM, P.rowsA - a_row0);
     C = min((int64_t)OZ_BN, P.rowsB - b_row0);
@@ -350,19 +356,27 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       ptx::prefetch_tmap(&tmA);
       ptx::prefetch_tmap(tmB);
       int issued = 0;
-      // A tiles are pulled into L2 OZ_PREFETCH stages ahead of their loads,
-      // so that the two-stage ring waits on L2 rather than on HBM latency
-      for (int i = 0; i < OZ_PREFETCH && i < ksteps; ++i) ptx::tma_prefetch_3d(&tmA, i * OZ_BK, (int)a_row0, 0);
-      for (int i = 0; i < ksteps; ++i) {
-        const int s = i % OZ_STAGES;
-        const uint32_t ph = (uint32_t)((i / OZ_STAGES) & 1);
-        if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_cycles)) break;
-        unsigned char *st = sm + s * OZ_STAGE_BYTES;
-        ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
-        ptx::tma_load_3d(st, &tmA, &full[s], i * OZ_BK, (int)a_row0, 0);
-        ptx::tma_load_3d(st + OZ_A_BYTES, tmB, &full[s], i * OZ_BK, (int)b_row0, 0);
-        if (i + OZ_PREFETCH < ksteps) ptx::tma_prefetch_3d(&tmA, (i + OZ_PREFETCH) * OZ_BK, (int)a_row0, 0);
-        ++issued;
+      bool stop = false;
+      for (int tt = 0; tt < ntt && !stop; ++tt) {
+        const int ar = (int)(a_row0 + (int64_t)tt * OZ_BM);
+        // A tiles are pulled into L2 OZ_PREFETCH stages ahead of their loads,
+        // so that the two-stage ring waits on L2 rather than on HBM latency
+        for (int i = 0; i < OZ_PREFETCH && i < ksteps; ++i) ptx::tma_prefetch_3d(&tmA, i * OZ_BK, ar, 0);
+        for (int i = 0; i < ksteps; ++i) {
+          const int g = tt * ksteps + i;  // step count of the CTA: stage and phase
+          const int s = g % OZ_STAGES;
+          const uint32_t ph = (uint32_t)((g / OZ_STAGES) & 1);
+          if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_cycles)) {
+            stop = true;
+            break;
+          }
+          unsigned char *st = sm + s * OZ_STAGE_BYTES;
+          ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
+          ptx::tma_load_3d(st, &tmA, &full[s], i * OZ_BK, ar, 0);
+          ptx::tma_load_3d(st + OZ_A_BYTES, tmB, &full[s], i * OZ_BK, (int)b_row0, 0);
+          if (i + OZ_PREFETCH < ksteps) ptx::tma_prefetch_3d(&tmA, (i + OZ_PREFETCH) * OZ_BK, ar, 0);
+          ++issued;
+        }
       }
       // on abort: wait (bounded) for the copies in flight before anyone frees smem
       if (*abort_flag) {
@@ -382,10 +396,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
       for (int r = 0; r < OZ_PLAN_MAX; ++r) run[r] = plan[1 + r];
       const uint32_t sbase = ptx::smem_u32(sm);
-      int chunk = 0;
-      for (int i = 0; i < ksteps; ++i) {
-        const int s = i % OZ_STAGES;
-        const uint32_t ph = (uint32_t)((i / OZ_STAGES) & 1);
+      int chunk = 0;  // chunks of the CTA, over all its tiles
+      const int nsteps = ntt * ksteps;
+      for (int g = 0; g < nsteps; ++g) {
+        const int i = g % ksteps;  // step inside the tile
+        const int s = g % OZ_STAGES;
+        const uint32_t ph = (uint32_t)((g / OZ_STAGES) & 1);
         const bool chunk_start = (i % steps_per_chunk) == 0;
         if (chunk_start && chunk > 0) {
           // accumulators must have been drained by the epilogue
@@ -414,7 +430,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
         }
         ptx::mma_commit(&empty[s]);  // stage s may be refilled once these MMAs retire
-        const bool chunk_end = ((i + 1) % steps_per_chunk) == 0 || i + 1 == ksteps;
+        const bool chunk_end = ((i + 1) % steps_per_chunk) == 0 || i + 1 == ksteps;  // per tile
         if (chunk_end) {
           ptx::mma_commit(acc_full);
           ++chunk;
@@ -436,20 +452,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int ebias = emA + emB + 40;
     const int nacc = (int)((P.plan[ntile / 16 - 1][0] >> 8) & 0xffu);
     float hi[64];  // high halves in registers, low halves in lo_s
+    bool ok = true;
+    for (int tt = 0; tt < ntt && ok; ++tt) {
+    const int64_t ar0 = a_row0 + (int64_t)tt * OZ_BM;  // this tile's first row of A
+    const int64_t Rt = OUT_MODE == 0 ? min((int64_t)OZ_BM, P.rowsA - ar0) : R;
 #pragma unroll
     for (int c = 0; c < 64; ++c) {
       hi[c] = 0.f;
       lo_s[(col0 + c) * OZ_BM + row] = 0.f;
     }
-    bool ok = true;
     for (int ch = 0; ch < P.nchunks; ++ch) {
+      const int cg = tt * P.nchunks + ch;  // chunk count of the CTA (barrier phase)
       // the whole warp goes on or gives up together (shuffles below)
-      const bool got = ptx::mbar_wait(acc_full, (uint32_t)(ch & 1), abort_flag, P.wait_cycles);
+      const bool got = ptx::mbar_wait(acc_full, (uint32_t)(cg & 1), abort_flag, P.wait_cycles);
       if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
       ptx::tc_fence_after();
       // the chunk's scale 2^(ea + eb - 2 BETA - ebias) = row factor x column factor;
       // lane i holds the column factors of columns col0 + i and col0 + 32 + i
-      const int ea = (a_row0 + row < P.rowsA) ? P.eA[(int64_t)ch * P.rowsA + a_row0 + row] : -100000;
+      const int ea = (ar0 + row < P.rowsA) ? P.eA[(int64_t)ch * P.rowsA + ar0 + row] : -100000;
       const float fa = pow2f_or0(ea - emA);
       float fbl[2];
 #pragma unroll
@@ -491,14 +511,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       ptx::tc_fence_before();
       ptx::mbar_arrive(acc_empty);
     }
-    if (ok && !*abort_flag && row < R) {
+    if (ok && !*abort_flag && row < Rt) {
 #pragma unroll  // full unroll keeps hi[]/lo[] in registers
       for (int c = 0; c < 64; ++c) {
         const int col = col0 + c;
         if (col >= C) continue;
         const double v = ldexp((double)hi[c] + (double)lo_s[(col0 + c) * OZ_BM + row], ebias);
         if (OUT_MODE == 0) {
-          const int64_t rA = a_row0 + row, rB = b_row0 + col;
+          const int64_t rA = ar0 + row, rB = b_row0 + col;
           const int j = (int)(rA / P.nbl), a = (int)(rA % P.nbl);
           const int xl = (int)(rB / P.nbp), p = (int)(rB % P.nbp);
           P.out[(((int64_t)xl * P.n_mu + j) * P.nbl + a) * P.nbp + p] = v;
@@ -508,6 +528,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
       }
     }
+    }  // tiles of the CTA
   }
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) atomicOr(P.err, ERR_TIMEOUT);
@@ -753,7 +774,12 @@ int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_
     if ((e = cudaFuncSetAttribute(k_ozaki_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
         cudaSuccess)
       goto cuda_fail;
-    dim3 grid((unsigned)cdiv64(rowsB, OZ_BN), (unsigned)cdiv64(rowsA, OZ_BM));
+    // row tiles per CTA: a few, keeping at least ~4 waves of CTAs
+    const int64_t nrt = cdiv64(rowsA, OZ_BM), nct = cdiv64(rowsB, OZ_BN);
+    int rpc = (int)(nrt * nct / (4 * 152));
+    rpc = rpc < 1 ? 1 : (rpc > 4 ? 4 : rpc);
+    P.rows_per_cta = rpc;
+    dim3 grid((unsigned)nct, (unsigned)cdiv64(nrt, rpc));
     ProfScope ps(prof, "tc_gemm_l", st);
     k_ozaki_gemm<0><<<grid, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
