@@ -40,7 +40,7 @@ typedef struct CUstream_st *modal_stream_t;
 #define MODAL_ENOMEM 2        /* device allocation for the handle's scratch failed */
 #define MODAL_ECUDA 3         /* a CUDA runtime/launch error (message has the CUDA text) */
 #define MODAL_ETIMEOUT 4      /* a bounded device-side wait gave up */
-#define MODAL_EUNSUPPORTED 5  /* valid request this build/device cannot serve */
+#define MODAL_EUNSUPPORTED 5  /* valid request the library or the device cannot serve */
 
 /* arithmetic of the separable path (modal_opts.precision) */
 #define MODAL_PREC_FP64 0        /* FP64 everywhere (CUDA cores) */

@@ -82,7 +82,7 @@ constexpr int PROMOTE_STEPS = 2;
 // ---------------------------------------------------------------------------
 // a5 (CUDA cores): M[xl][j][a][p] = sum_l A[j][l] q_a(l) q~_p(l, x0 + xl).
 // GEMM rows (j, a), columns (xl, p), K = l; the A operand A[j][l] q_a(l) is
-// formed while staging (R of the survey is never materialised).
+// formed while staging (the product table q_a q~_p over l is never materialised).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_contract_l(SepShape s, const double *__restrict__ A,

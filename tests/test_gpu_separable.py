@@ -1,7 +1,6 @@
 """GPU parity of the separable path (rows a1-a7) against the FP64 oracle,
 called through the C ABI.  FP64 tolerance: 1e-10 normwise
-(max |dGamma| / max |Gamma_ref|), the bar the spec problem statement
-sets for the FP64 path."""
+(max |dGamma| / max |Gamma_ref|), the accuracy required of the FP64 path."""
 from __future__ import annotations
 
 import math

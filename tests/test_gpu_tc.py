@@ -1,7 +1,7 @@
 """GPU parity of the tensor-core (tcgen05) form of the separable path: the
 l contraction and the triple product with exponent-aligned BF16 slices,
 against the FP64 oracle.  Tolerance for the mixed form: 1e-8 normwise (the
-spec bound for it), 1e-10 for the l contraction alone (M error)."""
+accuracy required of it), 1e-10 for the l contraction alone (M error)."""
 from __future__ import annotations
 
 import numpy as np
