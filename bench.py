@@ -42,7 +42,10 @@ TC_SLICE_PRODUCTS = 15       # BF16 slice products per useful MAC in the tensor-
 # capture (profiles/k_ozaki_gemm_triple_planck.md: n_x = 4 gives one launch
 # with the same K as every launch of the 500-point step).  Kept only while
 # the kernels are unchanged since that capture.
-NCU_TRAFFIC = {"tc_gemm_triple": 5.775e9 + 48.6e6, "tc_make_Y": 44.5e6 + 5.242e9}
+NCU_TRAFFIC = {"tc_gemm_triple": 5.795e9 + 48.3e6, "tc_make_Y": 44.5e6 + 5.245e9}
+# kernels inside one profiler scope (the library counts kernels; a roofline
+# divides the scope's time by its scope count)
+SCOPE_KERNELS = {"tc_make_Y": 2, "tc_prep_M": 2}
 
 
 def parse():
@@ -340,6 +343,8 @@ def kernel_roofline(name, rec, per_step, P, prec_name, peaks, src, steps, ms):
     """Achieved algorithmic work per launch / mean launch time against the
     measured peak of the unit that bounds the kernel (None if not modelled)."""
     nl, tot = rec
+    nl = max(1, nl // SCOPE_KERNELS.get(name, 1))
+    per_step = max(1, per_step // SCOPE_KERNELS.get(name, 1))
     avg_s = tot / nl * 1e-3
     g2 = P.nb_prim * (P.nb_prim + 1) // 2
     gsize = g2 * P.nb_prim * P.n_late          # useful MACs per slice of the triple product

@@ -31,7 +31,7 @@ def mg(gpu):
 
 
 # ---- a1: Gauss-Legendre nodes ----------------------------------------------
-@pytest.mark.parametrize("n", [1, 2, 3, 24, 73, 1501, 3001])
+@pytest.mark.parametrize("n", [1, 2, 3, 24, 31, 32, 33, 73, 1501, 3001, 6400])
 def test_gl_nodes_parity(mg, n):
     mu, om = mg.gl_nodes(n)
     mo, oo = oracle.gl_nodes(n) if n > 1 else (np.zeros(1), np.full(1, 2.0))
