@@ -6,7 +6,8 @@ leg may import this package.  It wraps ``modal_oracle.c`` (plain C, built by
 library.  Each wrapper names the passage of arXiv 1503.08809 it follows; the
 C file has the derivations.
 
-Parity status: all functions pinned by ``tests/test_oracle_pins.py`` except
+Parity status: all functions (including ``gram`` and ``full_gamma``) pinned by
+``tests/test_oracle_pins.py`` except
 ``direct(..., weight_mode=SMOOTH)`` on sparse grids (an approximation of the
 dense sum): parity unpinned there.
 """
@@ -15,6 +16,7 @@ from __future__ import annotations
 import ctypes
 import os
 from pathlib import Path
+from types import SimpleNamespace
 
 import numpy as np
 
@@ -172,6 +174,33 @@ def direct(P, l_grid=None, l_dw=None, weight_mode: int = EXACT, xw=None,
                           int(late.shape[0]), _pi(late), int(prim.shape[0]), _pi(prim),
                           _pd(g))
     return g
+
+
+def gram(P, w_gram, late=None) -> np.ndarray:
+    """Gram matrix <Q_n, Q_r> of the late basis (Appendix A: the inner product
+    with weight (h / v1 v2 v3)^2, applied to two late-time basis functions).
+
+    Q_r has the same form as the projected Q~ of Eq. 3D with q~(l, x) replaced
+    by q(l) and no radial integral, so this is ``direct`` (the dense
+    tetrahedral sum with the exact 3j^2) on a problem whose projected basis is
+    q itself at one radial point of unit weight, with the l weight
+    w_gram = (2l+1) / v_l^2 in place of w_l = (2l+1) / (v_l sqrt(C_l))."""
+    late = _i32(P.late_modes if late is None else late)
+    Pg = SimpleNamespace(l_min=P.l_min, l_max=P.l_max, nb_late=P.nb_late, nb_prim=P.nb_late, n_x=1,
+                         q=_f64(P.q), qt=_f64(P.q)[None], w_l=_f64(w_gram),
+                         late_modes=late, prim_modes=late)
+    return direct(Pg, xw=np.ones(1))
+
+
+def full_gamma(gram_matrix, gamma_prime) -> np.ndarray:
+    """Gamma = <Q, Q>^{-1} Gamma' (Appendix A: Gamma_nm = sum_r <Q_n,Q_r>^{-1}
+    <Q_r, Q~_m>), by numpy's Cholesky factor of the Gram matrix and two
+    triangular solves (scipy).  Raises numpy.linalg.LinAlgError if the Gram
+    matrix is not positive definite."""
+    from scipy.linalg import solve_triangular
+    Lc = np.linalg.cholesky(_f64(gram_matrix))
+    y = solve_triangular(Lc, _f64(gamma_prime), lower=True)
+    return solve_triangular(Lc.T, y, lower=False)
 
 
 def backward(P, gbar, n_mu: int | None = None, xw=None, want_dq: bool = True):

@@ -150,6 +150,13 @@ def make_problem(l_max: int, nb: int, n_x: int, seed: int = 1, l_min: int = 2,
                    seed=seed, name=name)
 
 
+def gram_weights(l_min: int, l_max: int) -> np.ndarray:
+    """l weight of the Gram matrix <Q_n, Q_r> (Appendix A): (2l+1) / v_l^2
+    with v_l = (2l+1)^(1/6), i.e. (2l+1)^(2/3)."""
+    lf = np.arange(l_min, l_max + 1, dtype=np.float64)
+    return (2.0 * lf + 1.0) ** (2.0 / 3.0)
+
+
 # Named workloads -------------------------------------------------------------
 
 def cpu_size(seed: int = 1) -> Problem:

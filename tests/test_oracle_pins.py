@@ -417,3 +417,84 @@ def test_error_scale_matches_brute_force():
     assert np.abs(g).max() < ga.max()            # cancellation happens somewhere
     Pn = syn.Problem(**{**P.__dict__, "qt": -2.0 * P.qt})
     assert np.allclose(oracle.separable(Pn, magnitudes=True), 8.0 * ga, rtol=1e-13, atol=0)
+
+
+# --------------------------------------------------------------------------
+# 11. Gram matrix <Q_n, Q_r> and the full Gamma = <Q,Q>^{-1} Gamma' (Appendix A)
+# --------------------------------------------------------------------------
+
+def brute_force_gram(l_min, l_max, q, v, modes):
+    """<Q_n, Q_r> over the whole cube straight from Appendix A:
+    sum (h/(v1 v2 v3))^2 Q_n Q_r with Q_n = 1/6 sum_perm q q q."""
+    ls = range(l_min, l_max + 1)
+    G = np.zeros((len(modes), len(modes)))
+    for l1, l2, l3 in itertools.product(ls, repeat=3):
+        tj = float(threej_factorial_exact(l1, l2, l3))
+        if tj == 0.0:
+            continue
+        k = (l1 - l_min, l2 - l_min, l3 - l_min)
+        h2 = (2 * l1 + 1) * (2 * l2 + 1) * (2 * l3 + 1) / (4 * math.pi) * tj
+        vv = v[k[0]] * v[k[1]] * v[k[2]]
+        Q = np.array([sum(q[pa, k[0]] * q[pb, k[1]] * q[pc, k[2]]
+                          for pa, pb, pc in itertools.permutations(m)) / 6.0 for m in modes])
+        G += h2 / vv ** 2 * np.outer(Q, Q)
+    return G
+
+
+def test_gram_brute_force_tiny():
+    """oracle.gram with w_gram = (2l+1)/v_l^2 equals the inner-product
+    definition summed over every ordered (l1, l2, l3)."""
+    rng = np.random.default_rng(21)
+    l_min, l_max, nb = 2, 7, 3
+    ls = np.arange(l_min, l_max + 1)
+    q = rng.standard_normal((nb, ls.size))
+    v = (2 * ls + 1.0) ** (1 / 6)
+    modes = syn.mode_list(nb)
+    P = syn.Problem(l_min=l_min, l_max=l_max, nb_late=nb, nb_prim=nb, n_x=1, q=q,
+                    qt=q[None].copy(), w_l=np.ones(ls.size), x=np.zeros(1), phi=np.zeros(nb),
+                    late_modes=modes, prim_modes=modes)
+    ref = brute_force_gram(l_min, l_max, q, v, modes.tolist())
+    g = oracle.gram(P, (2 * ls + 1.0) / v ** 2)
+    assert np.abs(g - ref).max() / np.abs(ref).max() < 1e-13
+
+
+def test_gram_symmetric_positive_definite():
+    P = syn.cpu_size()
+    g = oracle.gram(P, syn.gram_weights(P.l_min, P.l_max))
+    assert np.abs(g - g.T).max() / np.abs(g).max() < 1e-14
+    assert np.linalg.eigvalsh(g).min() > 0.0
+    # a mode list with a repeated mode is singular: its Cholesky must fail
+    late = np.concatenate([P.late_modes, P.late_modes[3:4]])
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.full_gamma(oracle.gram(P, syn.gram_weights(P.l_min, P.l_max), late=late),
+                          np.eye(late.shape[0]))
+
+
+def test_full_gamma_is_identity_when_projected_basis_is_late_basis():
+    """With q~(l, x) = q(l) at one radial point of unit weight and the Gram
+    weights as l weights, Q~' = Q, so Gamma' = <Q,Q> and Gamma = I.  Gamma'
+    comes from the separable form (Eq. 2D), the Gram matrix from the direct
+    sum: the two routes and the solve must agree."""
+    P0 = syn.cpu_size()
+    wg = syn.gram_weights(P0.l_min, P0.l_max)
+    P = syn.Problem(**{**P0.__dict__, "qt": P0.q[None].copy(), "n_x": 1, "x": np.zeros(1),
+                       "w_l": wg})
+    gp = oracle.separable(P, xw=np.ones(1))
+    G = oracle.gram(P, wg)
+    assert np.abs(gp - G).max() / np.abs(G).max() < 1e-12
+    cond = np.linalg.cond(G)
+    gam = oracle.full_gamma(G, gp)
+    assert np.abs(gam - np.eye(P.n_late)).max() < 1e-15 * cond
+
+
+def test_full_gamma_backward_error_and_scaling():
+    """The solve's backward error is at rounding level, and Gamma scales as
+    Gamma' / (scale of the Gram matrix)."""
+    P = syn.cpu_size()
+    G = oracle.gram(P, syn.gram_weights(P.l_min, P.l_max))
+    gp = oracle.separable(P)
+    X = oracle.full_gamma(G, gp)
+    r = np.abs(G @ X - gp).max() / (np.abs(G).max() * np.abs(X).max())
+    assert r < 1e-13
+    X2 = oracle.full_gamma(4.0 * G, gp)
+    assert np.allclose(X2, X / 4.0, rtol=1e-12, atol=1e-12 * np.abs(X).max())
