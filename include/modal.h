@@ -236,6 +236,39 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
                                     const modal_opts *opts, double *const *gammas,
                                     modal_stream_t stream);
 
+/* ---- the full Gamma (Appendix A) ------------------------------------------ */
+
+/* Gram matrix of the late basis, <Q_n, Q_r> with the inner product of
+ * Appendix A (weight (h_l1l2l3 / v_l1 v_l2 v_l3)^2 over all l triples):
+ *   gram[n][r] = 1/(144 pi) sum_{l1,l2,l3} w_l1 w_l2 w_l3 (l1 l2 l3; 0 0 0)^2
+ *                 (sum of the 6 assignments of q_a q_b q_c) (same for r)
+ * with w_l = w_gram[l - l_min], which for the paper's inner product is
+ * (2l+1)/v_l^2 = (2l+1)^(2/3).  It is the separable projection (Eq. 2D) of a
+ * problem whose projected basis is q itself at one radial point of unit
+ * weight and whose primordial modes are the late modes, so it runs on the
+ * same kernels and honours opts (precision, n_mu; error_estimate receives the
+ * symmetrised magnitude form).  Reads prob's l range, nb_late, q, n_late and
+ * late_modes; ignores qt, w_l, x_w and the primordial side.  w_gram: device
+ * [L].  gram: device [n_late][n_late] (overwritten), symmetrised as
+ * (G + G^T)/2.  Stream-ordered, no host synchronisation. */
+int modal_gram(modal_handle *h, const modal_problem *prob, const double *w_gram,
+               const modal_opts *opts, double *gram, modal_stream_t stream);
+
+/* x = gram^{-1} rhs by a Cholesky factorisation gram = L L^T (FP64, blocks of
+ * 64) and two triangular solves: with gram from modal_gram and rhs = Gamma'
+ * from modal_project_separable (or _direct), x is the full
+ *   Gamma_nm = sum_r <Q_n, Q_r>^{-1} <Q_r, Q~_m>           (Appendix A).
+ * gram: device [n][n] row-major, only entries i >= j are read (not
+ * modified).  rhs, x: device [n][m] row-major; x may be rhs (solved in
+ * place) but not gram.  info: device int32 or NULL; it receives 0, or k > 0
+ * if the k-th pivot is not above n 2^-52 times gram[k-1][k-1] or is not a
+ * number: the leading minor of order k is not positive definite, or is
+ * singular to working precision (e.g. a mode listed twice) -- then x is
+ * filled with NaN.  m = 0 factors only (info still set).  The factor lives in the handle's scratch.  Stream-ordered, no
+ * host synchronisation: read info after the stream. */
+int modal_gram_solve(modal_handle *h, int32_t n, int32_t m, const double *gram, const double *rhs,
+                     double *x, int32_t *info, modal_stream_t stream);
+
 /* Allocation-free form of modal_project_separable, for callers that cannot
  * allocate device memory: programs that hand all of a GPU's memory to their
  * own allocator or budget, plugins whose host forbids cudaMalloc, and

@@ -21,7 +21,7 @@ EXPORTS = [
     "modal_contract_l", "modal_project_separable", "modal_project_direct",
     "modal_project_backward", "modal_project_separable_batched", "modal_profile_enable",
     "modal_profile_read", "modal_handle_status", "modal_handle_set_wait_limit",
-    "modal_project_separable_noalloc", "modal_handle_set_option",
+    "modal_project_separable_noalloc", "modal_handle_set_option", "modal_gram", "modal_gram_solve",
 ]
 
 
@@ -85,6 +85,8 @@ def lib():
         "modal_handle_status": [vp],
         "modal_handle_set_option": [vp, i32, ctypes.c_int64],
         "modal_project_separable_noalloc": [P, O, vp, vp],
+        "modal_gram": [vp, P, vp, O, vp, vp],
+        "modal_gram_solve": [vp, i32, i32, vp, vp, vp, vp, vp],
         "modal_handle_set_wait_limit": [vp, ctypes.c_int64],
         "modal_profile_read": [vp, i32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)],

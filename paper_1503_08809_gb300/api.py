@@ -272,3 +272,56 @@ def project_separable_batched(dps: Sequence[DeviceProblem], precision: int = _li
     check(lib().modal_project_separable_batched(h.ptr, len(dps), arr, ctypes.byref(o), outp,
                                                 _stream(dev)), h.ptr)
     return gammas
+
+
+def gram(dp: DeviceProblem, w_gram, precision: int = _lib.PREC_FP64, n_mu: int = 0,
+         allow_inexact_gl: bool = False, out=None, handle=None,
+         error_estimate: Optional[torch.Tensor] = None):
+    """modal_gram: the late basis's Gram matrix <Q_n, Q_r> [n_late][n_late]
+    (Appendix A inner product) with l weight ``w_gram`` ([L]; the paper's is
+    (2l+1)^(2/3))."""
+    h = _h(handle, dp.device)
+    G = out if out is not None else torch.empty(dp.n_late, dp.n_late, dtype=_f64, device=dp.device)
+    wg = _dev(w_gram, dp.device, _f64)
+    s = dp.struct()
+    o = _opts(precision, n_mu, allow_inexact_gl, 0, error_estimate)
+    check(lib().modal_gram(h.ptr, ctypes.byref(s), _ptr(wg), ctypes.byref(o), _ptr(G),
+                           _stream(dp.device)), h.ptr)
+    return G
+
+
+def gram_solve(G: torch.Tensor, rhs: torch.Tensor, out=None, handle=None, raise_if_not_pd: bool = True):
+    """modal_gram_solve: X = G^{-1} rhs by Cholesky (FP64).  Returns X; with
+    ``raise_if_not_pd`` (the default) waits for the stream and raises
+    ModalError(MODAL_EINVAL) if G is not positive definite, else returns
+    (X, info) where info is the device status word."""
+    G = G.to(_f64).contiguous()
+    rhs = rhs.to(_f64).contiguous()
+    n, m = int(G.shape[0]), int(rhs.shape[1])
+    if G.shape != (n, n) or rhs.shape[0] != n:
+        raise ValueError("G must be [n][n] and rhs [n][m]")
+    h = _h(handle, G.device)
+    X = out if out is not None else torch.empty_like(rhs)
+    info = torch.zeros(1, dtype=_i32, device=G.device)
+    check(lib().modal_gram_solve(h.ptr, n, m, _ptr(G), _ptr(rhs), _ptr(X), _ptr(info),
+                                 _stream(G.device)), h.ptr)
+    if not raise_if_not_pd:
+        return X, info
+    k = int(info.item())
+    if k:
+        raise _lib.ModalError(_lib.MODAL_EINVAL,
+                         f"the Gram matrix is not positive definite (leading minor of order {k})")
+    return X
+
+
+def project_full(dp: DeviceProblem, w_gram, precision: int = _lib.PREC_FP64, handle=None):
+    """The full Gamma = <Q,Q>^{-1} Gamma' (Appendix A): Gamma' by
+    modal_project_separable, the Gram matrix by modal_gram, then
+    modal_gram_solve.  Raises ModalError if the Gram matrix is not positive
+    definite or a device-side check of the tensor-core form failed."""
+    h = _h(handle, dp.device)
+    gp = project_separable(dp, precision=precision, handle=h)
+    G = gram(dp, w_gram, precision=precision, handle=h)
+    if precision == _lib.PREC_OZAKI_BF16:
+        handle_status(handle=h)
+    return gram_solve(G, gp, out=gp, handle=h)

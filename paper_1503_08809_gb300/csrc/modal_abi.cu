@@ -16,6 +16,7 @@
 #include "kernels.cuh"
 #include "tc.cuh"
 #include "backward.cuh"
+#include "gram.cuh"
 #include "profile.cuh"
 
 using namespace modal;
@@ -80,8 +81,9 @@ static int fail(modal_handle *h, int code, const char *fmt, ...) {
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Grow-only device scratch per slot (0: general, 1: direct-path triples,
-// 2: batched problem table).  Growing frees the old block (cudaFree waits for
-// the device), so pointers from an earlier call must not be reused.
+// 2: batched problem table, 3: the Cholesky factor of modal_gram_solve).
+// Growing frees the old block (cudaFree waits for the device), so pointers
+// from an earlier call must not be reused.
 static int ws_get(modal_handle *h, int slot, size_t bytes, void **out) {
   if (bytes == 0) bytes = 256;
   if (h->slot_bytes[slot] < bytes) {
@@ -563,6 +565,59 @@ int modal_project_separable(modal_handle *h, const modal_problem *p, const modal
   void *scratch;
   if (int r = ws_get(h, 0, pl.bytes, &scratch)) return r;
   return run_separable(h, h->num_sms, p, pl, gamma, (cudaStream_t)stream, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// Gram matrix <Q_n, Q_r> and the full Gamma (Appendix A)
+// ---------------------------------------------------------------------------
+int modal_gram(modal_handle *h, const modal_problem *p, const double *w_gram, const modal_opts *o,
+               double *gram, modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (!p) return fail(h, MODAL_EINVAL, "null problem");
+  if (p->l_min < 0 || p->l_max < p->l_min) return fail(h, MODAL_EINVAL, "bad l range [%d, %d]", p->l_min, p->l_max);
+  if (p->nb_late < 1 || p->nb_late > 64)
+    return fail(h, MODAL_EINVAL, "nb_late must be in [1, 64] (got %d)", p->nb_late);
+  if (p->n_late < 0) return fail(h, MODAL_EINVAL, "negative size");
+  if (p->n_late == 0) return MODAL_OK;
+  if (!p->q || !p->late_modes || !w_gram || !gram) return fail(h, MODAL_EINVAL, "null q, late_modes, w_gram or gram");
+  // the late basis projected on itself: q~ := q at one radial point of unit
+  // weight, l weight w_gram, primordial modes := late modes
+  modal_problem g = *p;
+  g.nb_prim = p->nb_late;
+  g.n_x = 1;
+  g.qt = p->q;
+  g.w_l = w_gram;
+  g.n_prim = p->n_late;
+  g.prim_modes = p->late_modes;
+  g.x_w = nullptr;
+  SepPlan pl;
+  if (int r = plan_separable(h, &g, o, pl, h->num_sms)) return r;
+  void *scratch;
+  if (int r = ws_get(h, 0, align256(pl.bytes) + 256, &scratch)) return r;
+  double *one = (double *)((char *)scratch + align256(pl.bytes));  // the unit radial weight
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(launch_fill(one, 1, 1.0, st));
+  g.x_w = one;
+  if (int r = run_separable(h, h->num_sms, &g, pl, gram, st, scratch)) return r;
+  PROFN(h, "gram_symmetrise", st, pl.est ? 2 : 1);
+  CK(launch_symmetrise(gram, p->n_late, st));
+  if (pl.est) CK(launch_symmetrise(pl.est, p->n_late, st));
+  return MODAL_OK;
+}
+
+int modal_gram_solve(modal_handle *h, int32_t n, int32_t m, const double *gram, const double *rhs, double *x,
+                     int32_t *info, modal_stream_t stream) {
+  if (int r = check_handle(h)) return r;
+  if (n < 0 || m < 0) return fail(h, MODAL_EINVAL, "negative size");
+  if (n > 0 && !gram) return fail(h, MODAL_EINVAL, "null gram");
+  if (n > 0 && m > 0 && (!rhs || !x)) return fail(h, MODAL_EINVAL, "null rhs or x");
+  if (n > 0 && m > 0 && x == gram) return fail(h, MODAL_EINVAL, "x must not alias gram");
+  void *scratch;
+  if (int r = ws_get(h, 3, gram_solve_scratch_bytes(n), &scratch)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  PROFN(h, "gram_solve", st, gram_solve_launches(n, m));
+  CK(gram_solve(n, m, gram, rhs, x, scratch, (int *)info, st));
+  return MODAL_OK;
 }
 
 // FNV-1a over the bytes of the problem set: the key of a captured graph
