@@ -61,11 +61,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="planck", choices=["planck", "grad", "batched", "direct", "full"],
+    ap.add_argument("--workload", default="planck",
+                    choices=["planck", "grad", "batched", "direct", "full", "integrators"],
                     help="planck: the headline line; grad: forward + adjoint at l_max 1000 / "
                          "16 functions / 300 x; batched: 64 uneven models in one call; direct: "
                          "the Planck problem by the tetrahedral sum on the sparse l grid; full: "
-                         "Gamma' + the Gram matrix + the Cholesky solve (the full Gamma)")
+                         "Gamma' + the Gram matrix + the Cholesky solve (the full Gamma); "
+                         "integrators: accuracy against time of the two radial rules")
     ap.add_argument("--tc-fused", type=int, default=0, choices=[0, 1, 2],
                     help="tensor-core triple product: 0 = Y through HBM, 1 and 2 = Y formed in "
                          "shared memory (two forms)")
@@ -560,8 +562,69 @@ def run_extra(args):
                       "config": cfg}), flush=True)
 
 
+INTEGRATOR_NX = (27, 54, 108, 216, 432, 864)
+INTEGRATOR_REF_NX = 1768
+
+
+def run_integrators(args):
+    """Accuracy against time of the two radial rules of Section 3.2.4 (the
+    analogue of the paper's integrator study): Gamma' of the l_max 1000 /
+    16-function problem with x resampled on 27..864 points, each rule, against
+    the Hermite rule on 1768 points; percentage RMSE of the unit-normalised
+    matrix and the device time of each projection (FP64 by default: the
+    tensor-core form's 1e-9 would hide the smaller errors)."""
+    import torch
+    import paper_1503_08809_gb300 as mg
+    import synthetic as syn
+    dev = torch.device("cuda", 0)
+    prec_name = "fp64" if args.precision == "auto" else args.precision
+    prec = PREC[prec_name]
+    h = mg.Handle(dev)
+    st = torch.cuda.current_stream(dev)
+
+    def project(n, kind, warm=False):
+        P = syn.make_problem(1000, 16, n)
+        dp = mg.DeviceProblem.from_host(P, device=dev, xw_kind=kind, handle=h)
+        if warm:  # the largest run first sizes the scratch for all
+            mg.project_separable(dp, precision=prec, handle=h)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g = mg.project_separable(dp, precision=prec, handle=h)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        if prec == PREC["ozaki"]:
+            mg.handle_status(handle=h)
+        return g.cpu().numpy(), e0.elapsed_time(e1), P.slices
+
+    def unit_rmse_pct(g, ref):
+        u = lambda a: a / np.sqrt((a ** 2).sum())
+        return 100.0 * float(np.sqrt(np.mean((u(g) - u(ref)) ** 2)))
+
+    ref, ref_ms, ref_slices = project(INTEGRATOR_REF_NX, mg.XW_HERMITE, warm=True)
+    table = {"trapezium": {}, "hermite": {}}
+    tot_ms, tot_slices = ref_ms, ref_slices
+    for name, kind in (("trapezium", mg.XW_TRAPEZOID), ("hermite", mg.XW_HERMITE)):
+        for n in INTEGRATOR_NX:
+            g, ms, sl = project(n, kind)
+            table[name][str(n)] = {"rmse_pct": unit_rmse_pct(g, ref), "ms": ms}
+            tot_ms += ms
+            tot_slices += sl
+    cfg = {"workload": "lmax1000_nb16_integrators", "l_max": 1000, "nb": 16,
+           "n_x": list(INTEGRATOR_NX), "reference": f"hermite rule, {INTEGRATOR_REF_NX} x",
+           "precision": prec_name, "error": "percentage RMSE of the unit-normalised Gamma'",
+           "study": table, "reference_ms": ref_ms}
+    print(json.dumps({"metric": METRIC, "value": tot_slices / (tot_ms * 1e-3), "unit": "slices/s",
+                      "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": tot_ms,
+                      "higher_is_better": True, "dtype": DTYPE[prec_name], "data": "synthetic",
+                      "config": cfg}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "integrators" and args.impl == "ours":
+        run_integrators(args)
+        return
     if args.workload != "planck" and args.impl == "ours":
         run_extra(args)
         return

@@ -498,3 +498,34 @@ def test_full_gamma_backward_error_and_scaling():
     assert r < 1e-13
     X2 = oracle.full_gamma(4.0 * G, gp)
     assert np.allclose(X2, X / 4.0, rtol=1e-12, atol=1e-12 * np.abs(X).max())
+
+
+# --------------------------------------------------------------------------
+# 12. Radial integrators on the synthetic tables (Section 3.2.4, accuracy study)
+# --------------------------------------------------------------------------
+
+def _unit_rmse_pct(g, ref):
+    """Percentage RMSE of the unit-normalised Gamma' (Frobenius norm 1)."""
+    u = lambda a: a / np.sqrt((a ** 2).sum())
+    return 100.0 * float(np.sqrt(np.mean((u(g) - u(ref)) ** 2)))
+
+
+def test_integrator_convergence_on_synthetic_tables():
+    """Gamma' (l_max 48, 5 functions) with x resampled on 54..432 points
+    against the Hermite rule on 1768 points (the sample size of the paper's
+    reference): the trapezium rule converges at second order (x4 per
+    doubling), the Hermite rule -- the trapezium sum plus the end-derivative
+    correction from forward differences -- at third order or better, and is
+    the more accurate from 108 points on."""
+    def gam(nx, kind):
+        P = syn.make_problem(48, 5, nx)
+        return oracle.separable(P, xw=oracle.x_weights(P.x, kind))
+    ref = gam(1768, oracle.HERMITE)
+    ns = (54, 108, 216, 432)
+    et = [_unit_rmse_pct(gam(n, oracle.TRAPEZOID), ref) for n in ns]
+    eh = [_unit_rmse_pct(gam(n, oracle.HERMITE), ref) for n in ns]
+    for a, b in zip(et, et[1:]):
+        assert 3.5 < a / b < 4.5
+    for a, b in zip(eh, eh[1:]):
+        assert a / b > 7.0
+    assert all(h < t for h, t in zip(eh[1:], et[1:]))
