@@ -76,6 +76,18 @@ def sparse_l_grid(l_max: int, l_min: int = 2):
     pts += list(range(52, min(200, l_max) + 1, 2))
     pts += list(range(205, min(500, l_max) + 1, 5))
     pts += list(range(510, l_max + 1, 10))
+    return _cells(pts, l_min, l_max)
+
+
+def stepped_l_grid(l_max: int, step: int, dense_to: int = 50, l_min: int = 2):
+    """Every l up to ``dense_to``, then every ``step``-th l up to l_max (and
+    l_max itself), with midpoint cells as in ``sparse_l_grid``."""
+    pts = list(range(l_min, min(dense_to, l_max) + 1))
+    pts += list(range(dense_to + step, l_max + 1, step)) + [l_max]
+    return _cells(pts, l_min, l_max)
+
+
+def _cells(pts, l_min: int, l_max: int):
     g = np.asarray(sorted(set(p for p in pts if l_min <= p <= l_max)), dtype=np.int64)
     lo = np.empty(g.size)
     hi = np.empty(g.size)
