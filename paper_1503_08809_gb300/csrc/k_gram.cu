@@ -16,8 +16,8 @@
 // Sizes are small next to the projection (n_late <= a few thousand), so the
 // kernels are plain CUDA-core FP64 tiles: the factorisation's trailing
 // update and the solves' updates are one strided tiled kernel (64 x 64 output
-// tiles, 4 x 4 per thread); the diagonal blocks (64 x 64) are factored and
-// substituted in shared memory.
+// tiles, 4 x 4 per thread); each diagonal block (64 x 64) is factored and
+// inverted in shared memory, and the panel and the solves apply the inverse.
 #include <cmath>
 #include <mutex>
 
@@ -26,10 +26,9 @@
 namespace modal {
 
 constexpr int GB = 64;  // block size of the factorisation and the solves
-// dynamic shared memory of the substitution kernels: the diagonal block
-// (GB x GB, read as broadcasts) and GB rows or columns of the operand
-// (stride GB + 1, so that the threads' rows or columns fall in distinct banks)
-constexpr int SUBST_SMEM = (GB * GB + GB * (GB + 1)) * (int)sizeof(double);
+// dynamic shared memory of the diagonal-block kernels: two GB x GB blocks
+// with rows padded to GB + 1 (distinct banks for threads on distinct rows)
+constexpr int DIAG_SMEM = 2 * GB * (GB + 1) * (int)sizeof(double);
 
 __global__ void k_symmetrise(double *G, int n) {
   const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
@@ -57,11 +56,21 @@ cudaError_t launch_fill(double *p, int64_t n, double v, cudaStream_t st) {
 }
 
 // Cholesky of the diagonal block at (k0, k0) of size nb <= GB, in place
-// (lower triangle), right-looking inside shared memory.  G: the input matrix
-// (its diagonal scales the pivot test), n: its order.
-__global__ void __launch_bounds__(256) k_potrf_diag(double *L, const double *G, int64_t ld, int n, int k0, int nb,
-                                                    int *info) {
-  __shared__ double s[GB][GB + 1];
+// (lower triangle), right-looking inside shared memory, followed by the
+// inverse of that factor, V = L_kk^{-1} (lower), written to Dinv (GB x GB,
+// zero outside the nb x nb lower triangle): the panel and both solves then
+// apply V as small parallel products instead of running a 64-step
+// dependent substitution per row or column (FP64 latency dominates those on
+// this part).  G: the input matrix (its diagonal scales the pivot test), n:
+// its order.
+__global__ void __launch_bounds__(256) k_potrf_inv_diag(double *L, const double *G, int64_t ld, int n, int k0,
+                                                        int nb, double *Dinv, int *info) {
+  extern __shared__ double diag_sm[];
+  double(*s)[GB + 1] = reinterpret_cast<double(*)[GB + 1]>(diag_sm);
+  double(*v)[GB + 1] = reinterpret_cast<double(*)[GB + 1]>(diag_sm + GB * (GB + 1));
+  __shared__ double gdiag[GB];  // the input's diagonal (scale of the pivot test)
+  __shared__ double rdiag[GB];  // 1 / pivot
+  __shared__ double piv_s;      // the current pivot
   __shared__ int bad;
   if (*info) return;  // an earlier block failed
   const int tid = threadIdx.x;
@@ -69,23 +78,37 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double *L, const double *G, 
     const int r = e / nb, c = e % nb;
     s[r][c] = c <= r ? L[(int64_t)(k0 + r) * ld + k0 + c] : 0.0;
   }
-  if (tid == 0) bad = 0;
+  if (tid < nb) gdiag[tid] = G[(int64_t)(k0 + tid) * ld + k0 + tid];
+  __syncthreads();
+  const double tol = (double)n * 0x1p-52;
+  // Thread 0 alone takes the square root and the reciprocal of each pivot
+  // (FP64 sequences that cost the whole warp's issue slots on this part), as
+  // soon as the pivot is final: step j's trailing update gives it the
+  // diagonal entry j + 1 first.  The others read the result after a barrier.
+  auto pivot = [&](int j) {
+    const double d = s[j][j], g = gdiag[j];
+    if (g > 0.0 && d > tol * g) {  // false also for NaN
+      const double p = sqrt(d);
+      piv_s = p;
+      rdiag[j] = 1.0 / p;
+    } else {
+      bad = j + 1;
+    }
+  };
+  if (tid == 0) {
+    bad = 0;
+    pivot(0);
+  }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      const double d = s[j][j], g = G[(int64_t)(k0 + j) * ld + k0 + j];
-      if (g > 0.0 && d > (double)n * 0x1p-52 * g) s[j][j] = sqrt(d);
-      else bad = j + 1;  // also for NaN
-    }
-    __syncthreads();
     if (bad) break;  // the same value for every thread
-    const double piv = s[j][j];
-    for (int i = j + 1 + tid; i < nb; i += blockDim.x) s[i][j] /= piv;
-    __syncthreads();
-    const int m = nb - j - 1;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e / m, l = j + 1 + e % m;
-      if (l <= i) s[i][l] -= s[i][j] * s[l][j];
+    const double r = rdiag[j], p = piv_s;
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) s[i][j] *= r;
+    __syncthreads();  // column j scaled; every thread has read the pivot
+    if (tid == 0) s[j][j] = p;
+    for (int i = j + 1 + (tid >> 4); i < nb; i += 16) {
+      for (int l = j + 1 + (tid & 15); l <= i; l += 16) s[i][l] -= s[i][j] * s[l][j];
+      if (tid == 0 && i == j + 1) pivot(j + 1);  // entry (j+1, j+1) is final now
     }
     __syncthreads();
   }
@@ -97,39 +120,52 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double *L, const double *G, 
     const int r = e / nb, c = e % nb;
     if (c <= r) L[(int64_t)(k0 + r) * ld + k0 + c] = s[r][c];
   }
+  // V[i][c] = (delta_ic - sum_{c <= l < i} L[i][l] V[l][c]) / L[i][i], row by
+  // row; four lanes of one warp share a column and split the sum
+  const int c = tid >> 2, q = tid & 3;
+  for (int i = 0; i < GB; ++i) {  // every lane runs every step (shuffles)
+    double part = 0.0;
+    if (c < nb && i < nb)
+      for (int l = c + q; l < i; l += 4) part += s[i][l] * v[l][c];
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    part += __shfl_xor_sync(0xffffffffu, part, 2);
+    if (q == 0 && c < nb && i < nb) v[i][c] = i < c ? 0.0 : ((i == c ? 1.0 : 0.0) - part) * rdiag[i];
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = tid; e < GB * GB; e += blockDim.x) {
+    const int r = e / GB, cc = e % GB;
+    Dinv[e] = (r < nb && cc <= r) ? v[r][cc] : 0.0;
+  }
 }
 
-// Panel below the diagonal block: L21 = A21 L11^{-T}, one thread per row
-// (forward substitution along the row), GB rows per CTA.
-__global__ void __launch_bounds__(GB) k_trsm_panel(double *L, int64_t ld, int k0, int nb, int n,
-                                                   const int *info) {
-  extern __shared__ double subst_sm[];
-  double(*Ls)[GB] = reinterpret_cast<double(*)[GB]>(subst_sm);
-  double(*Xs)[GB + 1] = reinterpret_cast<double(*)[GB + 1]>(subst_sm + GB * GB);
+// Panel below the diagonal block: L21 = A21 L11^{-T} = A21 V^T, GB rows per
+// CTA (each row's entries from its own copy in shared memory, so the result
+// overwrites A21 in place).
+__global__ void __launch_bounds__(256) k_panel_apply(double *L, int64_t ld, int k0, int nb, int n,
+                                                    const double *__restrict__ Dinv, const int *info) {
+  extern __shared__ double diag_sm[];
+  double(*A)[GB + 1] = reinterpret_cast<double(*)[GB + 1]>(diag_sm);
+  double(*V)[GB + 1] = reinterpret_cast<double(*)[GB + 1]>(diag_sm + GB * (GB + 1));
   if (*info) return;
   const int tid = threadIdx.x;
   const int row0 = k0 + nb + blockIdx.x * GB;
   const int rows = min(GB, n - row0);
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    Ls[r][c] = c <= r ? L[(int64_t)(k0 + r) * ld + k0 + c] : 0.0;
-  }
-  for (int e = tid; e < rows * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    Xs[r][c] = L[(int64_t)(row0 + r) * ld + k0 + c];
+  for (int e = tid; e < GB * GB; e += blockDim.x) {
+    const int r = e / GB, c = e % GB;
+    A[r][c] = (r < rows && c < nb) ? L[(int64_t)(row0 + r) * ld + k0 + c] : 0.0;
+    V[r][c] = Dinv[e];
   }
   __syncthreads();
-  if (tid < rows) {
-    for (int j = 0; j < nb; ++j) {
-      double v = Xs[tid][j];
-      for (int l = 0; l < j; ++l) v -= Xs[tid][l] * Ls[j][l];
-      Xs[tid][j] = v / Ls[j][j];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < rows * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    L[(int64_t)(row0 + r) * ld + k0 + c] = Xs[r][c];
+  const int r = tid >> 2, jq = tid & 3;
+  if (r >= rows) return;
+#pragma unroll 4
+  for (int t = 0; t < GB / 4; ++t) {
+    const int j = jq + 4 * t;
+    if (j >= nb) break;
+    double acc = 0.0;
+    for (int l = 0; l <= j; ++l) acc += A[r][l] * V[j][l];
+    L[(int64_t)(row0 + r) * ld + k0 + j] = acc;
   }
 }
 
@@ -198,47 +234,38 @@ __global__ void __launch_bounds__(256) k_gemm_sub(int m, int n, int K, const dou
   }
 }
 
-// Substitution with the diagonal block (rows k0 .. k0 + nb) on all m
-// right-hand columns, one thread per column, GB columns per CTA:
-// forward (L_kk Y = X) or backward (L_kk^T Y = X), in place.
+// The diagonal block's inverse applied to rows k0 .. k0 + nb of X, on all m
+// right-hand columns, in place: forward (Y_k = V X_k, from L_kk Y_k = X_k)
+// or backward (X_k = V^T Y_k, from L_kk^T X_k = Y_k).  GB columns per CTA;
+// a thread computes one row of 16 interleaved columns.
 template <bool BACKWARD>
-__global__ void __launch_bounds__(GB) k_trsv_diag(const double *L, int64_t ld, int k0, int nb, double *X,
-                                                  int m, const int *info) {
-  extern __shared__ double subst_sm[];
-  double(*Ls)[GB] = reinterpret_cast<double(*)[GB]>(subst_sm);
-  double(*Xs)[GB + 1] = reinterpret_cast<double(*)[GB + 1]>(subst_sm + GB * GB);
+__global__ void __launch_bounds__(256) k_tri_apply(const double *__restrict__ Dinv, double *X, int m, int k0,
+                                                  int nb, const int *info) {
+  extern __shared__ double diag_sm[];
+  double(*Xs)[GB + 1] = reinterpret_cast<double(*)[GB + 1]>(diag_sm);
+  double(*V)[GB + 1] = reinterpret_cast<double(*)[GB + 1]>(diag_sm + GB * (GB + 1));
   if (*info) return;
   const int tid = threadIdx.x;
   const int c0 = blockIdx.x * GB;
   const int cols = min(GB, m - c0);
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    Ls[r][c] = c <= r ? L[(int64_t)(k0 + r) * ld + k0 + c] : 0.0;
-  }
-  for (int e = tid; e < nb * cols; e += blockDim.x) {
-    const int r = e / cols, c = e % cols;
-    Xs[r][c] = X[(int64_t)(k0 + r) * m + c0 + c];
+  for (int e = tid; e < GB * GB; e += blockDim.x) {
+    const int r = e / GB, c = e % GB;
+    Xs[r][c] = (r < nb && c < cols) ? X[(int64_t)(k0 + r) * m + c0 + c] : 0.0;
+    V[r][c] = Dinv[e];
   }
   __syncthreads();
-  if (tid < cols) {
-    if (!BACKWARD) {
-      for (int j = 0; j < nb; ++j) {
-        double v = Xs[j][tid];
-        for (int l = 0; l < j; ++l) v -= Ls[j][l] * Xs[l][tid];
-        Xs[j][tid] = v / Ls[j][j];
-      }
-    } else {
-      for (int j = nb - 1; j >= 0; --j) {
-        double v = Xs[j][tid];
-        for (int l = j + 1; l < nb; ++l) v -= Ls[l][j] * Xs[l][tid];
-        Xs[j][tid] = v / Ls[j][j];
-      }
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < nb * cols; e += blockDim.x) {
-    const int r = e / cols, c = e % cols;
-    X[(int64_t)(k0 + r) * m + c0 + c] = Xs[r][c];
+  const int i = tid >> 2, cq = tid & 3;
+  if (i >= nb) return;
+#pragma unroll 4
+  for (int t = 0; t < GB / 4; ++t) {
+    const int c = cq + 4 * t;
+    if (c >= cols) break;
+    double acc = 0.0;
+    if (!BACKWARD)
+      for (int l = 0; l <= i; ++l) acc += V[i][l] * Xs[l][c];
+    else
+      for (int l = i; l < nb; ++l) acc += V[l][i] * Xs[l][c];
+    X[(int64_t)(k0 + i) * m + c0 + c] = acc;
   }
 }
 
@@ -252,11 +279,14 @@ __global__ void k_copy_word(const int *src, int *dst) { *dst = *src; }
 
 static size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-size_t gram_solve_scratch_bytes(int n) { return up256((size_t)n * n * sizeof(double)) + 256; }
+// scratch: the factor L (n x n), the inverses of its diagonal blocks
+// (GB x GB each), the status word
+static size_t dinv_offset(int n) { return up256((size_t)n * n * sizeof(double)); }
+static size_t info_offset(int n) { return dinv_offset(n) + up256((size_t)cdiv(n, GB) * GB * GB * sizeof(double)); }
 
-int *gram_solve_info(void *scratch, int n) {
-  return (int *)((char *)scratch + up256((size_t)n * n * sizeof(double)));
-}
+size_t gram_solve_scratch_bytes(int n) { return info_offset(n) + 256; }
+
+int *gram_solve_info(void *scratch, int n) { return (int *)((char *)scratch + info_offset(n)); }
 
 int gram_solve_launches(int n, int m) {
   if (n == 0) return 0;
@@ -266,15 +296,15 @@ int gram_solve_launches(int n, int m) {
   return k + 1;                               // status copy
 }
 
-static cudaError_t subst_attributes() {
+static cudaError_t diag_attributes() {
   static cudaError_t err = cudaSuccess;
   static std::once_flag once;
   std::call_once(once, [] {
-    err = cudaFuncSetAttribute(k_trsm_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, SUBST_SMEM);
-    if (err == cudaSuccess)
-      err = cudaFuncSetAttribute(k_trsv_diag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SUBST_SMEM);
-    if (err == cudaSuccess)
-      err = cudaFuncSetAttribute(k_trsv_diag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SUBST_SMEM);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    err = cudaFuncSetAttribute(k_potrf_inv_diag, a, DIAG_SMEM);
+    if (err == cudaSuccess) err = cudaFuncSetAttribute(k_panel_apply, a, DIAG_SMEM);
+    if (err == cudaSuccess) err = cudaFuncSetAttribute(k_tri_apply<false>, a, DIAG_SMEM);
+    if (err == cudaSuccess) err = cudaFuncSetAttribute(k_tri_apply<true>, a, DIAG_SMEM);
   });
   return err;
 }
@@ -282,9 +312,10 @@ static cudaError_t subst_attributes() {
 cudaError_t gram_solve(int n, int m, const double *G, const double *R, double *X, void *scratch, int *info,
                        cudaStream_t st) {
   double *L = (double *)scratch;
+  double *Dinv = (double *)((char *)scratch + dinv_offset(n));
   int *word = gram_solve_info(scratch, n);
   cudaError_t e;
-  if ((e = subst_attributes()) != cudaSuccess) return e;
+  if ((e = diag_attributes()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(word, 0, sizeof(int), st)) != cudaSuccess) return e;
   if (n == 0) return info && info != word ? cudaMemsetAsync(info, 0, sizeof(int), st) : cudaSuccess;
   if ((e = cudaMemcpyAsync(L, G, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
@@ -295,10 +326,11 @@ cudaError_t gram_solve(int n, int m, const double *G, const double *R, double *X
   // factorisation, one block column at a time
   for (int k0 = 0; k0 < n; k0 += GB) {
     const int nb = min(GB, n - k0);
-    k_potrf_diag<<<1, 256, 0, st>>>(L, G, n, n, k0, nb, word);
+    double *Vk = Dinv + (int64_t)(k0 / GB) * GB * GB;
+    k_potrf_inv_diag<<<1, 256, DIAG_SMEM, st>>>(L, G, n, n, k0, nb, Vk, word);
     const int rest = n - k0 - nb;
     if (rest > 0) {
-      k_trsm_panel<<<cdiv(rest, GB), GB, SUBST_SMEM, st>>>(L, n, k0, nb, n, word);
+      k_panel_apply<<<cdiv(rest, GB), 256, DIAG_SMEM, st>>>(L, n, k0, nb, n, Vk, word);
       const int T = cdiv(rest, 64);
       const double *P = L + (int64_t)(k0 + nb) * n + k0;  // L21 [rest][nb]
       k_gemm_sub<<<T * (T + 1) / 2, 256, 0, st>>>(rest, rest, nb, P, n, 1, P, 1, n,
@@ -310,7 +342,8 @@ cudaError_t gram_solve(int n, int m, const double *G, const double *R, double *X
     // L Y = R (in X), top block down
     for (int k0 = 0; k0 < n; k0 += GB) {
       const int nb = min(GB, n - k0);
-      k_trsv_diag<false><<<cdiv(m, GB), GB, SUBST_SMEM, st>>>(L, n, k0, nb, X, m, word);
+      k_tri_apply<false><<<cdiv(m, GB), 256, DIAG_SMEM, st>>>(Dinv + (int64_t)(k0 / GB) * GB * GB, X, m, k0,
+                                                               nb, word);
       const int rest = n - k0 - nb;
       if (rest > 0)
         k_gemm_sub<<<dim3(cdiv(rest, 64), cdiv(m, 64)), 256, 0, st>>>(
@@ -321,7 +354,8 @@ cudaError_t gram_solve(int n, int m, const double *G, const double *R, double *X
     // L^T X = Y, bottom block up
     for (int k0 = (n - 1) / GB * GB; k0 >= 0; k0 -= GB) {
       const int nb = min(GB, n - k0);
-      k_trsv_diag<true><<<cdiv(m, GB), GB, SUBST_SMEM, st>>>(L, n, k0, nb, X, m, word);
+      k_tri_apply<true><<<cdiv(m, GB), 256, DIAG_SMEM, st>>>(Dinv + (int64_t)(k0 / GB) * GB * GB, X, m, k0,
+                                                              nb, word);
       if (k0 > 0)  // rows above: X_top -= (L block row k)^T X_k
         k_gemm_sub<<<dim3(cdiv(k0, 64), cdiv(m, 64)), 256, 0, st>>>(
             k0, m, nb, L + (int64_t)k0 * n, 1, n, X + (int64_t)k0 * m, m, 1, X, m, 0, word);
