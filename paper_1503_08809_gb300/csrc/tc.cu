@@ -87,6 +87,23 @@ __device__ __forceinline__ float pow2f_or0(int k) {
   return k < -126 ? 0.f : __int_as_float((min(k, 127) + 127) << 23);
 }
 
+// x 2^e as a double, assembled from the bits of x with integer operations
+// (this part's FP64 pipe runs at 1/64 of the FP32 rate, and each epilogue
+// converts 16 K running sums per tile).  Exact; a zero keeps its sign; a
+// subnormal x, or a result outside the normal double range, goes through
+// ldexp.  (hi, lo) of a double-FP32 sum then becomes
+// f32_scaled_f64(hi, e) + f32_scaled_f64(lo, e), one exact FP64 addition.
+__device__ __noinline__ double f32_scaled_f64_slow(float x, int e) { return ldexp((double)x, e); }
+__device__ __forceinline__ double f32_scaled_f64(float x, int e) {
+  const uint32_t u = __float_as_uint(x);
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  const int E = (int)ex + (1023 - 127) + e;
+  if (ex == 0u || ex == 0xffu || E <= 0 || E >= 2047) return f32_scaled_f64_slow(x, e);
+  return __longlong_as_double((long long)(sign | ((uint64_t)E << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+
 // Scale factors 2^(BETA - e) as two exact float factors (the exponent range of
 // the values may exceed one float exponent).  e < -99999 marks an all-zero row.
 struct SplitScale {
@@ -512,19 +529,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       ptx::mbar_arrive(acc_empty);
     }
     if (ok && !*abort_flag && row < Rt) {
+      // OUT_MODE 0 writes M[x][j][a][p] for A row (j, a) and B row (x, p):
+      // the row's offset once per tile, the column's (x, p) stepped along
+      int64_t mrow = 0, mx = 0;
+      int xl = 0, p = 0;
+      if (OUT_MODE == 0) {
+        const int64_t rA = ar0 + row, rB = b_row0 + col0;
+        mrow = rA * P.nbp;  // (j nbl + a) nbp, as rA = j nbl + a
+        mx = (int64_t)P.n_mu * P.nbl * P.nbp;
+        xl = (int)(rB / P.nbp);
+        p = (int)(rB % P.nbp);
+      }
 #pragma unroll  // full unroll keeps hi[]/lo[] in registers
       for (int c = 0; c < 64; ++c) {
         const int col = col0 + c;
-        if (col >= C) continue;
-        const double v = ldexp((double)hi[c] + (double)lo_s[(col0 + c) * OZ_BM + row], ebias);
-        if (OUT_MODE == 0) {
-          const int64_t rA = ar0 + row, rB = b_row0 + col;
-          const int j = (int)(rA / P.nbl), a = (int)(rA % P.nbl);
-          const int xl = (int)(rB / P.nbp), p = (int)(rB % P.nbp);
-          P.out[(((int64_t)xl * P.n_mu + j) * P.nbl + a) * P.nbp + p] = v;
-        } else {
-          double *d = P.out + out_base + (int64_t)row * P.g.cols(bblk) + col;
-          *d += v;
+        if (col < C) {
+          const double v = f32_scaled_f64(hi[c], ebias) + f32_scaled_f64(lo_s[(col0 + c) * OZ_BM + row], ebias);
+          if (OUT_MODE == 0) {
+            P.out[xl * mx + mrow + p] = v;
+          } else {
+            double *d = P.out + out_base + (int64_t)row * P.g.cols(bblk) + col;
+            *d += v;
+          }
+        }
+        if (OUT_MODE == 0 && ++p == P.nbp) {
+          p = 0;
+          ++xl;
         }
       }
     }
@@ -1411,7 +1441,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int c = 0; c < 64; ++c) {
         const int col = col0 + c;
         if (col >= C) continue;
-        const double v = ldexp((double)hi[c] + (double)lo_s[col * OZ_BM + erow], ebias);
+        const double v = f32_scaled_f64(hi[c], ebias) + f32_scaled_f64(lo_s[col * OZ_BM + erow], ebias);
         double *d = P.G + out_base + (int64_t)erow * P.g.cols(bblk) + col;
         if (P.split_k > 1) atomicAdd(d, v);
         else *d += v;
@@ -1746,7 +1776,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
         const int col = col0 + c;
         if (col >= C) continue;
         double *d = P.G + out_base + (int64_t)erow * P.g.cols(bblk) + col;
-        *d += ldexp((double)hi[c] + (double)lo[c], ebias);
+        *d += f32_scaled_f64(hi[c], ebias) + f32_scaled_f64(lo[c], ebias);
       }
     }
   }
