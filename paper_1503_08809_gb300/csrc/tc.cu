@@ -843,6 +843,35 @@ __device__ __forceinline__ f2 df_from_d(double x) {
   float h = __double2float_rn(x);
   return {h, __double2float_rn(x - (double)h)};
 }
+// The same split with integer operations on the bits of x (this part's FP64
+// pipe runs at 1/64 of the FP32 rate): hi is x rounded to 24 significant
+// bits (to nearest, ties to even), and x - hi, an integer of at most 29 bits
+// times 2^(e - 52), goes to FP32 through the rounding integer-to-float
+// conversion and an exponent shift.  The results equal df_from_d's; zeros,
+// and exponents where hi or lo could leave the normal FP32 range
+// (|x| < 2^-73 or >= 2^127), take df_from_d.
+__device__ __forceinline__ f2 df_from_d_fast(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const int ex = (int)((u >> 52) & 0x7ffu);
+  if (ex < 950 || ex > 1149) return df_from_d(x);
+  const uint32_t sign = (uint32_t)(u >> 63) << 31;
+  const uint64_t mant = (u & 0xfffffffffffffull) | (1ull << 52);
+  uint32_t m24 = (uint32_t)(mant >> 29);
+  int rem = (int)(mant & 0x1fffffffu);  // units of 2^(e - 52)
+  if (rem > (1 << 28) || (rem == (1 << 28) && (m24 & 1u))) {
+    ++m24;
+    rem -= 1 << 29;
+  }
+  int eh = ex - 1023 + 127;
+  if (m24 == (1u << 24)) {  // rounded up to the next power of two
+    m24 >>= 1;
+    ++eh;
+  }
+  const float h = __uint_as_float(sign | ((uint32_t)eh << 23) | (m24 & 0x7fffffu));
+  if (rem == 0) return {h, 0.f};
+  const int r = (int)__float_as_uint(__int2float_rn(rem)) + ((ex - 1075) * (1 << 23));
+  return {h, __uint_as_float((uint32_t)r ^ sign)};
+}
 __device__ __forceinline__ f2 df_two_sum(float a, float b) {
   float s = a + b;
   float bb = s - a;
@@ -926,6 +955,7 @@ __global__ void __launch_bounds__(256) k_tp_split_cols(int64_t K, int Kpad, int 
                                                        __nv_bfloat16 *__restrict__ Bt, int *__restrict__ emaxB,
                                                        int *__restrict__ err, int absM) {
   __shared__ double sw[32];
+  __shared__ f2 swf[32];  // sqrt|w_k| as double-FP32
   __shared__ float sgn[32];
   __shared__ __nv_bfloat16 tile[OZ_SLICES][TP_COLS][32 + 8];
   __shared__ f2 mtile[TP_COLS][32 + 1];
@@ -940,6 +970,7 @@ __global__ void __launch_bounds__(256) k_tp_split_cols(int64_t K, int Kpad, int 
     const int64_t k = k0 + threadIdx.x;
     const double w = k < K ? om[k % n_mu] * xw[x0 + k / n_mu] : 0.0;
     sw[threadIdx.x] = sqrt(fabs(w));
+    swf[threadIdx.x] = df_from_d(sw[threadIdx.x]);
     sgn[threadIdx.x] = (w < 0.0 && !absM) ? -1.f : 1.f;
   }
   // the column's exponent for this chunk
@@ -970,12 +1001,14 @@ __global__ void __launch_bounds__(256) k_tp_split_cols(int64_t K, int Kpad, int 
     const int64_t k = k0 + kk;
     double v = (col < nblp && k < K) ? M[k * nblp + col] : 0.0;
     if (absM) v = fabs(v);
-    const f2 vd = df_from_d(v);
+    const f2 vd = df_from_d_fast(v);
     __nv_bfloat16 o[OZ_SLICES];
     split_scaled(sgn[kk] * vd.h, sgn[kk] * vd.l, sc, o);
 #pragma unroll
     for (int s = 0; s < OZ_SLICES; ++s) tile[s][tc][kk] = o[s];
-    mtile[tc][kk] = df_from_d(sw[kk] * v);
+    // M~ = sqrt|w| M in double-FP32 arithmetic (relative error ~2^-46, far
+    // below the 2^-36 of the BF16 slicing)
+    mtile[tc][kk] = df_mul(vd, swf[kk]);
   }
   __syncthreads();
   // B slices: per (slice, column) 64 contiguous bytes; M~: per column 256 bytes
