@@ -161,15 +161,26 @@ __global__ void __launch_bounds__(LEG_NODES) k_legendre_table(int n_mu, const do
   const int L = l_max - l_min + 1;
   const int j0 = blockIdx.x * LEG_NODES;
   const int j = j0 + threadIdx.x;
+  __shared__ double rinv[LEG_LT];  // 1 / (l + 1) for the degrees l of the window
   double x = (j < n_mu) ? mu[j] : 0.0;
   double p0 = 1.0, p1 = x;  // P_{l}, P_{l+1} with l = next degree to emit
   int lnext = 0;            // degree held in p0
+  while (lnext < l_min) {   // up to the first degree (l_min is small)
+    const double p2 = ((2.0 * lnext + 3.0) * x * p1 - (double)(lnext + 1) * p0) / (double)(lnext + 2);
+    p0 = p1;
+    p1 = p2;
+    ++lnext;
+  }
   for (int lb = l_min; lb <= l_max; lb += LEG_LT) {
+    // the divisions of the window's steps, one per thread and off the
+    // recurrence's dependency chain (an FP64 division is a long sequence on
+    // this part's FP64 pipe)
+    if (threadIdx.x < LEG_LT) rinv[threadIdx.x] = 1.0 / (double)(lb + threadIdx.x + 1);
+    __syncthreads();
     for (int c = 0; c < LEG_LT; ++c) {
-      int l = lb + c;
-      // advance the recurrence until p0 = P_l
-      while (lnext < l) {
-        double p2 = ((2.0 * lnext + 3.0) * x * p1 - (double)(lnext + 1) * p0) / (double)(lnext + 2);
+      const int l = lb + c;
+      if (l > lnext) {  // one step: P_l from P_{l-1}, P_{l-2} (divisor l + 1 = (l - 1) + 2)
+        const double p2 = ((2.0 * lnext + 3.0) * x * p1 - (double)(lnext + 1) * p0) * rinv[c];
         p0 = p1;
         p1 = p2;
         ++lnext;

@@ -169,10 +169,48 @@ __device__ __forceinline__ int exp_bound_f(float m) {
   return e;
 }
 
+// double-FP32 values (hi + lo)
+struct f2 {
+  float h, l;
+};
+__device__ __forceinline__ f2 df_from_d(double x) {
+  float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+// The same split with integer operations on the bits of x (this part's FP64
+// pipe runs at 1/64 of the FP32 rate): hi is x rounded to 24 significant
+// bits (to nearest, ties to even), and x - hi, an integer of at most 29 bits
+// times 2^(e - 52), goes to FP32 through the rounding integer-to-float
+// conversion and an exponent shift.  The results equal df_from_d's; zeros,
+// and exponents where hi or lo could leave the normal FP32 range
+// (|x| < 2^-73 or >= 2^127), take df_from_d.
+__device__ __forceinline__ f2 df_from_d_fast(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const int ex = (int)((u >> 52) & 0x7ffu);
+  if (ex < 950 || ex > 1149) return df_from_d(x);
+  const uint32_t sign = (uint32_t)(u >> 63) << 31;
+  const uint64_t mant = (u & 0xfffffffffffffull) | (1ull << 52);
+  uint32_t m24 = (uint32_t)(mant >> 29);
+  int rem = (int)(mant & 0x1fffffffu);  // units of 2^(e - 52)
+  if (rem > (1 << 28) || (rem == (1 << 28) && (m24 & 1u))) {
+    ++m24;
+    rem -= 1 << 29;
+  }
+  int eh = ex - 1023 + 127;
+  if (m24 == (1u << 24)) {  // rounded up to the next power of two
+    m24 >>= 1;
+    ++eh;
+  }
+  const float h = __uint_as_float(sign | ((uint32_t)eh << 23) | (m24 & 0x7fffffu));
+  if (rem == 0) return {h, 0.f};
+  const int r = (int)__float_as_uint(__int2float_rn(rem)) + ((ex - 1075) * (1 << 23));
+  return {h, __uint_as_float((uint32_t)r ^ sign)};
+}
 // Rows of the l-contraction operands.  Row r of A is A[j][l] q_a(l) with
 // r = (j, a); row r of B is q~_p(l, x0 + xl) with r = (xl, p).  One warp per
 // (row, K chunk): pass 1 finds max |x|, pass 2 writes the slices; only the
-// one product A q and the FP64 -> double-FP32 conversion use the FP64 unit.
+// one product A q uses the FP64 unit (the split into double-FP32 is integer
+// work, df_from_d_fast).
 template <bool IS_A>
 __global__ void k_split_lrows(int64_t rows, int L, int Kpad, const double *__restrict__ Atab,
                               const double *__restrict__ q, const double *__restrict__ qt, int nbl, int nbp,
@@ -207,10 +245,9 @@ __global__ void k_split_lrows(int64_t rows, int L, int Kpad, const double *__res
   const int lend = min(Kpad, l0 + OZ_KC);
   for (int l = l0 + lane; l < lend; l += 32) {
     const double v = l < L ? val(l) : 0.0;
-    const float h = __double2float_rn(v);
-    const float lo = __double2float_rn(v - (double)h);
+    const f2 vd = df_from_d_fast(v);
     __nv_bfloat16 o[OZ_SLICES];
-    split_f2(h, lo, e, o);
+    split_f2(vd.h, vd.l, e, o);
 #pragma unroll
     for (int s = 0; s < OZ_SLICES; ++s) out[s * sstride + r * Kpad + l] = o[s];
   }
@@ -836,42 +873,6 @@ cuda_fail:
 //   B operand: M columns (c, t) transposed to K-major, exact per-chunk maxima;
 //   output:    G block b (rows (a,{u,v}), columns (c,t) with c >= b), FP64 add.
 // ===========================================================================
-struct f2 {
-  float h, l;
-};
-__device__ __forceinline__ f2 df_from_d(double x) {
-  float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-// The same split with integer operations on the bits of x (this part's FP64
-// pipe runs at 1/64 of the FP32 rate): hi is x rounded to 24 significant
-// bits (to nearest, ties to even), and x - hi, an integer of at most 29 bits
-// times 2^(e - 52), goes to FP32 through the rounding integer-to-float
-// conversion and an exponent shift.  The results equal df_from_d's; zeros,
-// and exponents where hi or lo could leave the normal FP32 range
-// (|x| < 2^-73 or >= 2^127), take df_from_d.
-__device__ __forceinline__ f2 df_from_d_fast(double x) {
-  const uint64_t u = (uint64_t)__double_as_longlong(x);
-  const int ex = (int)((u >> 52) & 0x7ffu);
-  if (ex < 950 || ex > 1149) return df_from_d(x);
-  const uint32_t sign = (uint32_t)(u >> 63) << 31;
-  const uint64_t mant = (u & 0xfffffffffffffull) | (1ull << 52);
-  uint32_t m24 = (uint32_t)(mant >> 29);
-  int rem = (int)(mant & 0x1fffffffu);  // units of 2^(e - 52)
-  if (rem > (1 << 28) || (rem == (1 << 28) && (m24 & 1u))) {
-    ++m24;
-    rem -= 1 << 29;
-  }
-  int eh = ex - 1023 + 127;
-  if (m24 == (1u << 24)) {  // rounded up to the next power of two
-    m24 >>= 1;
-    ++eh;
-  }
-  const float h = __uint_as_float(sign | ((uint32_t)eh << 23) | (m24 & 0x7fffffu));
-  if (rem == 0) return {h, 0.f};
-  const int r = (int)__float_as_uint(__int2float_rn(rem)) + ((ex - 1075) * (1 << 23));
-  return {h, __uint_as_float((uint32_t)r ^ sign)};
-}
 __device__ __forceinline__ f2 df_two_sum(float a, float b) {
   float s = a + b;
   float bb = s - a;
