@@ -31,7 +31,7 @@ def nvcc() -> str:
 
 
 def _newest_header() -> float:
-    hs = list(CSRC.glob("*.cuh")) + [ROOT / "include" / "modal.h"]
+    hs = list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) + [ROOT / "include" / "modal.h"]
     return max(h.stat().st_mtime for h in hs)
 
 

@@ -34,6 +34,7 @@
 #include "kernels.cuh"
 #include "ptx.cuh"
 #include "tc.cuh"
+#include "mma_plan.h"
 
 namespace modal {
 
@@ -657,83 +658,14 @@ static int make_slices_map(CUtensorMap *m, const void *base, int64_t rows, int K
   return MODAL_OK;
 }
 
-// Schedules of the slice products of one 16-deep K step as runs of MMAs.
-// For A slice sa the B slices sb = 0 .. MAXLEV - sa are needed.  B slices lie
-// w rows apart in shared memory, so a run of n consecutive sb is one MMA with
-// N = n w whose result columns fall on n consecutive accumulators spaced w
-// TMEM columns apart.  Accumulator 0 takes level 0 (sa + sb = 0), 1 takes
-// level 1, and 2, 3, ... take levels >= 2 (summed by the drain).  In a chunk
-// the first MMA on an accumulator overwrites it, so a run touches only fresh
-// or only used accumulators.  Of the schedules that fit in 512 columns the
-// search keeps the one of least issue cost, with an MMA (M = 128, K = 16)
-// costed at max(80, N / 2) clocks -- the rate measured for back-to-back MMAs
-// from one thread, flat up to N = 160.
-struct PlanSearch {
-  int w, nacc, R;
-  double best = 1e30;
-  uint32_t best_plan[OZ_PLAN_MAX];
-  int best_n = 0, best_used = 0;
-  uint32_t cur[OZ_PLAN_MAX];
-  void rec(int sa, int sb, unsigned fresh, double cost, int n, int used) {
-    if (cost >= best || n > OZ_PLAN_MAX) return;
-    if (sa == OZ_SLICES) {
-      best = cost;
-      best_n = n;
-      best_used = used;
-      memcpy(best_plan, cur, sizeof cur);
-      return;
-    }
-    const int nb = OZ_MAXLEV - sa + 1;
-    if (sb >= nb) return rec(sa + 1, 0, fresh, cost, n, used);
-    if (n == OZ_PLAN_MAX) return;
-    for (int len = (R < nb - sb ? R : nb - sb); len >= 1; --len) {
-      const int L = sa + sb;
-      const int lo = L < 2 ? L : 2, hi = L < 2 ? L : nacc - len;
-      for (int a0 = lo; a0 <= hi; ++a0) {
-        if (a0 + len > nacc) continue;
-        bool ok = true, allf = true, nonef = true;
-        for (int t = 0; t < len; ++t) {
-          const int a = a0 + t, lv = L + t;
-          if (!((a >= 2 && lv >= 2) || a == lv)) ok = false;
-          const bool f = (fresh >> a) & 1u;
-          allf = allf && f;
-          nonef = nonef && !f;
-        }
-        if (!ok || !(allf || nonef)) continue;
-        const unsigned mask = ((1u << len) - 1u) << a0;
-        const double c = (len * w / 2.0 > 80.0) ? len * w / 2.0 : 80.0;
-        cur[n] = (uint32_t)sa | (uint32_t)sb << 4 | (uint32_t)len << 8 | (uint32_t)a0 << 12 |
-                 (allf ? 1u << 16 : 0u);
-        rec(sa, sb + len, fresh & ~mask, cost + c, n + 1, used > a0 + len ? used : a0 + len);
-      }
-    }
-  }
-};
-
+// Schedules of the slice products as MMA runs: mma_plan.h (host code).
+static_assert(OZ_SLICES == plan::SLICES && OZ_MAXLEV == plan::MAXLEV && OZ_PLAN_MAX == plan::RUNS_MAX,
+              "the schedules and the kernels agree on the slicing");
 static void fill_mma_plans(uint32_t (&dst)[OZ_BN / 16][1 + OZ_PLAN_MAX]) {
   static uint32_t plans[OZ_BN / 16][1 + OZ_PLAN_MAX];
   static std::once_flag once;
   std::call_once(once, [] {
-    for (int i = 0; i < OZ_BN / 16; ++i) {
-      PlanSearch ps;
-      ps.w = 16 * (i + 1);
-      ps.nacc = 512 / ps.w < 15 ? 512 / ps.w : 15;
-      ps.R = 256 / ps.w < OZ_SLICES ? 256 / ps.w : OZ_SLICES;
-      ps.rec(0, 0, (1u << ps.nacc) - 1u, 0.0, 0, 0);
-      if (ps.best_n == 0) {  // not reached for nacc >= 3; the singles schedule is always valid
-        ps.best_n = 0;
-        for (int sa = 0; sa < OZ_SLICES; ++sa)
-          for (int sb = 0; sa + sb <= OZ_MAXLEV; ++sb) {
-            const int L = sa + sb, acc = L < 2 ? L : 2;
-            ps.best_plan[ps.best_n++] = (uint32_t)sa | (uint32_t)sb << 4 | 1u << 8 | (uint32_t)acc << 12 |
-                                        ((sa == 0 && sb <= 2) ? 1u << 16 : 0u);
-          }
-        ps.best_used = 3;
-      }
-      memset(plans[i], 0, sizeof plans[i]);
-      plans[i][0] = (uint32_t)ps.best_n | (uint32_t)ps.best_used << 8;
-      for (int r = 0; r < ps.best_n; ++r) plans[i][1 + r] = ps.best_plan[r];
-    }
+    for (int i = 0; i < OZ_BN / 16; ++i) plan::mma_plan(16 * (i + 1), plans[i]);
   });
   memcpy(dst, plans, sizeof plans);
 }
