@@ -35,8 +35,15 @@
 #include "ptx.cuh"
 #include "tc.cuh"
 #include "mma_plan.h"
+#include "fp_bits.h"
 
 namespace modal {
+
+// double-FP32 values and FP64 <-> double-FP32 conversions by integer work
+using fpb::df_from_d;
+using fpb::df_from_d_fast;
+using fpb::f2;
+using fpb::f32_scaled_f64;
 
 static thread_local char g_tc_err[256] = "";
 const char *tc_last_error() { return g_tc_err; }
@@ -86,23 +93,6 @@ __device__ __forceinline__ float pow2f(int k) {
 // multiplies contributions far below the FP32 resolution of the result).
 __device__ __forceinline__ float pow2f_or0(int k) {
   return k < -126 ? 0.f : __int_as_float((min(k, 127) + 127) << 23);
-}
-
-// x 2^e as a double, assembled from the bits of x with integer operations
-// (this part's FP64 pipe runs at 1/64 of the FP32 rate, and each epilogue
-// converts 16 K running sums per tile).  Exact; a zero keeps its sign; a
-// subnormal x, or a result outside the normal double range, goes through
-// ldexp.  (hi, lo) of a double-FP32 sum then becomes
-// f32_scaled_f64(hi, e) + f32_scaled_f64(lo, e), one exact FP64 addition.
-__device__ __noinline__ double f32_scaled_f64_slow(float x, int e) { return ldexp((double)x, e); }
-__device__ __forceinline__ double f32_scaled_f64(float x, int e) {
-  const uint32_t u = __float_as_uint(x);
-  const uint64_t sign = (uint64_t)(u >> 31) << 63;
-  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
-  const uint32_t ex = (u >> 23) & 0xffu;
-  const int E = (int)ex + (1023 - 127) + e;
-  if (ex == 0u || ex == 0xffu || E <= 0 || E >= 2047) return f32_scaled_f64_slow(x, e);
-  return __longlong_as_double((long long)(sign | ((uint64_t)E << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
 }
 
 // Scale factors 2^(BETA - e) as two exact float factors (the exponent range of
@@ -170,43 +160,6 @@ __device__ __forceinline__ int exp_bound_f(float m) {
   return e;
 }
 
-// double-FP32 values (hi + lo)
-struct f2 {
-  float h, l;
-};
-__device__ __forceinline__ f2 df_from_d(double x) {
-  float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-// The same split with integer operations on the bits of x (this part's FP64
-// pipe runs at 1/64 of the FP32 rate): hi is x rounded to 24 significant
-// bits (to nearest, ties to even), and x - hi, an integer of at most 29 bits
-// times 2^(e - 52), goes to FP32 through the rounding integer-to-float
-// conversion and an exponent shift.  The results equal df_from_d's; zeros,
-// and exponents where hi or lo could leave the normal FP32 range
-// (|x| < 2^-73 or >= 2^127), take df_from_d.
-__device__ __forceinline__ f2 df_from_d_fast(double x) {
-  const uint64_t u = (uint64_t)__double_as_longlong(x);
-  const int ex = (int)((u >> 52) & 0x7ffu);
-  if (ex < 950 || ex > 1149) return df_from_d(x);
-  const uint32_t sign = (uint32_t)(u >> 63) << 31;
-  const uint64_t mant = (u & 0xfffffffffffffull) | (1ull << 52);
-  uint32_t m24 = (uint32_t)(mant >> 29);
-  int rem = (int)(mant & 0x1fffffffu);  // units of 2^(e - 52)
-  if (rem > (1 << 28) || (rem == (1 << 28) && (m24 & 1u))) {
-    ++m24;
-    rem -= 1 << 29;
-  }
-  int eh = ex - 1023 + 127;
-  if (m24 == (1u << 24)) {  // rounded up to the next power of two
-    m24 >>= 1;
-    ++eh;
-  }
-  const float h = __uint_as_float(sign | ((uint32_t)eh << 23) | (m24 & 0x7fffffu));
-  if (rem == 0) return {h, 0.f};
-  const int r = (int)__float_as_uint(__int2float_rn(rem)) + ((ex - 1075) * (1 << 23));
-  return {h, __uint_as_float((uint32_t)r ^ sign)};
-}
 // Rows of the l-contraction operands.  Row r of A is A[j][l] q_a(l) with
 // r = (j, a); row r of B is q~_p(l, x0 + xl) with r = (xl, p).  One warp per
 // (row, K chunk): pass 1 finds max |x|, pass 2 writes the slices; only the
