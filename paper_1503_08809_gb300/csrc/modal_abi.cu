@@ -16,6 +16,7 @@
 #include "kernels.cuh"
 #include "tc.cuh"
 #include "backward.cuh"
+#include "batch_plan.h"
 #include "gram.cuh"
 #include "profile.cuh"
 
@@ -638,38 +639,18 @@ static double problem_cost(const modal_problem *p, int n_mu) {
   return ((double)g.size() + L * p->nb_late * p->nb_prim) * (double)p->n_x * (double)n_mu;
 }
 
-// A batch spread over `ns` streams: problems in decreasing cost, each to the
-// least loaded stream (longest processing time first); each stream owns a
-// scratch block of its largest plan.
-struct BatchLayout {
-  int ns;
-  std::vector<int> stream_of;
-  size_t off[MAX_BATCH_STREAMS + 1];
-};
+// A batch spread over `ns` streams (batch_plan.h: longest first, each to
+// the least loaded stream; one scratch block per stream)
+using BatchLayout = batch::Layout;
+static_assert(batch::MAX_STREAMS == MAX_BATCH_STREAMS, "one stream limit");
 static BatchLayout batch_layout(int n, const modal_problem *probs, const std::vector<SepPlan> &plans, int ns) {
-  BatchLayout bl;
-  bl.ns = ns;
-  bl.stream_of.assign(n, 0);
-  std::vector<int> order(n);
   std::vector<double> cost(n);
+  std::vector<size_t> bytes(n);
   for (int i = 0; i < n; ++i) {
-    order[i] = i;
     cost[i] = problem_cost(&probs[i], plans[i].s.n_mu);
+    bytes[i] = plans[i].bytes;
   }
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-  double load[MAX_BATCH_STREAMS] = {};
-  size_t need[MAX_BATCH_STREAMS] = {};
-  for (int i : order) {
-    int best = 0;
-    for (int k = 1; k < ns; ++k)
-      if (load[k] < load[best]) best = k;
-    bl.stream_of[i] = best;
-    load[best] += cost[i];
-    need[best] = plans[i].bytes > need[best] ? plans[i].bytes : need[best];
-  }
-  bl.off[0] = 0;
-  for (int k = 0; k < ns; ++k) bl.off[k + 1] = bl.off[k] + align256(need[k] ? need[k] : 256);
-  return bl;
+  return batch::layout(n, cost.data(), bytes.data(), ns);
 }
 
 // Capture every launch of the batch into one graph, the problems of stream k
