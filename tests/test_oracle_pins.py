@@ -545,3 +545,30 @@ def test_smooth_weights_improve_with_grid_density():
         g, dw = syn.stepped_l_grid(160, step, dense_to=20)
         err.append(np.sqrt(np.mean((u(oracle.direct(P, g, dw, oracle.SMOOTH)) - u(dense)) ** 2)))
     assert err[1] < err[0] / 10
+
+
+def test_gram_delta_basis_closed_forms():
+    """Gram matrices of delta-function bases in closed form (Eq. 2D with
+    q~ := q, the Gaunt integral of Section 2.2 and tabulated 3j values, Gram
+    weight (2l+1)^(2/3)):
+      one function at l = 2, mode (000):
+        1/(48 pi) * 6 * (5^(2/3))^3 * 2 (2 2 2;000)^2 = 6*25*2*(2/35)/(48 pi) = 5/(14 pi);
+      functions at l = 2, 4, mode (001) with itself: perm = 2 M_00^2 M_11, so
+        1/(48 pi) * 2 * 5^(4/3) * 9^(2/3) * 2 (2 2 4;000)^2, (2 2 4;000)^2 = 2/35."""
+    def problem(ls):
+        l_min, l_max = 2, 6
+        L = l_max - l_min + 1
+        q = np.zeros((len(ls), L))
+        for a, l in enumerate(ls):
+            q[a, l - l_min] = 1.0
+        modes = syn.mode_list(len(ls))
+        return syn.Problem(l_min=l_min, l_max=l_max, nb_late=len(ls), nb_prim=len(ls), n_x=1, q=q,
+                           qt=q[None].copy(), w_l=np.ones(L), x=np.zeros(1), phi=np.zeros(len(ls)),
+                           late_modes=modes, prim_modes=modes)
+    P = problem([2])
+    g = oracle.gram(P, syn.gram_weights(2, 6))
+    assert g[0, 0] == pytest.approx(5.0 / (14.0 * math.pi), rel=1e-13)
+    P = problem([2, 4])
+    g = oracle.gram(P, syn.gram_weights(2, 6), late=np.array([[0, 0, 1]], dtype=np.int32))
+    expect = 2.0 * 5.0 ** (4.0 / 3.0) * 9.0 ** (2.0 / 3.0) * 2.0 * (2.0 / 35.0) / (48.0 * math.pi)
+    assert g[0, 0] == pytest.approx(expect, rel=1e-13)
