@@ -572,3 +572,16 @@ def test_gram_delta_basis_closed_forms():
     g = oracle.gram(P, syn.gram_weights(2, 6), late=np.array([[0, 0, 1]], dtype=np.int32))
     expect = 2.0 * 5.0 ** (4.0 / 3.0) * 9.0 ** (2.0 / 3.0) * 2.0 * (2.0 / 35.0) / (48.0 * math.pi)
     assert g[0, 0] == pytest.approx(expect, rel=1e-13)
+
+
+def test_mode_order_follows_the_appendix_example():
+    """The n -> ijk map of the input generator starts as in Appendix A's
+    example (000, 001, 011, 111, 002, 012, ...), lists each sorted triple
+    once, and has C(nb+2, 3) modes."""
+    m = syn.mode_list(4)
+    assert [tuple(r) for r in m[:6]] == [(0, 0, 0), (0, 0, 1), (0, 1, 1), (1, 1, 1), (0, 0, 2), (0, 1, 2)]
+    for nb in (1, 5, 20):
+        m = syn.mode_list(nb)
+        assert m.shape == (math.comb(nb + 2, 3), 3)
+        assert all(a <= b <= c < nb for a, b, c in m)
+        assert len({tuple(r) for r in m}) == m.shape[0]
