@@ -36,6 +36,7 @@
 #include "tc.cuh"
 #include "mma_plan.h"
 #include "fp_bits.h"
+#include "oz_split.h"
 
 namespace modal {
 
@@ -110,32 +111,11 @@ __device__ __forceinline__ SplitScale split_scale(int e) {
   return r;
 }
 
-// Slices of a double-FP32 value scaled so that |H + L| <= 2^BETA (BETA = 7,
-// five slices).  Slice s is the running residual rounded to a multiple of
-// 2^(-BETA s) (round to nearest, by adding and removing 1.5 2^(23 - BETA s)),
-// so each slice carries its own weight.  The first three slices come from H
-// alone, with exact residuals; the residual is then at most 2^-15 and takes
-// the low part L in one FP32 addition whose rounding is below 2^-37; the
-// last two slices come from that sum.  Slices s >= 1 are integer multiples
-// of 2^(-BETA s) of magnitude <= 64, except the fourth: <= 64 + |L| 2^21,
-// which stays below 256 for |L| <= 2^-14 -- so every slice is exact in BF16
-// and the levels 0 and 1 never see L.  |H + L - sum of slices| <= 2^-29 +
-// 2^-37 (2^-36 of the scale 2^7).
-__host__ __device__ constexpr float oz_pow2c(int k) {
-  return k >= 0 ? (float)(1ull << k) : 1.0f / (float)(1ull << -k);
-}
-constexpr int OZ_FOLD = 3;  // slice before which L joins the residual
-static_assert(OZ_BETA == 7 && OZ_SLICES == 5, "the bounds of split_hl are stated for 5 slices of 7 bits");
-__device__ __forceinline__ void split_hl(float H, float L, float (&q)[OZ_SLICES]) {
-  float r = H;
-#pragma unroll
-  for (int s = 0; s < OZ_SLICES; ++s) {
-    const float m = 1.5f * oz_pow2c(23 - OZ_BETA * s);
-    if (s == OZ_FOLD) r = __fadd_rn(r, L);
-    q[s] = __fsub_rn(__fadd_rn(r, m), m);
-    if (s + 1 < OZ_SLICES) r = __fsub_rn(r, q[s]);  // exact
-  }
-}
+// The slicing of one double-FP32 value: oz_split.h (host and device code).
+static_assert(OZ_BETA == ozs::BETA && OZ_SLICES == ozs::SLICES, "one slicing for splits and kernels");
+constexpr int OZ_FOLD = ozs::FOLD;  // slice before which L joins the residual
+using ozs::split_hl;
+__host__ __device__ constexpr float oz_pow2c(int k) { return ozs::pow2c(k); }
 
 __device__ __forceinline__ void split_scaled(float h, float l, const SplitScale &sc,
                                               __nv_bfloat16 (&out)[OZ_SLICES]) {
