@@ -1,11 +1,12 @@
-// fp_bits.h -- conversions between FP64 and double-FP32 (hi + lo) by
-// integer operations on the bits, for the tensor-core form's prologue and
-// epilogues: this part's FP64 pipe runs at 1/64 of the FP32 rate, and these
-// conversions touch every value of M and every running sum of a tile.  Each
-// function equals its plain-FP64 counterpart bit for bit (the same rounding),
-// with the FP64 route kept for the rare inputs outside the fast path.  The
-// file compiles as CUDA device code and as host C++, so the CPU tests check
-// the equalities with g++ (tests/test_fp_bits.py).
+// fp_bits.h -- double-FP32 values (hi + lo) of the tensor-core form: their
+// running sum, and conversions between FP64 and double-FP32 by integer
+// operations on the bits, for the prologue and the epilogues (this part's
+// FP64 pipe runs at 1/64 of the FP32 rate, and these conversions touch every
+// value of M and every running sum of a tile).  Each conversion equals its
+// plain-FP64 counterpart bit for bit (the same rounding), with the FP64 route
+// kept for the rare inputs outside the fast path.  The file compiles as CUDA
+// device code and as host C++, so the CPU tests check it with g++
+// (tests/test_fp_bits.py).
 #pragma once
 #include <cmath>
 #include <cstdint>
@@ -122,6 +123,20 @@ FPB_HD f2 df_from_d_fast(double x) {
   if (rem == 0) return {h, 0.f};
   const int r = (int)f_bits(int_to_f_rn(rem)) + ((ex - 1075) * (1 << 23));
   return {h, f_from((uint32_t)r ^ sign)};
+}
+
+// (hi, lo) += (bh, bl): the running double-FP32 sums of the GEMM drains
+// (compensated summation of the chunk sums across the slices).  The high
+// parts meet in an error-free two-sum (Knuth); the low parts and that error
+// are added in FP32 and the pair is renormalised -- ~2^-48 of the sum per
+// step, FP32 operations only.
+FPB_HD void df_add(float &hi, float &lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  float e = (hi - (s - bb)) + (bh - bb);
+  e += lo + bl;
+  hi = s + e;
+  lo = e - (hi - s);
 }
 
 }  // namespace fpb

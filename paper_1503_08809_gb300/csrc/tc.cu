@@ -45,6 +45,7 @@ using fpb::df_from_d;
 using fpb::df_from_d_fast;
 using fpb::f2;
 using fpb::f32_scaled_f64;
+using fpb::df_add;
 
 static thread_local char g_tc_err[256] = "";
 const char *tc_last_error() { return g_tc_err; }
@@ -235,14 +236,6 @@ struct OzParams {
   long long wait_cycles;
 };
 
-__device__ __forceinline__ void df_add(float &hi, float &lo, float bh, float bl) {
-  float s = hi + bh;
-  float bb = s - hi;
-  float e = (hi - (s - bb)) + (bh - bb);
-  e += lo + bl;
-  hi = s + e;
-  lo = e - (hi - s);
-}
 
 // Width of the column tiles of a G block with `cols` columns: the block is cut
 // into ceil(cols / 128) tiles of equal width, rounded up to a multiple of 16
