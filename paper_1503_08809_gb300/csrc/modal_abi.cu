@@ -861,7 +861,7 @@ extern "C" int modal_project_separable_noalloc(const modal_problem *p, const mod
   if (prec != MODAL_PREC_FP64 && prec != MODAL_PREC_FP32)
     return fail(nullptr, MODAL_EINVAL, "the allocation-free entry point serves MODAL_PREC_FP64 and MODAL_PREC_FP32");
   // largest radial chunk whose scratch fits the static buffer
-  modal_opts oo = o ? *o : modal_opts{0, MODAL_PREC_FP64, 0, 0};
+  modal_opts oo = o ? *o : modal_opts{0, MODAL_PREC_FP64, 0, 0, nullptr};
   SepPlan pl;
   if (int r = plan_separable(nullptr, p, &oo, pl, nd.num_sms)) return r;
   int nxc = pl.nxc;

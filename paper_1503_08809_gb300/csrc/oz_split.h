@@ -53,7 +53,9 @@ OZS_HD float sub_rn(float a, float b) {
 
 OZS_HD void split_hl(float H, float L, float (&q)[SLICES]) {
   float r = H;
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
   for (int s = 0; s < SLICES; ++s) {
     const float m = 1.5f * pow2c(23 - BETA * s);
     if (s == FOLD) r = add_rn(r, L);
