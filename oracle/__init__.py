@@ -7,9 +7,10 @@ library.  Each wrapper names the passage of arXiv 1503.08809 it follows; the
 C file has the derivations.
 
 Parity status: all functions (including ``gram`` and ``full_gamma``) pinned by
-``tests/test_oracle_pins.py`` except
-``direct(..., weight_mode=SMOOTH)`` on sparse grids (an approximation of the
-dense sum): parity unpinned there.
+``tests/test_oracle_pins.py``.  ``direct(..., weight_mode=SMOOTH)`` on sparse
+grids is pinned to its formula (a literal cube sum on a small grid), but it
+only approximates the dense sum: how close it comes is measured and
+reported, not pinned.
 """
 from __future__ import annotations
 

@@ -585,3 +585,42 @@ def test_mode_order_follows_the_appendix_example():
         assert m.shape == (math.comb(nb + 2, 3), 3)
         assert all(a <= b <= c < nb for a, b, c in m)
         assert len({tuple(r) for r in m}) == m.shape[0]
+
+
+def brute_force_direct_grid(P, grid, dw, xw, weight):
+    """Eq. 3D on a multipole grid, literally: the ordered cube of grid points,
+    (1/(144 pi)) dw1 dw2 dw3 w1 w2 w3 H(l1,l2,l3) [sum_perm q q q]
+    [sum_x W_x sum_perm q~ q~ q~]."""
+    G = np.zeros((P.n_late, P.n_prim))
+    for (i1, l1), (i2, l2), (i3, l3) in itertools.product(list(enumerate(grid)), repeat=3):
+        H = weight(l1, l2, l3)
+        if H == 0.0:
+            continue
+        k = (l1 - P.l_min, l2 - P.l_min, l3 - P.l_min)
+        wgt = dw[i1] * dw[i2] * dw[i3] * P.w_l[k[0]] * P.w_l[k[1]] * P.w_l[k[2]] * H / (144.0 * math.pi)
+        Q = np.array([sum(P.q[a, k[0]] * P.q[b, k[1]] * P.q[c, k[2]]
+                          for a, b, c in itertools.permutations(m)) for m in P.late_modes])
+        Qt = np.array([sum(xw[x] * sum(P.qt[x, a, k[0]] * P.qt[x, b, k[1]] * P.qt[x, c, k[2]]
+                                       for a, b, c in itertools.permutations(m))
+                           for x in range(P.n_x)) for m in P.prim_modes])
+        G += wgt * np.outer(Q, Qt)
+    return G
+
+
+@pytest.mark.parametrize("mode", ["exact", "smooth"])
+def test_direct_sparse_grid_formula_brute_force(mode):
+    """The sparse-grid direct sum (reading of the unstated weights: EXACT =
+    exact 3j^2 with triangle and parity, SMOOTH = 1/2 Gosper 3j^2 with the
+    triangle only, both times prod dw) equals the literal cube sum above on a
+    stepped grid.  This pins the oracle's SMOOTH formula; how well SMOOTH
+    approximates the dense sum stays unpinned (an approximation)."""
+    P = syn.make_problem(30, 2, 2, seed=13)
+    grid, dw = syn.stepped_l_grid(30, 3, dense_to=10)
+    xw = oracle.x_weights(P.x)
+    if mode == "exact":
+        weight, wm = oracle.threej000_sq, oracle.EXACT
+    else:
+        weight, wm = (lambda a, b, c: 0.5 * oracle.gosper_threej000_sq(a, b, c)), oracle.SMOOTH
+    ref = brute_force_direct_grid(P, grid, dw, xw, weight)
+    got = oracle.direct(P, l_grid=grid, l_dw=dw, weight_mode=wm, xw=xw)
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-12
