@@ -23,9 +23,10 @@
  *   gamma [nlate][nprim]  row n = late mode, column n' = primordial mode.
  *
  * parity status: every function here is pinned by tests/test_oracle_pins.py
- * (closed forms, exact rationals, brute force, identities) except
- * oracle_direct in SMOOTH (Gosper) weight mode on sparse grids, whose
- * agreement with the dense sum is an approximation: parity unpinned there.
+ * (closed forms, exact rationals, brute force, identities).  oracle_direct in
+ * SMOOTH (Gosper) weight mode is pinned to its formula (a literal cube sum on
+ * a small grid); its agreement with the dense sum on sparse grids is an
+ * approximation, measured but not pinned.
  */
 #include <float.h>
 #include <math.h>
@@ -325,7 +326,7 @@ void oracle_separable_abs(int l_min, int l_max, int nbl, int nbp, int nx,
 /* l2 >= l1, l3 >= l2 loop bounds.                                            */
 /* weight_mode 0 (EXACT): exact 3j^2 (zero off triangle and odd parity).     */
 /* weight_mode 1 (SMOOTH): 1/2 x Gosper 3j^2, triangle only (parity averaged) */
-/*   -- an approximation for sparse grids; parity unpinned.                  */
+/*   -- an approximation of the dense sum on sparse grids.                   */
 /* ------------------------------------------------------------------------ */
 void oracle_direct(int l_min, int l_max, int nbl, int nbp, int nx, const double *q,
                    const double *qt, const double *wl, const double *xw, int ng,
