@@ -6,19 +6,23 @@
 // run as C = A B^T over K on 5th-generation tensor cores:
 //
 //  * every row of A and B is scaled by a power of two 2^e (per K chunk) so
-//    that |x / 2^e| <= 1, then written as five BF16 slices of 7 bits each:
-//    x / 2^e * 2^7 = q0 + q1 2^-7 + q2 2^-14 + q3 2^-21 + q4 2^-28 (35 bits),
-//    |q0| <= 128, |qs| <= 64 (up to 72 for the last);
-//  * the 15 slice products with s + t <= 4 are issued as tcgen05.mma into
-//    three TMEM accumulators: level 0 (q0 q0'), level 1 (q0 q1' + q1 q0') and
-//    levels 2-4.  With at most 1024 K terms per chunk the level-0 and level-1
-//    partial sums are integers (in units of 1 and 2^-7) of magnitude at most
-//    2^24, hence exact in the FP32 accumulator whatever the summation order;
+//    that |x / 2^e| <= 1, then written as five BF16 slices of 7 bits each
+//    (oz_split.h): x / 2^e * 2^7 = q0 + q1 2^-7 + q2 2^-14 + q3 2^-21 +
+//    q4 2^-28 (35 bits), |q0| <= 128, |qs| <= 64 except the fourth, which
+//    takes the low part of the double-FP32 value (<= 192);
+//  * the 15 slice products with s + t <= 4 are issued as runs of
+//    tcgen05.mma (mma_plan.h: consecutive B slices of one A slice in one MMA)
+//    into four or five TMEM accumulators: level 0 (q0 q0'), level 1
+//    (q0 q1' + q1 q0') and levels 2-4 on the others.  With at most 1024 K
+//    terms per chunk the level-0 and level-1 partial sums are integers (in
+//    units of 1 and 2^-7) of magnitude at most 2^24, hence exact in the FP32
+//    accumulator whatever the summation order;
 //  * at the end of each chunk the epilogue warps read the accumulators
 //    (tcgen05.ld), apply the row and column scales and add the chunk into a
-//    double-FP32 (hi, lo) running sum held in registers, offset by a global
-//    exponent bias so that the FP32 range cannot overflow.  The result is
-//    written (or added) in FP64.
+//    double-FP32 (hi, lo) running sum (hi in registers, lo in shared
+//    memory; fp_bits.h), offset by a global exponent bias so that the FP32
+//    range cannot overflow.  The result is written (or added) in FP64, its
+//    conversion assembled from the bits (fp_bits.h).
 //
 // Operands are staged by TMA (cp.async.bulk.tensor, 64-byte swizzle) in a
 // two-stage mbarrier pipeline; one thread issues the MMAs.  Every wait is
