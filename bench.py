@@ -12,7 +12,8 @@ functions (1540 modes each side), 500 radial points, N_mu = 3001, i.e.
 
 Under torchrun (N > 1) every rank projects its own independent problem (a
 different seed): weak scaling with no collective on the data path; the time
-is the max over ranks.
+is the max over ranks.  With --shard x the ranks split the radial points of
+ONE problem and sum Gamma' with an all-reduce (strong scaling).
 """
 from __future__ import annotations
 
@@ -33,16 +34,18 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "Γ_nm (x,μ)-slices/s and % tensor peak vs plain FP64 GPU at stated error"
-PREC = {"fp64": 0, "fp32": 1, "ozaki": 2}
-DTYPE = {"fp64": "f64", "fp32": "f32", "ozaki": "bf16x(ozaki)+f64"}
+PREC = {"fp64": 0, "fp32": 1, "ozaki": 2, "tf32": 3, "bf16x3": 4}
+DTYPE = {"fp64": "f64", "fp32": "f32", "ozaki": "bf16x(ozaki)+f64", "tf32": "tf32+f32", "bf16x3": "bf16x3+f32"}
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates of the part
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (CUDA cores), nominal figure
 FP32_TFLOPS = 73.3           # GB300 FP32 FMA rate measured on this machine with an FMA-chain kernel
 TC_SLICE_PRODUCTS = 15       # BF16 slice products per useful MAC in the tensor-core form
 # DRAM bytes (read + write) per launch of the workload's size, from one ncu
-# capture (profiles/k_ozaki_gemm_triple_planck.md: n_x = 4 gives one launch
-# with the same K as every launch of the 500-point step).  Kept only while
-# the kernels are unchanged since that capture.
-NCU_TRAFFIC = {"tc_gemm_triple": 5.557e9 + 48.4e6, "tc_make_Y": 44.4e6 + 5.245e9}
+# capture (n_x = 4 gives one launch with the same K as every launch of the
+# 500-point step), keyed by the kernel's form.  A form that changed since its
+# capture is left out (its traffic is then reported as null).
+NCU_TRAFFIC = {("tc_gemm_triple", "single"): 5.557e9 + 48.4e6, ("tc_make_Y", "single"): 44.4e6 + 5.245e9,
+               ("tc_make_Y", "pair"): 44.4e6 + 5.245e9}
 # kernels inside one profiler scope (the library counts kernels; a roofline
 # divides the scope's time by its scope count)
 SCOPE_KERNELS = {"tc_make_Y": 2, "tc_prep_M": 2}
@@ -72,6 +75,12 @@ def parse():
     ap.add_argument("--tc-fused", type=int, default=0, choices=[0, 1, 2],
                     help="tensor-core triple product: 0 = Y through HBM, 1 and 2 = Y formed in "
                          "shared memory (two forms)")
+    ap.add_argument("--shard", default="none", choices=["none", "x"],
+                    help="none: one independent problem per rank (weak scaling); x: the radial "
+                         "points of one problem split over the ranks, Gamma' summed by an "
+                         "all-reduce (strong scaling)")
+    ap.add_argument("--tc-pair", type=int, default=1, choices=[0, 1],
+                    help="tensor-core triple product GEMM on CTA pairs (2-SM MMA): 1, or single CTAs: 0")
     ap.add_argument("--once", action="store_true",
                     help="run one projection and exit (a small case for profiler captures)")
     ap.add_argument("--fp64-x", type=int, default=20,
@@ -230,15 +239,20 @@ def run_ours(args):
 
     prec_name = "ozaki" if args.precision == "auto" else args.precision
     prec = PREC[prec_name]
-    P = syn.planck_size(seed=1 + rank, n_x=args.n_x)
+    sharded = args.shard == "x"
+    P = syn.planck_size(seed=1 if sharded else 1 + rank, n_x=args.n_x)
     h = mg.Handle(dev)
     mg.set_option(mg.OPT_TC_TRIPLE_FUSED, args.tc_fused, handle=h)
+    mg.set_option(mg.OPT_TC_PAIR, args.tc_pair, handle=h)
     dp = mg.DeviceProblem.from_host(P, device=dev, handle=h)
     gamma = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream(dev)
 
     def step():
-        mg.project_separable(dp, precision=prec, out=gamma, handle=h)
+        if sharded:
+            mg.project_separable_sharded(dp, rank, ws, precision=prec, out=gamma, handle=h)
+        else:
+            mg.project_separable(dp, precision=prec, out=gamma, handle=h)
 
     for _ in range(args.warmup):
         step()
@@ -273,13 +287,15 @@ def run_ours(args):
         nm = names.raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
         prof[nm] = (int(launches[i]), float(tms[i]))
     ms_max = max_over_ranks(ms, ws, dev)
-    value = ws * P.slices / (ms_max * 1e-3)
+    job_slices = P.slices if sharded else ws * P.slices
+    value = job_slices / (ms_max * 1e-3)
 
     # ---- rooflines: the dominant kernel, and every tensor / HBM kernel ------
     peaks, src = measured_peaks()
     launches_per_step = {k: max(1, v[0] // args.steps) for k, v in prof.items()}
-    rooflines = {k: kernel_roofline(k, prof[k], launches_per_step[k], P, prec_name, peaks, src, args.steps, ms)
-                 for k in prof}
+    form = "pair" if args.tc_pair else "single"
+    rooflines = {k: kernel_roofline(k, prof[k], launches_per_step[k], P, prec_name, peaks, src, args.steps, ms,
+                                    form) for k in prof}
     rooflines = {k: v for k, v in rooflines.items() if v is not None}
     dom = max(prof, key=lambda k: prof[k][1]) if prof else None
     roof = rooflines.get(dom)
@@ -302,7 +318,10 @@ def run_ours(args):
                 d.copy_(s, non_blocking=True)
             xw = mg.x_weights(dx, handle=h)
             dpe = mg.DeviceProblem(dq, dqt, dw, xw, dl, dpm, P.l_min, P.l_max, dev)
-            g = mg.project_separable(dpe, precision=prec, out=gamma, handle=h)
+            if sharded:
+                g = mg.project_separable_sharded(dpe, rank, ws, precision=prec, out=gamma, handle=h)
+            else:
+                g = mg.project_separable(dpe, precision=prec, out=gamma, handle=h)
             hg.copy_(g, non_blocking=True)
 
         e2e_step()
@@ -315,7 +334,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         barrier(ws)
         ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws, dev)
-        e2e = {"value": ws * P.slices / (ms_e2e * 1e-3), "unit": "slices/s",
+        e2e = {"value": job_slices / (ms_e2e * 1e-3), "unit": "slices/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank != 0:
@@ -330,20 +349,23 @@ def run_ours(args):
         cpu = {"value": v, "unit": "slices/s", "cores": cores, "kind": "oracle", "sample": desc}
     line = {"metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
             "dtype": DTYPE[prec_name], "data": "synthetic",
             "config": {"workload": P.name, "l_max": P.l_max, "nb": P.nb_late, "n_x": P.n_x,
                        "n_mu": P.n_mu, "slices": P.slices, "precision": prec_name,
                        "n_modes": P.n_late, "tc_triple": ["Y through HBM", "shared-memory Y",
                                                           "shared-memory Y (16 warps)"][args.tc_fused],
-                       "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)"},
+                       "tc_gemm": "CTA pairs (2-SM MMA)" if args.tc_pair else "single CTAs",
+                       "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)",
+                       "parallelism": (f"x-sharded over {ws} ranks, FP64 all-reduce of Gamma'" if sharded
+                                       else f"{ws} independent problem(s)")},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "fp64_gpu": fp64, "error": err, "kernel_rooflines": rooflines,
             "clocks": clk, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
 
 
-def kernel_roofline(name, rec, per_step, P, prec_name, peaks, src, steps, ms):
+def kernel_roofline(name, rec, per_step, P, prec_name, peaks, src, steps, ms, form="single"):
     """Achieved algorithmic work per launch / mean launch time against the
     measured peak of the unit that bounds the kernel (None if not modelled)."""
     nl, tot = rec
@@ -367,6 +389,18 @@ def kernel_roofline(name, rec, per_step, P, prec_name, peaks, src, steps, ms):
         extra = {"flops_counted": f"issued tensor flops ({TC_SLICE_PRODUCTS} BF16 slice products "
                                   "per useful MAC)",
                  "useful_achieved": 2.0 * macs * k / avg_s / 1e12}
+    elif name in ("fa_gemm_l_tf32", "fa_gemm_l_bf16x3"):
+        # the l contraction with FP32 accumulation: 1 TF32 or 3 BF16 products per useful MAC
+        macs = P.nb_late * P.nb_prim * P.L
+        nprod = 1 if name.endswith("tf32") else 3
+        k_launch = P.slices / per_step           # slices per launch
+        work, unit, bound = nprod * 2.0 * macs * k_launch, "TFLOP/s", "tensor"
+        if name.endswith("tf32"):
+            peak, note = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16, f"tf32 = bf16 {src} x nominal 1.1/2.25"
+        else:
+            peak, note = peaks["bf16_tflops"], f"bf16 {src}"
+        extra = {"flops_counted": f"issued tensor flops ({nprod} product(s) per useful MAC)",
+                 "useful_achieved": 2.0 * macs * k_launch / avg_s / 1e12}
     elif name == "tc_make_Y":
         rows = g2 * P.nb_late * (P.nb_late + 1) // 2
         work = 10.0 * rows * kpad + 8.0 * P.nb_late * P.nb_prim * kpad   # Y slices out, M~ in
@@ -376,7 +410,7 @@ def kernel_roofline(name, rec, per_step, P, prec_name, peaks, src, steps, ms):
     scale = 1e9 if bound == "hbm" else 1e12
     achieved = work / avg_s / scale
     r = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-         "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name) if P.n_x == 500 else None,
+         "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((name, form)) if P.n_x == 500 else None,
          "peak_source": note, "kernel_ms_avg": avg_s * 1e3, "launches_per_step": per_step,
          "kernel_share_of_step": tot / (ms * steps)}
     r.update(extra)
@@ -434,6 +468,7 @@ def run_once(args):
     prec = PREC["ozaki" if args.precision == "auto" else args.precision]
     P = syn.planck_size(n_x=args.n_x)
     mg.set_option(mg.OPT_TC_TRIPLE_FUSED, args.tc_fused)
+    mg.set_option(mg.OPT_TC_PAIR, args.tc_pair)
     g = mg.project_separable(mg.DeviceProblem.from_host(P), precision=prec)
     if prec == PREC["ozaki"]:
         mg.handle_status()
@@ -626,9 +661,10 @@ def run_extra(args):
             cfg["parts_ms"][name] = e0.elapsed_time(e1) / args.steps
         _, info = mg.gram_solve(S, gp, handle=h, raise_if_not_pd=False)
         assert int(info.item()) == 0
+    dtype = "f64" if args.workload == "direct" else DTYPE[prec_name]   # the direct form is FP64 throughout
     print(json.dumps({"metric": METRIC, "value": slices / (ms * 1e-3), "unit": unit,
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                      "higher_is_better": True, "dtype": DTYPE[prec_name], "data": "synthetic",
+                      "higher_is_better": True, "dtype": dtype, "data": "synthetic",
                       "config": cfg}), flush=True)
 
 

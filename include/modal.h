@@ -49,6 +49,13 @@ typedef struct CUstream_st *modal_stream_t;
 #define MODAL_PREC_OZAKI_BF16 2  /* tcgen05 tensor cores: operands split into
                                     exponent-aligned BF16 slices, exact FP32
                                     chunk sums, FP64 accumulation */
+#define MODAL_PREC_TF32 3        /* l contraction on tcgen05 in TF32 (kind::tf32,
+                                    one product, FP32 accumulation); triple
+                                    product as MODAL_PREC_FP32 (FP32 products,
+                                    compensated sums of the slices) */
+#define MODAL_PREC_BF16X3 4      /* l contraction on tcgen05 with BF16 hi/lo
+                                    operands, hi hi' + hi lo' + lo hi' (FP32
+                                    accumulation); triple product as FP32 */
 
 /* radial quadrature (modal_x_weights) */
 #define MODAL_XW_TRAPEZOID 0  /* trapezium rule (Section 3.2.4), times x^2 */
@@ -126,6 +133,9 @@ int modal_handle_status(modal_handle *h);
  *   up to ~21 functions; larger ones use 0).  All give the same results to
  *   rounding; 0 is the fastest at the sizes measured.
  * MODAL_OPT_TC_SPLIT_K: K splits of the shared-memory variant (0 = automatic).
+ * MODAL_OPT_TC_PAIR: 1 runs the triple-product GEMM of MODAL_OPT_TC_TRIPLE_FUSED = 0
+ *   on CTA pairs (clusters of two, 2-SM tcgen05 MMA with M = 256: each SM
+ *   reads half of the B operand); 0 on single CTAs.  Same results to rounding.
  * MODAL_OPT_BATCH_STREAMS: concurrent streams of modal_project_separable_batched
  *   (1 .. 8), or 0 (default): the first call for a problem set captures one
  *   graph each for 1, 2, 4 and 8 streams (as far as their scratch fits),
@@ -133,6 +143,7 @@ int modal_handle_status(modal_handle *h);
 #define MODAL_OPT_TC_TRIPLE_FUSED 1
 #define MODAL_OPT_TC_SPLIT_K 2
 #define MODAL_OPT_BATCH_STREAMS 3
+#define MODAL_OPT_TC_PAIR 4
 int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value);
 
 /* Bound (in SM clock cycles) of those device-side waits for later calls on
@@ -174,8 +185,9 @@ int modal_x_weights(modal_handle *h, int32_t kind, int32_t n_x, const double *x,
 /* l contraction of Eq. legendre for every (x, mu_j) slice:
  *   M[x][j][a][p] = sum_l A[j][l] q_a(l) q~_p(l, x),   A from modal_legendre_table.
  * A: device [n_mu][L]; M: device [n_x][n_mu][nb_late][nb_prim] FP64.
- * precision: MODAL_PREC_FP64 (CUDA cores) or MODAL_PREC_OZAKI_BF16 (tcgen05
- * with exponent-aligned BF16 slices; ~1e-11 normwise).
+ * precision: MODAL_PREC_FP64 (CUDA cores), MODAL_PREC_OZAKI_BF16 (tcgen05
+ * with exponent-aligned BF16 slices; ~1e-11 normwise), MODAL_PREC_TF32 or
+ * MODAL_PREC_BF16X3 (tcgen05 with FP32 accumulation; ~1e-3 and ~1e-5).
  * (prob->late_modes/prim_modes/x_w are not used.) */
 int modal_contract_l(modal_handle *h, const modal_problem *prob, int32_t n_mu,
                      const double *A, int32_t precision, double *M, modal_stream_t stream);
@@ -204,7 +216,11 @@ int modal_project_separable(modal_handle *h, const modal_problem *prob,
  * l_dw: device [n_grid] multipoles represented by each grid point (1 on a
  * dense grid; NULL = all 1).  On a dense grid with EXACT weights this equals
  * modal_project_separable.  gamma: device [n_late][n_prim] (overwritten).
- * This call synchronises `stream` once (to size its triple batches). */
+ * Stream-ordered, no host synchronisation: the triples are counted on the
+ * device and processed in batches sized on the host from the bound
+ * C(n_grid + 2, 3); batches past the true count do no work.  The call can be
+ * captured in a CUDA graph once the handle has served a call with the same
+ * n_grid and sizes (its scratch is then allocated). */
 int modal_project_direct(modal_handle *h, const modal_problem *prob, const int32_t *l_grid,
                          const double *l_dw, int32_t n_grid, int32_t weight_mode,
                          double *gamma, modal_stream_t stream);
@@ -279,15 +295,18 @@ int modal_gram_solve(modal_handle *h, int32_t n, int32_t m, const double *gram, 
  *    it calls no cudaMalloc, cudaFree or allocating library routine.
  *  - Scratch lives in a fixed 48 MiB device array compiled into the library;
  *    every GPU that loads the library holds it until the process exits.
- *    Problems whose scratch does not fit (radial points are streamed in
- *    smaller chunks first) are rejected with MODAL_EINVAL and a message
- *    giving the bytes needed; e.g. 20-function bases (the 52 MB triple-product
- *    table alone) do not fit.
+ *    Radial points are streamed in the largest chunk (at most opts->x_chunk
+ *    when that is set) whose scratch fits, so a caller's x_chunk may be
+ *    reduced; problems that do not fit even one radial point at a time are
+ *    rejected with MODAL_EINVAL and a message giving the bytes needed; e.g.
+ *    20-function bases (the 52 MB triple-product table alone) do not fit.
  *  - precision: MODAL_PREC_FP64 or MODAL_PREC_FP32 (the tensor-core form
  *    needs more scratch than the fixed buffer).
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture begins.
+ *    (cudaGetSymbolAddress) and caches it with the id of the device's current
+ *    context; a call that finds a different context (after cudaDeviceReset,
+ *    or on a thread without one) looks it up again.  Make the first call on a
+ *    device, and the first after a reset, before any stream capture begins.
  *  - All calls share the one buffer and it keeps the last call's contents
  *    (everything a call reads is written first).  Calls that overlap on the
  *    GPU -- on different streams, or from different threads, without

@@ -59,36 +59,57 @@ __device__ __forceinline__ double gosper_3j2(int l1, int l2, int l3) {
   return v * sqrt((L1 + 1.0 / 6.0) * (L2 + 1.0 / 6.0) * (L3 + 1.0 / 6.0) / (L + 1.0 / 6.0));
 }
 
-// Write the triples of each pair at its scanned offset with their weight
-//   z = mult * dw1 dw2 dw3 * w_l1 w_l2 w_l3 * H / (144 pi).
-__global__ void k_direct_fill(int ng, const int *__restrict__ grid, const double *__restrict__ dw,
-                              const double *__restrict__ w_l, int l_min, const double *__restrict__ ctab,
-                              int mode, const int64_t *__restrict__ offsets, int *__restrict__ tri,
-                              double *__restrict__ z) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)ng * ng) return;
-  int i1 = (int)(idx / ng), i2 = (int)(idx % ng);
-  if (i2 < i1) return;
-  int64_t o = offsets[idx];
-  int l1 = grid[i1], l2 = grid[i2];
-  double d12 = (dw ? dw[i1] * dw[i2] : 1.0) * w_l[l1 - l_min] * w_l[l2 - l_min];
+// Length of the flat triple list: the last pair's offset plus its count.
+__global__ void k_direct_total(const int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
+                               int64_t npairs, int64_t *__restrict__ ntri) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ntri = npairs > 0 ? offsets[npairs - 1] + counts[npairs - 1] : 0;
+}
+
+// Triples t0 .. t0 + T - 1 of the flat list (grid pairs (i1 <= i2) in
+// row-major order, then l3 ascending) with their weights
+//   z = mult * dw1 dw2 dw3 * w_l1 w_l2 w_l3 * H / (144 pi),
+// into batch-local arrays.  Thread tt finds its pair by a binary search of
+// the scanned pair counts and its l3 by counting that pair's valid ones; the
+// list's length is read on the device (threads past it write nothing).
+__global__ void k_direct_fill_batch(int ng, const int *__restrict__ grid, const double *__restrict__ dw,
+                                    const double *__restrict__ w_l, int l_min, const double *__restrict__ ctab,
+                                    int mode, const int64_t *__restrict__ offsets, const int64_t *__restrict__ ntri,
+                                    int64_t t0, int T, int *__restrict__ tri, double *__restrict__ z) {
+  const int tt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= T) return;
+  const int64_t t = t0 + tt;
+  if (t >= *ntri) return;
+  // the last pair whose offset is <= t (pairs with no triples share the next
+  // pair's offset, so this one has t inside its range)
+  int64_t lo = 0, hi = (int64_t)ng * ng;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (offsets[mid] <= t) lo = mid + 1;
+    else hi = mid;
+  }
+  const int64_t pr = lo - 1;
+  const int i1 = (int)(pr / ng), i2 = (int)(pr % ng);
+  int64_t k = t - offsets[pr];
+  const int l1 = grid[i1], l2 = grid[i2];
   for (int i3 = i2; i3 < ng; ++i3) {
-    int l3 = grid[i3];
+    const int l3 = grid[i3];
     if (l3 > l1 + l2) break;
+    if (mode == MODAL_W_EXACT_3J && ((l1 + l2 + l3) & 1)) continue;
+    if (k-- > 0) continue;
     double H;
     if (mode == MODAL_W_EXACT_3J) {
-      if ((l1 + l2 + l3) & 1) continue;
-      int g = (l1 + l2 + l3) / 2;
+      const int g = (l1 + l2 + l3) / 2;
       H = ctab[g - l1] * ctab[g - l2] * ctab[g - l3] / ((2.0 * g + 1.0) * ctab[g]);
     } else {
       H = 0.5 * gosper_3j2(l1, l2, l3);
     }
-    int mult = (l1 == l2 && l2 == l3) ? 1 : ((l1 == l2 || l2 == l3) ? 3 : 6);
-    tri[3 * o] = l1;
-    tri[3 * o + 1] = l2;
-    tri[3 * o + 2] = l3;
-    z[o] = (double)mult * d12 * (dw ? dw[i3] : 1.0) * w_l[l3 - l_min] * H / (144.0 * MODAL_PI);
-    ++o;
+    const int mult = (l1 == l2 && l2 == l3) ? 1 : ((l1 == l2 || l2 == l3) ? 3 : 6);
+    const double d = (dw ? dw[i1] * dw[i2] * dw[i3] : 1.0) * w_l[l1 - l_min] * w_l[l2 - l_min] * w_l[l3 - l_min];
+    tri[3 * tt] = l1;
+    tri[3 * tt + 1] = l2;
+    tri[3 * tt + 2] = l3;
+    z[tt] = (double)mult * d * H / (144.0 * MODAL_PI);
+    return;
   }
 }
 
@@ -98,8 +119,10 @@ __global__ void k_direct_fill(int ng, const int *__restrict__ grid, const double
 __global__ void __launch_bounds__(256) k_direct_X(int nbp, int n_x, int l_min, const double *__restrict__ qtT,
                                                   const double *__restrict__ xw, const int *__restrict__ tri,
                                                   int64_t t0, int T, int xc, const int *__restrict__ prim,
-                                                  int n_prim, double *__restrict__ Xb) {
+                                                  int n_prim, double *__restrict__ Xb,
+                                                  const int64_t *__restrict__ ntri, int64_t tglob0) {
   extern __shared__ double sm[];
+  if (tglob0 + blockIdx.x >= *ntri) return;  // past the end of the triple list (whole block)
   const int P2 = nbp * (nbp + 1) / 2;
   const int NZ = nbp * P2;
   double *Z = sm;                      // [nbp][P2]
@@ -154,10 +177,12 @@ __global__ void __launch_bounds__(256) k_direct_X(int nbp, int n_x, int l_min, c
 // Y[n][tt] = z_t sum over the 6 assignments of (a,b,c) to (l1,l2,l3).
 __global__ void k_direct_Y(int nbl, int L, int l_min, const double *__restrict__ q,
                            const int *__restrict__ tri, const double *__restrict__ z, int64_t t0,
-                           int T, int ntri_batch, const int *__restrict__ late, int n_late,
-                           double *__restrict__ Yb) {
+                           int T, const int64_t *__restrict__ ntri, int64_t tglob0, const int *__restrict__ late,
+                           int n_late, double *__restrict__ Yb) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n_late * T) return;
+  const int64_t ntri_batch = *ntri - tglob0;  // triples of this batch (<= 0: none)
+  if (ntri_batch <= 0) return;
   int n = (int)(idx / T), tt = (int)(idx % T);
   double v = 0.0;
   if (tt < ntri_batch) {

@@ -410,8 +410,14 @@ cudaError_t launch_zero(double *p, size_t n, cudaStream_t st) {
 __global__ void __launch_bounds__(256) k_gemm_nt_f64(int m, int n, int K, const double *__restrict__ A,
                                                      int64_t lda, const double *__restrict__ B,
                                                      int64_t ldb, double *__restrict__ C, int64_t ldc,
-                                                     int accumulate) {
+                                                     int accumulate, const int64_t *__restrict__ kdev,
+                                                     int64_t koff) {
   using Cf = SimtCfg<double>;
+  if (kdev) {  // K read on the device: at most *kdev - koff terms
+    const int64_t kd = *kdev - koff;
+    if (kd < K) K = kd < 0 ? 0 : (int)kd;
+    if (K == 0 && accumulate) return;
+  }
   constexpr int BM = Cf::BM, BN = Cf::BN, BK = Cf::BK, TM = Cf::TM, TN = Cf::TN;
   constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
   __shared__ double As[BK][BM + 1];
@@ -451,10 +457,11 @@ __global__ void __launch_bounds__(256) k_gemm_nt_f64(int m, int n, int K, const 
 }
 
 cudaError_t launch_gemm_nt_f64(int m, int n, int k, const double *A, int64_t lda, const double *B,
-                               int64_t ldb, double *C, int64_t ldc, bool accumulate, cudaStream_t st) {
+                               int64_t ldb, double *C, int64_t ldc, bool accumulate, cudaStream_t st,
+                               const int64_t *kdev, int64_t koff) {
   if (m == 0 || n == 0) return cudaSuccess;
   dim3 grid(cdiv(m, 64), cdiv(n, 64));
-  k_gemm_nt_f64<<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0);
+  k_gemm_nt_f64<<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0, kdev, koff);
   return cudaGetLastError();
 }
 

@@ -30,8 +30,11 @@ cudaError_t launch_gather(const SepShape &s, const double *G, const int *late, c
                           int n_late, int n_prim, double scale, double *gamma, cudaStream_t st);
 cudaError_t launch_zero(double *p, size_t n, cudaStream_t st);
 
-// generic K-major FP64 GEMM: C[m][n] (+)= sum_k A[m*lda + k] B[n*ldb + k]
+// generic K-major FP64 GEMM: C[m][n] (+)= sum_k A[m*lda + k] B[n*ldb + k]; with
+// kdev, only the first min(k, *kdev - koff) terms (read on the device; none:
+// C unchanged when accumulating, zero otherwise)
 cudaError_t launch_gemm_nt_f64(int m, int n, int k, const double *A, int64_t lda, const double *B,
-                               int64_t ldb, double *C, int64_t ldc, bool accumulate, cudaStream_t st);
+                               int64_t ldb, double *C, int64_t ldc, bool accumulate, cudaStream_t st,
+                               const int64_t *kdev = nullptr, int64_t koff = 0);
 
 }  // namespace modal

@@ -91,6 +91,29 @@ inline void singles_plan(uint32_t (&out)[1 + RUNS_MAX]) {
   out[0] = (uint32_t)n | (uint32_t)MIN_ACC << 8;
 }
 
+// Schedule of the 2-SM (CTA pair) form.  The pair's MMA takes the columns
+// 0 .. N/2-1 of B from the even CTA's shared memory and N/2 .. N-1 from the
+// odd CTA's, at the same offsets.  The odd CTA holds the B slices shifted by
+// one (its slot j holds slice j + 1; slot 4 holds zeros), so an MMA with
+// N = 2w at slot j multiplies the A slice by B slices j and j + 1 at once:
+// a run of exactly two, whose columns fall on accumulators acc and acc + 1.
+// Nine such runs cover the 15 products with sa + sb <= 4; three of them pair
+// a wanted product with the zero slot or with a level-5 product (which only
+// adds a smaller term to an accumulator of levels >= 2).  Accumulators: 0 =
+// level 0, 1 = level 1 (exact), 2 and 3 = levels >= 2.  The two fresh runs
+// come first (the first touch of an accumulator in a chunk overwrites it).
+constexpr int PAIR_RUNS = 9;
+inline void pair_plan(uint32_t (&out)[1 + RUNS_MAX]) {
+  static const int runs[PAIR_RUNS][4] = {  // sa, slot j, first accumulator, fresh
+      {0, 2, 2, 1}, {0, 0, 0, 1}, {1, 0, 1, 0}, {0, 4, 2, 0}, {1, 2, 2, 0},
+      {2, 0, 2, 0}, {2, 2, 2, 0}, {3, 0, 2, 0}, {4, 0, 2, 0}};
+  memset(out, 0, sizeof out);
+  for (int r = 0; r < PAIR_RUNS; ++r)
+    out[1 + r] = (uint32_t)runs[r][0] | (uint32_t)runs[r][1] << 4 | 2u << 8 | (uint32_t)runs[r][2] << 12 |
+                 (runs[r][3] ? 1u << 16 : 0u);
+  out[0] = (uint32_t)PAIR_RUNS | (uint32_t)MIN_ACC << 8;
+}
+
 // The schedule of least modelled cost for tile width w (a multiple of 16,
 // 16 .. 128); the singles schedule if the search finds none.
 inline void mma_plan(int w, uint32_t (&out)[1 + RUNS_MAX]) {

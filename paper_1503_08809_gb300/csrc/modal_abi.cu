@@ -11,6 +11,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cuda.h>
+
 #include "common.cuh"
 #include "direct.cuh"
 #include "kernels.cuh"
@@ -30,7 +32,7 @@ struct modal_handle {
   std::string err;
   void *slot_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t slot_bytes[4] = {0, 0, 0, 0};
-  int64_t *pinned_i64 = nullptr;  // host-pinned word for the direct path's triple count
+  int64_t *pinned_i64 = nullptr;  // host-pinned block: a spare word, then the error words below
   int *pinned_err = nullptr;      // host-pinned copies of the tensor path's device error words
   int n_err_words = 1;            // how many of them the last call filled
   cudaEvent_t err_event = nullptr;
@@ -38,6 +40,7 @@ struct modal_handle {
   long long wait_cycles = TC_DEFAULT_WAIT_CYCLES;
   int opt_triple_variant = TC_TRIPLE_MATERIALISED;
   int opt_split_k = 0;
+  int opt_pair = 0;               // the triple GEMM on CTA pairs (2-SM MMA)
   int opt_batch_streams = 0;      // 0: chosen by timing on the first call for a problem set
   Profiler prof;
   // batched calls: graphs of all launches, keyed by the problem set; the
@@ -155,8 +158,7 @@ static int resolve_opts(modal_handle *h, const modal_problem *p, const modal_opt
                 "(set allow_inexact_gl to accept)",
                 n_mu, n_mu_exact(p->l_max));
   if (n_mu > 6400) return fail(h, MODAL_EUNSUPPORTED, "n_mu > 6400 (l_max > 4266) is not supported");
-  if (prec != MODAL_PREC_FP64 && prec != MODAL_PREC_FP32 && prec != MODAL_PREC_OZAKI_BF16)
-    return fail(h, MODAL_EINVAL, "unknown precision %d", prec);
+  if (prec < MODAL_PREC_FP64 || prec > MODAL_PREC_BF16X3) return fail(h, MODAL_EINVAL, "unknown precision %d", prec);
   if (x_chunk < 0) return fail(h, MODAL_EINVAL, "x_chunk < 0");
   return MODAL_OK;
 }
@@ -270,6 +272,10 @@ int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value) {
       if (value < 0 || value > 4096) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_SPLIT_K out of range");
       h->opt_split_k = (int)value;
       return MODAL_OK;
+    case MODAL_OPT_TC_PAIR:
+      if (value < 0 || value > 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_PAIR takes 0 or 1");
+      h->opt_pair = (int)value;
+      return MODAL_OK;
     case MODAL_OPT_BATCH_STREAMS:
       if (value < 0 || value > MAX_BATCH_STREAMS)
         return fail(h, MODAL_EINVAL, "MODAL_OPT_BATCH_STREAMS takes 0 .. %d", MAX_BATCH_STREAMS);
@@ -328,8 +334,9 @@ int modal_contract_l(modal_handle *h, const modal_problem *p, int32_t n_mu, cons
   if (int r = check_handle(h)) return r;
   if (int r = validate_problem(h, p, false, false)) return r;
   if (n_mu < 0 || !A || !M) return fail(h, MODAL_EINVAL, "bad A/M/n_mu");
-  if (precision != MODAL_PREC_FP64 && precision != MODAL_PREC_OZAKI_BF16)
-    return fail(h, MODAL_EINVAL, "modal_contract_l supports FP64 and OZAKI_BF16");
+  if (precision != MODAL_PREC_FP64 && precision != MODAL_PREC_OZAKI_BF16 && precision != MODAL_PREC_TF32 &&
+      precision != MODAL_PREC_BF16X3)
+    return fail(h, MODAL_EINVAL, "modal_contract_l supports FP64, OZAKI_BF16, TF32 and BF16X3");
   if (n_mu == 0 || p->n_x == 0) return MODAL_OK;
   cudaStream_t st = (cudaStream_t)stream;
   SepShape s{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};
@@ -339,6 +346,19 @@ int modal_contract_l(modal_handle *h, const modal_problem *p, int32_t n_mu, cons
     return MODAL_OK;
   }
   void *scratch;
+  if (precision == MODAL_PREC_TF32 || precision == MODAL_PREC_BF16X3) {
+    const int kind = precision == MODAL_PREC_TF32 ? TC_FORM_TF32 : TC_FORM_BF16X3;
+    if (int r = ws_get(h, 0, fa_scratch_bytes(s, p->n_x), &scratch)) return r;
+    Profiler *prof = h->prof.on ? &h->prof : nullptr;
+    if (int r = fa_prepare_l(kind, s, A, p->q, scratch, p->n_x, st, prof)) return fail(h, r, "%s", fa_last_error());
+    if (int r = fa_contract_l(kind, s, p->qt, 0, p->n_x, p->n_x, M, true, scratch, h->wait_cycles, st, prof))
+      return fail(h, r, "%s", fa_last_error());
+    CK(cudaMemcpyAsync(h->pinned_err, fa_error_word(scratch), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(h->err_event, st));
+    h->n_err_words = 1;
+    h->err_pending = true;
+    return MODAL_OK;
+  }
   if (int r = ws_get(h, 0, tc_scratch_bytes(s, p->n_x, 1, TC_TRIPLE_FUSED), &scratch)) return r;
   {
     PROF(h, "tc_contract_l", st);
@@ -373,11 +393,14 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
                           int num_sms) {
   pl.variant = h ? h->opt_triple_variant : TC_TRIPLE_MATERIALISED;
   if (pl.variant == TC_TRIPLE_FUSED2 && !tc_fused2_fits(p->nb_late, p->nb_prim)) pl.variant = TC_TRIPLE_MATERIALISED;
+  if (pl.variant == TC_TRIPLE_MATERIALISED && h && h->opt_pair) pl.variant = TC_TRIPLE_PAIR;
+  const bool y_hbm = pl.variant == TC_TRIPLE_MATERIALISED || pl.variant == TC_TRIPLE_PAIR;
   int n_mu, prec, xch;
   if (int r = resolve_opts(h, p, o, n_mu, prec, xch)) return r;
   pl.s = SepShape{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};
   pl.prec = prec;
-  pl.elem = (prec == MODAL_PREC_FP32) ? sizeof(float) : sizeof(double);
+  const bool m_f32 = prec == MODAL_PREC_FP32 || prec == MODAL_PREC_TF32 || prec == MODAL_PREC_BF16X3;
+  pl.elem = m_f32 ? sizeof(float) : sizeof(double);
   const int64_t nblp = (int64_t)p->nb_late * p->nb_prim;
   if (xch > 0) {
     pl.nxc = xch < p->n_x ? xch : p->n_x;
@@ -388,7 +411,7 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
     const int64_t L = p->l_max - p->l_min + 1;
     int64_t per_x = 26 * (int64_t)n_mu * nblp + 10 * (int64_t)p->nb_prim * L;
     int64_t budget = (int64_t)2 << 30;
-    if (pl.variant == TC_TRIPLE_MATERIALISED) {
+    if (y_hbm) {
       const int64_t P2 = (int64_t)p->nb_prim * (p->nb_prim + 1) / 2;
       per_x += 10 * P2 * p->nb_late * (p->nb_late + 1) / 2 * (int64_t)n_mu;
       budget = (int64_t)6 << 30;
@@ -404,7 +427,7 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   }
   if (pl.nxc < 1) pl.nxc = 1;
   pl.nxl = pl.nxc;
-  if (prec == MODAL_PREC_OZAKI_BF16 && pl.variant == TC_TRIPLE_MATERIALISED) {
+  if (prec == MODAL_PREC_OZAKI_BF16 && y_hbm) {
     // the l contraction runs on up to 64 radial points at once (M <= 1 GiB),
     // a whole number of triple-product chunks
     int64_t c = ((int64_t)1 << 30) / ((int64_t)n_mu * nblp * 8);
@@ -427,6 +450,7 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   if (pl.est) b += align256(sizeof(double) * (size_t)pl.Gsize);   // G of |M| (error scale)
   if (need_part) b += align256(sizeof(double) * (size_t)pl.Gsize * pl.ksplit);
   if (prec == MODAL_PREC_OZAKI_BF16) b += tc_scratch_bytes(pl.s, pl.nxl, pl.nxc, pl.variant);
+  if (prec == MODAL_PREC_TF32 || prec == MODAL_PREC_BF16X3) b += fa_scratch_bytes(pl.s, pl.nxc);
   pl.bytes = b + 1024;
   return MODAL_OK;
 }
@@ -438,9 +462,11 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
   Bump bp{(char *)scratch};
   // the tensor-core scratch comes first, so that its status words sit at the
   // same address for every problem of a batch
+  const bool fa = pl.prec == MODAL_PREC_TF32 || pl.prec == MODAL_PREC_BF16X3;
+  const int fa_kind = pl.prec == MODAL_PREC_TF32 ? TC_FORM_TF32 : TC_FORM_BF16X3;
   void *tcs = (pl.prec == MODAL_PREC_OZAKI_BF16)
                   ? bp.take<char>(tc_scratch_bytes(s, pl.nxl, pl.nxc, pl.variant))
-                  : nullptr;
+                  : fa ? bp.take<char>(fa_scratch_bytes(s, pl.nxc)) : nullptr;
   double *mu = bp.take<double>(s.n_mu), *om = bp.take<double>(s.n_mu);
   double *A = bp.take<double>((size_t)s.n_mu * s.L);
   void *M = bp.take<char>(pl.elem * (size_t)pl.nxl * s.n_mu * s.nbl * s.nbp);
@@ -481,8 +507,17 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
         CK(launch_triple<double>(s, (double *)M, om, p->x_w, x0, nxc, pl.ksplit, Gabs, Gpart, c > 0,
                                  num_sms, st, true));
       }
-    } else if (pl.prec == MODAL_PREC_FP32) {
-      {
+    } else if (pl.prec == MODAL_PREC_FP32 || fa) {
+      if (fa) {
+        // the l contraction on the tensor cores with FP32 accumulation
+        Profiler *prof = (h && h->prof.on && !capturing) ? &h->prof : nullptr;
+        if (c == 0)
+          if (int r = fa_prepare_l(fa_kind, s, A, p->q, tcs, pl.nxc, st, prof, first_in_call))
+            return fail(h, r, "tensor-core operand split failed: %s", fa_last_error());
+        const long long wc = h ? h->wait_cycles : TC_DEFAULT_WAIT_CYCLES;
+        if (int r = fa_contract_l(fa_kind, s, p->qt, x0, nxc, pl.nxc, M, false, tcs, wc, st, prof))
+          return fail(h, r, "tensor-core l contraction failed: %s", fa_last_error());
+      } else {
         PROF(h, "contract_l_f32", st);
         CK(launch_contract_l<float>(s, A, p->q, p->qt, x0, nxc, (float *)M, st));
       }
@@ -523,9 +558,10 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
       }
     }
   }
-  if (pl.prec == MODAL_PREC_OZAKI_BF16 && nchunks > 0 && !capturing) {
+  if ((pl.prec == MODAL_PREC_OZAKI_BF16 || fa) && nchunks > 0 && !capturing && h) {
     // surface a bounded-wait give-up through modal_handle_status (no sync here)
-    CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(tcs), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->pinned_err, fa ? fa_error_word(tcs) : tc_error_word(tcs), sizeof(int),
+                       cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(h->err_event, st));
     h->n_err_words = 1;
     h->err_pending = true;
@@ -715,7 +751,8 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
       return fail(h, r, "problem %d: %s", i, h->err.c_str());
     if ((int64_t)probs[i].n_late * probs[i].n_prim > 0 && !gammas[i])
       return fail(h, MODAL_EINVAL, "null gamma for problem %d", i);
-    any_tc = any_tc || plans[i].prec == MODAL_PREC_OZAKI_BF16;
+    any_tc = any_tc || plans[i].prec == MODAL_PREC_OZAKI_BF16 || plans[i].prec == MODAL_PREC_TF32 ||
+             plans[i].prec == MODAL_PREC_BF16X3;  // their status word heads each stream's scratch
   }
   // stream counts to consider: the fixed option, or 1, 2, 4, 8 (at most n)
   // while their scratch fits in half of the free device memory
@@ -746,6 +783,7 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
   key = fnv1a(key, &scratch, sizeof scratch);
   key = fnv1a(key, &h->opt_triple_variant, sizeof(int));
   key = fnv1a(key, &h->opt_split_k, sizeof(int));
+  key = fnv1a(key, &h->opt_pair, sizeof(int));
   key = fnv1a(key, &h->opt_batch_streams, sizeof(int));
   key = fnv1a(key, &h->wait_cycles, sizeof(long long));
   auto it = h->graphs.find(key);
@@ -811,8 +849,10 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
 // Allocation-free variant of modal_project_separable.  Its scratch is this
 // file-scope device array (present on every GPU that loads the library, for
 // the life of the process).  In host code the array's name is only a
-// host-side stand-in, so the device address is taken once per device with
-// cudaGetSymbolAddress and cached; kernels receive that address.
+// host-side stand-in, so the device address is taken with
+// cudaGetSymbolAddress at set-up -- once per device, in its current context,
+// and again only if that context was replaced (a cudaDeviceReset reloads the
+// module, and the array may then sit elsewhere) -- and kernels receive it.
 // ---------------------------------------------------------------------------
 #define MODAL_NOALLOC_SCRATCH_BYTES ((size_t)48 << 20)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MODAL_NOALLOC_SCRATCH_BYTES];
@@ -821,6 +861,7 @@ namespace {
 struct NoallocDevice {
   void *scratch = nullptr;
   int num_sms = 0;
+  unsigned long long ctx_id = 0;  // context the address belongs to
   bool ready = false;
 };
 constexpr int NOALLOC_MAX_DEVICES = 64;
@@ -835,15 +876,46 @@ extern "C" int modal_project_separable_noalloc(const modal_problem *p, const mod
   if (e != cudaSuccess) return fail(nullptr, MODAL_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
     return fail(nullptr, MODAL_EUNSUPPORTED, "device ordinal %d beyond %d", dev, NOALLOC_MAX_DEVICES);
+  // the unique id of the thread's current context (never reused within the
+  // process); 0 if none is current yet
+  // (driver entry points resolved through the runtime, so that loading the
+  // library needs no libcuda on machines without a GPU)
+  typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+  typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+  static const CtxGetCurrentFn get_current = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+               ? (CtxGetCurrentFn)p
+               : (CtxGetCurrentFn) nullptr;
+  }();
+  static const CtxGetIdFn get_id = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+               ? (CtxGetIdFn)p
+               : (CtxGetIdFn) nullptr;
+  }();
+  auto current_ctx_id = []() -> unsigned long long {
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+      return 0;
+    return id;
+  };
+  const unsigned long long ctx_id = current_ctx_id();
   NoallocDevice nd;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     NoallocDevice &slot = g_noalloc_dev[dev];
-    if (!slot.ready) {  // one-time set-up on this device (no allocation)
+    if (!slot.ready || ctx_id == 0 || slot.ctx_id != ctx_id) {  // set-up on this device / context (no allocation)
       void *ptr = nullptr;
-      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);  // also makes the device's context current
       if (e != cudaSuccess)
         return fail(nullptr, MODAL_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+      slot.ctx_id = current_ctx_id();
       int sms = 0;
       e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e != cudaSuccess)
@@ -860,13 +932,12 @@ extern "C" int modal_project_separable_noalloc(const modal_problem *p, const mod
   const int prec = o ? o->precision : MODAL_PREC_FP64;
   if (prec != MODAL_PREC_FP64 && prec != MODAL_PREC_FP32)
     return fail(nullptr, MODAL_EINVAL, "the allocation-free entry point serves MODAL_PREC_FP64 and MODAL_PREC_FP32");
-  // largest radial chunk whose scratch fits the static buffer
+  // the largest radial chunk (at most the caller's or the automatic one)
+  // whose scratch fits the static buffer
   modal_opts oo = o ? *o : modal_opts{0, MODAL_PREC_FP64, 0, 0, nullptr};
   SepPlan pl;
   if (int r = plan_separable(nullptr, p, &oo, pl, nd.num_sms)) return r;
-  int nxc = pl.nxc;
-  while (pl.bytes > MODAL_NOALLOC_SCRATCH_BYTES && nxc > 1) {
-    nxc = nxc > 2 ? nxc / 2 : 1;
+  for (int nxc = pl.nxc - 1; pl.bytes > MODAL_NOALLOC_SCRATCH_BYTES && nxc >= 1; --nxc) {
     oo.x_chunk = nxc;
     if (int r = plan_separable(nullptr, p, &oo, pl, nd.num_sms)) return r;
   }
@@ -897,66 +968,56 @@ int modal_project_direct(modal_handle *h, const modal_problem *p, const int32_t 
   if (!l_grid) return fail(h, MODAL_EINVAL, "null l_grid");
   const int64_t npairs = (int64_t)ng * ng;
   const int cmax = 3 * p->l_max / 2 + 2;
-  // phase 1: qt transpose, 3j table, counts, scan
-  size_t b1 = 0;
-  b1 += align256(sizeof(double) * (size_t)L * p->n_x * p->nb_prim);
-  b1 += 2 * align256(sizeof(int64_t) * (size_t)npairs);
-  b1 += align256(sizeof(double) * (size_t)(cmax + 1));
-  size_t scan_b = scan_tmp_bytes(npairs);
-  b1 += align256(scan_b) + 1024;
-  void *s1;
-  if (int r = ws_get(h, 0, b1, &s1)) return r;
-  Bump bp{(char *)s1};
-  double *qtT = bp.take<double>((size_t)L * p->n_x * p->nb_prim);
-  int64_t *counts = bp.take<int64_t>((size_t)npairs);
-  int64_t *offs = bp.take<int64_t>((size_t)npairs);
-  double *ctab = bp.take<double>((size_t)cmax + 1);
-  void *scan_tmp = bp.take<char>(scan_b);
-
-  {
-    int64_t rows = (int64_t)p->n_x * p->nb_prim, cols = L;
-    dim3 grid((unsigned)cdiv64(cols, 32), (unsigned)cdiv64(rows, 32));
-    k_transpose<<<grid, dim3(32, 8), 0, st>>>(p->qt, rows, cols, qtT);
-    CK(cudaGetLastError());
-  }
-  CK(launch_threej_table(cmax, ctab, st));
-  k_direct_count<<<(unsigned)cdiv64(npairs, 256), 256, 0, st>>>(ng, l_grid, mode, counts);
-  CK(cudaGetLastError());
-  CK(scan_exclusive_i64(scan_tmp, scan_b, counts, offs, npairs, st));
-  // total = offs[last] + counts[last]; one synchronisation to size the batches
-  int64_t last_off = 0, last_cnt = 0;
-  CK(cudaMemcpyAsync(h->pinned_i64, offs + npairs - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  last_off = *h->pinned_i64;
-  CK(cudaMemcpyAsync(h->pinned_i64, counts + npairs - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  last_cnt = *h->pinned_i64;
-  const int64_t ntri = last_off + last_cnt;
-  if (ntri == 0) {
-    CK(launch_zero(gamma, (size_t)p->n_late * p->n_prim, st));
-    return MODAL_OK;
-  }
-  // phase 2: triples, weights and batch buffers (slot 1)
+  // The triple count is known only on the device.  Batches of T triples are
+  // sized on the host from the bound C(ng + 2, 3) (every sorted triple of
+  // grid points); each kernel reads the true count and batches past it do no
+  // work, so the call never waits for the device.
+  const int64_t ntri_max = (int64_t)ng * (ng + 1) * (ng + 2) / 6;
   int T = 32768;
   {
     int64_t cap = ((int64_t)1 << 30) / (8 * (int64_t)(p->n_late + p->n_prim));
     if (cap < 256) cap = 256;
     if (T > cap) T = (int)(cap / 32 * 32);
-    if (T > ntri) T = (int)ntri;
+    if (T > ntri_max) T = (int)ntri_max;
   }
-  size_t b2 = align256(sizeof(int) * 3 * (size_t)ntri) + align256(sizeof(double) * (size_t)ntri) +
-              align256(sizeof(double) * (size_t)T * p->n_late) + align256(sizeof(double) * (size_t)T * p->n_prim) +
-              1024;
-  void *s2;
-  if (int r = ws_get(h, 1, b2, &s2)) return r;
-  Bump b2p{(char *)s2};
-  int *tri = b2p.take<int>(3 * (size_t)ntri);
-  double *z = b2p.take<double>((size_t)ntri);
-  double *Yb = b2p.take<double>((size_t)T * p->n_late);
-  double *Xb = b2p.take<double>((size_t)T * p->n_prim);
-  k_direct_fill<<<(unsigned)cdiv64(npairs, 256), 256, 0, st>>>(ng, l_grid, l_dw, p->w_l, p->l_min, ctab, mode,
-                                                                offs, tri, z);
-  CK(cudaGetLastError());
+  const int64_t nbatch = cdiv64(ntri_max, T);
+  size_t scan_b = scan_tmp_bytes(npairs);
+  size_t b1 = 0;
+  b1 += align256(sizeof(double) * (size_t)L * p->n_x * p->nb_prim);     // qt transposed
+  b1 += 2 * align256(sizeof(int64_t) * (size_t)npairs);                 // counts, offsets
+  b1 += align256(sizeof(double) * (size_t)(cmax + 1));                  // 3j product table
+  b1 += align256(sizeof(int64_t));                                      // triple count
+  b1 += align256(scan_b);
+  b1 += align256(sizeof(int) * 3 * (size_t)T) + align256(sizeof(double) * (size_t)T);  // batch triples, weights
+  b1 += align256(sizeof(double) * (size_t)T * p->n_late) + align256(sizeof(double) * (size_t)T * p->n_prim);
+  b1 += 1024;
+  void *s1;
+  if (int r = ws_get(h, 1, b1, &s1)) return r;
+  Bump bp{(char *)s1};
+  double *qtT = bp.take<double>((size_t)L * p->n_x * p->nb_prim);
+  int64_t *counts = bp.take<int64_t>((size_t)npairs);
+  int64_t *offs = bp.take<int64_t>((size_t)npairs);
+  double *ctab = bp.take<double>((size_t)cmax + 1);
+  int64_t *ntri = bp.take<int64_t>(1);
+  void *scan_tmp = bp.take<char>(scan_b);
+  int *tri = bp.take<int>(3 * (size_t)T);
+  double *z = bp.take<double>((size_t)T);
+  double *Yb = bp.take<double>((size_t)T * p->n_late);
+  double *Xb = bp.take<double>((size_t)T * p->n_prim);
+
+  {
+    PROFN(h, "direct_setup", st, 6);  // transpose, 3j table, counts, scan (2), total
+    int64_t rows = (int64_t)p->n_x * p->nb_prim, cols = L;
+    dim3 grid((unsigned)cdiv64(cols, 32), (unsigned)cdiv64(rows, 32));
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(p->qt, rows, cols, qtT);
+    CK(cudaGetLastError());
+    CK(launch_threej_table(cmax, ctab, st));
+    k_direct_count<<<(unsigned)cdiv64(npairs, 256), 256, 0, st>>>(ng, l_grid, mode, counts);
+    CK(cudaGetLastError());
+    CK(scan_exclusive_i64(scan_tmp, scan_b, counts, offs, npairs, st));
+    k_direct_total<<<1, 32, 0, st>>>(counts, offs, npairs, ntri);
+    CK(cudaGetLastError());
+  }
   const int nbp = p->nb_prim, P2 = nbp * (nbp + 1) / 2;
   int xc = 16;
   size_t smem = 0;
@@ -966,23 +1027,29 @@ int modal_project_direct(modal_handle *h, const modal_problem *p, const int32_t 
   }
   if (smem > 200 * 1024) return fail(h, MODAL_EUNSUPPORTED, "primordial basis too large for the direct path");
   CK(cudaFuncSetAttribute(k_direct_X, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  for (int64_t t0 = 0; t0 < ntri; t0 += T) {
-    int nb = (int)((ntri - t0) < T ? (ntri - t0) : T);
+  for (int64_t bi = 0; bi < nbatch; ++bi) {
+    const int64_t t0 = bi * T;
+    {
+      PROF(h, "direct_fill", st);
+      k_direct_fill_batch<<<(unsigned)cdiv(T, 256), 256, 0, st>>>(ng, l_grid, l_dw, p->w_l, p->l_min, ctab, mode,
+                                                                  offs, ntri, t0, T, tri, z);
+      CK(cudaGetLastError());
+    }
     {
       PROF(h, "direct_X", st);
-      k_direct_X<<<nb, 256, smem, st>>>(nbp, p->n_x, p->l_min, qtT, p->x_w, tri, t0, T, xc, p->prim_modes,
-                                        p->n_prim, Xb);
+      k_direct_X<<<T, 256, smem, st>>>(nbp, p->n_x, p->l_min, qtT, p->x_w, tri, 0, T, xc, p->prim_modes,
+                                       p->n_prim, Xb, ntri, t0);
       CK(cudaGetLastError());
     }
     {
       PROF(h, "direct_Y", st);
       int64_t ny = (int64_t)p->n_late * T;
-      k_direct_Y<<<(unsigned)cdiv64(ny, 256), 256, 0, st>>>(p->nb_late, L, p->l_min, p->q, tri, z, t0, T, nb,
+      k_direct_Y<<<(unsigned)cdiv64(ny, 256), 256, 0, st>>>(p->nb_late, L, p->l_min, p->q, tri, z, 0, T, ntri, t0,
                                                             p->late_modes, p->n_late, Yb);
       CK(cudaGetLastError());
     }
     PROF(h, "direct_gemm", st);
-    CK(launch_gemm_nt_f64(p->n_late, p->n_prim, nb, Yb, T, Xb, T, gamma, p->n_prim, t0 > 0, st));
+    CK(launch_gemm_nt_f64(p->n_late, p->n_prim, T, Yb, T, Xb, T, gamma, p->n_prim, bi > 0, st, ntri, t0));
   }
   return MODAL_OK;
 }

@@ -544,6 +544,259 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// The triple GEMM on CTA pairs (2-SM tcgen05.mma, M = 256).
+//
+// A cluster of two CTAs takes two 128-row tiles of one G block (rows
+// 2 rp * 128 + rank * 128 ..) and one column tile of width w.  Each CTA's
+// shared memory holds its own 128 rows of the five A slices; the even CTA
+// holds the five B slices of the column tile, the odd CTA the same slices
+// shifted by one (slot j = slice j + 1, slot 4 = zeros from the tensor map's
+// out-of-range fill).  The pair MMA reads B columns 0 .. N/2-1 from the even
+// CTA and N/2 .. N-1 from the odd CTA, so one MMA of N = 2w at slot j
+// multiplies the A slice by B slices j and j + 1 (mma_plan.h, pair_plan):
+// each SM's tensor core reads half of the B columns it would read alone.
+// The even CTA issues everything: the four TMA loads of a stage (into both
+// CTAs' shared memory, all signalled on its own mbarrier), the MMAs and the
+// commits; both CTAs drain their own accumulators (their 128 rows of D).
+// Roles of the odd CTA: TMEM allocation and the drain only.
+// ---------------------------------------------------------------------------
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OZ_THREADS, 1)
+    k_ozaki_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ BMaps bmaps, OzParams P) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  float *lo_s = (float *)(sm + OZ_STAGES * OZ_STAGE_BYTES);  // [col][row]
+  uint64_t *full = (uint64_t *)(sm + OZ_STAGES * OZ_STAGE_BYTES + OZ_LO_BYTES);
+  uint64_t *empty = full + OZ_STAGES;
+  uint64_t *acc_full = empty + OZ_STAGES;
+  uint64_t *acc_empty = acc_full + 1;
+  uint64_t *mma_done = acc_empty + 1;
+  uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = ptx::cluster_ctarank();  // 0: issues the pair's work, 1: its partner
+  const bool leader = rank == 0;
+
+  // ---- tile of the pair: row tiles 2 rp, 2 rp + 1 of block bblk, column tile ct ----
+  int t = (int)(blockIdx.x >> 1), rp = 0, ct = 0, bblk;
+  int64_t rowoff = 0;
+  for (bblk = 0; bblk < P.g.nbl; ++bblk) {
+    const int nrp = (int)cdiv64(cdiv64(P.g.rows(bblk), OZ_BM), 2), nct = (int)cdiv64(P.g.cols(bblk), OZ_BN);
+    if (t < nrp * nct) {
+      rp = t / nct;
+      ct = t % nct;
+      break;
+    }
+    t -= nrp * nct;
+    rowoff += P.g.rows(bblk);
+  }
+  if (bblk >= P.g.nbl) return;  // both CTAs of a cluster decode the same tile
+  const bool lead = ct == 0;    // the first column tile prefetches the rows of A
+  const int ntile = g_tile_width(P.g.cols(bblk));
+  const int64_t pair_row0 = rowoff + (int64_t)rp * 2 * OZ_BM;       // first A row of the pair
+  const int64_t rt_loc = (int64_t)rp * 2 + rank;                      // this CTA's row tile in the block
+  const int64_t R = min((int64_t)OZ_BM, P.g.rows(bblk) - rt_loc * OZ_BM);  // may be <= 0 (odd tail)
+  const int64_t C = min((int64_t)ntile, P.g.cols(bblk) - (int64_t)ct * ntile);
+  const int64_t a_row0 = pair_row0 + (int64_t)rank * OZ_BM;
+  const int64_t b_row0 = (int64_t)bblk * P.g.nbp + (int64_t)ct * ntile;
+  const int64_t out_base = P.g.offset(bblk) + rt_loc * OZ_BM * P.g.cols(bblk) + (int64_t)ct * ntile;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(acc_full, 1);
+    ptx::mbar_init(acc_empty, 2 * OZ_EPI_WARPS);  // one arrival per drain warp of both CTAs
+    ptx::mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc_pair(tmem_slot, 512);
+    ptx::tmem_relinquish_pair();
+  }
+  ptx::tc_fence_before();
+  ptx::cluster_sync();  // both CTAs' barriers and TMEM exist before either is used
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ksteps = P.Kpad / OZ_BK;
+  const int steps_per_chunk = OZ_KC / OZ_BK;
+  const CUtensorMap *tmB = &bmaps.m[ntile / 16 - 1];
+  const uint32_t stage_bytes = (uint32_t)(OZ_A_BYTES + OZ_SLICES * ntile * OZ_ROWB);
+
+  if (warp == 0) {
+    // ================= TMA producer (even CTA) =================
+    if (leader && lane == 0) {
+      ptx::prefetch_tmap(&tmA);
+      ptx::prefetch_tmap(tmB);
+      const uint32_t own = ptx::smem_u32(sm), peer = ptx::mapa_shared(own, 1);
+      const int ar = (int)pair_row0;
+      if (lead)
+        for (int i = 0; i < OZ_PREFETCH && i < ksteps; ++i) {
+          ptx::tma_prefetch_3d(&tmA, i * OZ_BK, ar, 0);
+          ptx::tma_prefetch_3d(&tmA, i * OZ_BK, ar + OZ_BM, 0);
+        }
+      int issued = 0;
+      for (int i = 0; i < ksteps; ++i) {
+        const int s = i % OZ_STAGES;
+        const uint32_t ph = (uint32_t)((i / OZ_STAGES) & 1);
+        if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_cycles)) break;
+        const uint32_t fb = ptx::smem_u32(&full[s]), so = (uint32_t)(s * OZ_STAGE_BYTES);
+        ptx::mbar_arrive_expect_tx(&full[s], 2 * stage_bytes);
+        ptx::tma_load_3d_pair(own + so, &tmA, fb, i * OZ_BK, ar, 0);
+        ptx::tma_load_3d_pair(own + so + OZ_A_BYTES, tmB, fb, i * OZ_BK, (int)b_row0, 0);
+        ptx::tma_load_3d_pair(peer + so, &tmA, fb, i * OZ_BK, ar + OZ_BM, 0);
+        ptx::tma_load_3d_pair(peer + so + OZ_A_BYTES, tmB, fb, i * OZ_BK, (int)b_row0, 1);  // slices 1..5
+        if (lead && i + OZ_PREFETCH < ksteps) {
+          ptx::tma_prefetch_3d(&tmA, (i + OZ_PREFETCH) * OZ_BK, ar, 0);
+          ptx::tma_prefetch_3d(&tmA, (i + OZ_PREFETCH) * OZ_BK, ar + OZ_BM, 0);
+        }
+        ++issued;
+      }
+      // on abort: wait (bounded) for the copies in flight, which land in both
+      // CTAs and all complete on this CTA's barriers
+      if (*abort_flag) {
+        for (int i = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); i < issued; ++i) {
+          volatile int dummy = 0;
+          ptx::mbar_wait(&full[i % OZ_STAGES], (uint32_t)((i / OZ_STAGES) & 1), &dummy, OZ_WAIT_CYCLES);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ================= MMA issuer (even CTA) =================
+    if (leader && lane == 0) {
+      const uint32_t idesc = ptx::idesc_bf16_f32(2 * OZ_BM, 2 * ntile);
+      const uint32_t *plan = P.plan[0];
+      const int nruns = (int)(plan[0] & 0xffu);
+      uint32_t run[OZ_PLAN_MAX];
+#pragma unroll
+      for (int r = 0; r < OZ_PLAN_MAX; ++r) run[r] = plan[1 + r];
+      const uint32_t sbase = ptx::smem_u32(sm);
+      int chunk = 0;
+      for (int i = 0; i < ksteps; ++i) {
+        const int s = i % OZ_STAGES;
+        const uint32_t ph = (uint32_t)((i / OZ_STAGES) & 1);
+        const bool chunk_start = (i % steps_per_chunk) == 0;
+        if (chunk_start && chunk > 0) {
+          // both CTAs have drained the accumulators of the previous chunk
+          if (!ptx::mbar_wait(acc_empty, (uint32_t)((chunk - 1) & 1), abort_flag, P.wait_cycles)) break;
+        }
+        if (!ptx::mbar_wait(&full[s], ph, abort_flag, P.wait_cycles)) break;
+        ptx::tc_fence_after();
+        const uint32_t a0 = sbase + s * OZ_STAGE_BYTES;
+        const uint64_t ad0 = ptx::smem_desc(a0, 16, 8 * OZ_ROWB, ptx::SW_64B);
+        const uint64_t bd0 = ptx::smem_desc(a0 + OZ_A_BYTES, 16, 8 * OZ_ROWB, ptx::SW_64B);
+#pragma unroll
+        for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+#pragma unroll
+          for (int r = 0; r < OZ_PLAN_MAX; ++r) {
+            if (r >= nruns) break;
+            const uint32_t e = run[r];
+            const uint32_t sa = e & 15u, j = (e >> 4) & 15u, acc = (e >> 12) & 15u;
+            const bool first = chunk_start && kk == 0 && ((e >> 16) & 1u);
+            const uint64_t ad = ad0 + (uint64_t)((sa * OZ_BM * OZ_ROWB + kk * 32) >> 4);
+            const uint64_t bd = bd0 + (uint64_t)((j * (uint32_t)ntile * OZ_ROWB + kk * 32) >> 4);
+            ptx::mma_bf16_pair(tmem + acc * (uint32_t)ntile, ad, bd, idesc, first ? 0u : 1u);
+          }
+        }
+        ptx::mma_commit_pair(&empty[s]);
+        const bool chunk_end = ((i + 1) % steps_per_chunk) == 0 || i + 1 == ksteps;
+        if (chunk_end) {
+          ptx::mma_commit_pair_mc(acc_full, (uint16_t)3);  // both CTAs' drains
+          ++chunk;
+        }
+      }
+      ptx::mma_commit_pair(mma_done);
+      volatile int dummy = 0;
+      ptx::mbar_wait(mma_done, 0, &dummy, OZ_WAIT_CYCLES);
+    }
+  } else {
+    // ================= epilogue (both CTAs): drain own 128 rows =================
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int chalf = ew >> 2;
+    const int row = quarter * 32 + lane;
+    const int col0 = chalf * 64;
+    const int emA = *P.emaxA, emB = *P.emaxB;
+    const int ebias = emA + emB + 40;
+    const uint32_t empty_addr = leader ? 0u : ptx::mapa_shared(ptx::smem_u32(acc_empty), 0);
+    float hi[64];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+      hi[c] = 0.f;
+      lo_s[(col0 + c) * OZ_BM + row] = 0.f;
+    }
+    for (int ch = 0; ch < P.nchunks; ++ch) {
+      const bool got = ptx::mbar_wait(acc_full, (uint32_t)(ch & 1), abort_flag, P.wait_cycles);
+      if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+      ptx::tc_fence_after();
+      const int ea = (a_row0 + row < P.rowsA) ? P.eA[(int64_t)ch * P.rowsA + a_row0 + row] : -100000;
+      const float fa = pow2f_or0(ea - emA);
+      float fbl[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t bcol = b_row0 + col0 + h * 32 + lane;
+        const int eb = (bcol < P.rowsB) ? __ldg(P.eB + (int64_t)ch * P.rowsB + bcol) : -100000;
+        fbl[h] = pow2f_or0(eb - emB - 2 * OZ_BETA - 40);
+      }
+      const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+      for (int cb = 0; cb < 16; ++cb) {
+        if (col0 + cb * 4 >= ntile) break;
+        float v0[4], v1[4], v2[4], v3[4];
+        const uint32_t cc = (uint32_t)(col0 + cb * 4);
+        const uint32_t w = (uint32_t)ntile;
+        ptx::tmem_ld4(tl + cc, v0);
+        ptx::tmem_ld4(tl + w + cc, v1);
+        ptx::tmem_ld4(tl + 2 * w + cc, v2);
+        ptx::tmem_ld4(tl + 3 * w + cc, v3);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = cb * 4 + k;
+          const float f = fa * __shfl_sync(0xffffffffu, fbl[c >> 5], c & 31);
+          float s = v0[k] + v1[k];
+          float bb = s - v0[k];
+          float e = (v0[k] - (s - bb)) + (v1[k] - bb);
+          e += v2[k] + v3[k];
+          float lo = lo_s[(col0 + c) * OZ_BM + row];
+          df_add(hi[c], lo, s * f, e * f);
+          lo_s[(col0 + c) * OZ_BM + row] = lo;
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (leader) ptx::mbar_arrive(acc_empty);
+        else ptx::mbar_arrive_cluster(empty_addr);
+      }
+    }
+    if (ok && !*abort_flag && row < R) {
+#pragma unroll
+      for (int c = 0; c < 64; ++c) {
+        const int col = col0 + c;
+        if (col < C) {
+          const double v = f32_scaled_f64(hi[c], ebias) + f32_scaled_f64(lo_s[(col0 + c) * OZ_BM + row], ebias);
+          double *d = P.out + out_base + (int64_t)row * P.g.cols(bblk) + col;
+          *d += v;
+        }
+      }
+    }
+  }
+  // neither CTA frees TMEM or exits while its partner may still use its
+  // shared memory (TMA writes, MMA operand reads, remote arrivals)
+  ptx::tc_fence_before();
+  ptx::cluster_sync();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(P.err, ERR_TIMEOUT);
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc_pair(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -1705,9 +1958,9 @@ size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
   b += up256((size_t)Kpad * nblp * 8) + up256((size_t)nch * nblp * 8); // Mdf, column maxima
   b += up256((size_t)nch * nblp * 8) + up256((size_t)nch * nblp * 4);  // mxW, eB
   b += up256((size_t)OZ_SLICES * nblp * Kpad * 2);                     // Bt
-  if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_FUSED2)
+  if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR || variant == TC_TRIPLE_FUSED2)
     b += up256((size_t)nch * y_rows(s) * 4);                            // eY
-  if (variant == TC_TRIPLE_MATERIALISED)
+  if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR)
     b += up256((size_t)OZ_SLICES * y_rows(s) * Kpad * 2);               // Y slices
   return b;
 }
@@ -1815,8 +2068,9 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
     return MODAL_OK;
   }
-  if (variant == TC_TRIPLE_MATERIALISED) {
-    // Y slices through HBM, then the TMA-fed GEMM for both operands
+  if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR) {
+    // Y slices through HBM, then the TMA-fed GEMM for both operands (single
+    // CTAs, or CTA pairs with the 2-SM MMA)
     const int64_t rowsY = y_rows(s);
     char *wy = (char *)Bt + up256((size_t)OZ_SLICES * nblp * Kpad * 2);
     int *eY = (int *)wy;
@@ -1855,6 +2109,19 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     P.err = words;
     P.g = make_glayout(s.nbl, s.nbp);
     P.wait_cycles = wait_cycles;
+    if (variant == TC_TRIPLE_PAIR) {
+      // one schedule for every width (pair_plan), two 128-row tiles per cluster
+      for (int i = 0; i < OZ_BN / 16; ++i) plan::pair_plan(P.plan[i]);
+      int64_t pairs = 0;
+      for (int b = 0; b < s.nbl; ++b) pairs += cdiv64(cdiv64(P.g.rows(b), OZ_BM), 2) * cdiv64(P.g.cols(b), OZ_BN);
+      if ((e = cudaFuncSetAttribute(k_ozaki_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
+          cudaSuccess)
+        goto cuda_fail;
+      ProfScope ps(prof, "tc_gemm_triple", st);
+      k_ozaki_gemm_pair<<<(unsigned)(2 * pairs), OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+      if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+      return MODAL_OK;
+    }
     fill_mma_plans(P.plan);
     int64_t tiles = 0;
     for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(P.g.rows(b), OZ_BM) * cdiv64(P.g.cols(b), OZ_BN);

@@ -9,6 +9,7 @@ namespace modal {
 constexpr int TC_TRIPLE_MATERIALISED = 0;
 constexpr int TC_TRIPLE_FUSED = 1;
 constexpr int TC_TRIPLE_FUSED2 = 2;
+constexpr int TC_TRIPLE_PAIR = 3;  // Y through HBM, GEMM on CTA pairs (2-SM MMA)
 // whether the second fused form can serve a basis (its M~ tile per stage)
 bool tc_fused2_fits(int nbl, int nbp);
 // scratch for l-contraction chunks of nxl radial points and triple-product
@@ -33,4 +34,17 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
 int *tc_error_word(void *scratch);
 const char *tc_last_error();
 void tc_release(int device);
+
+// The l contraction with plain FP32 accumulation (tc_f32acc.cu): TF32
+// operands (one kind::tf32 product) or BF16 hi/lo pairs (three products).
+constexpr int TC_FORM_TF32 = 0;
+constexpr int TC_FORM_BF16X3 = 1;
+size_t fa_scratch_bytes(const SepShape &s, int nxc_max);
+int fa_prepare_l(int kind, const SepShape &s, const double *A, const double *q, void *scratch, int nxc_max,
+                 cudaStream_t st, Profiler *prof = nullptr, bool reset_status = true);
+// M [xl][j][a][p] of radial points [x0, x0 + nxc), FP32 or FP64
+int fa_contract_l(int kind, const SepShape &s, const double *qt, int x0, int nxc, int nxc_max, void *M,
+                  bool out_f64, void *scratch, long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
+int *fa_error_word(void *scratch);
+const char *fa_last_error();
 }  // namespace modal

@@ -1,5 +1,5 @@
 // Prints the MMA schedules of mma_plan.h (the searched one for every tile
-// width, then the singles fallback) as hex words: "w header run run ...".
+// width, then the singles fallback, then the pair schedule) as hex words: "w header run run ...".
 #include <cstdio>
 
 #include "../paper_1503_08809_gb300/csrc/mma_plan.h"
@@ -18,5 +18,7 @@ int main() {
   }
   modal::plan::singles_plan(o);
   for (int w = 16; w <= 128; w += 16) dump(-w, o);  // negative width: the fallback at width w
+  modal::plan::pair_plan(o);
+  dump(0, o);                                       // width 0: the 2-SM (pair) schedule, any width
   return 0;
 }

@@ -83,3 +83,35 @@ def test_direct_planck_sparse_sampled(mg):
     got = g[np.ix_(rows, cols)]
     assert np.abs(got - ref).max() / np.abs(ref).max() < TOL
     assert np.isfinite(g).all()
+
+
+def test_direct_graph_capture(mg):
+    """modal_project_direct makes no host synchronisation: after one call
+    (which sizes the handle's scratch) it is captured into a CUDA graph;
+    replays match the oracle, also after new tables are copied into the same
+    device buffers."""
+    P = syn.make_problem(160, 4, 9, seed=3, nb_prim=3)
+    lg, dw = syn.sparse_l_grid(160)
+    h = mg.Handle()
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    lgd = torch.tensor(lg, dtype=torch.int32, device="cuda")
+    dwd = torch.tensor(dw, dtype=torch.float64, device="cuda")
+    out = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device="cuda")
+    mg.project_direct(dp, lgd, dwd, out=out, handle=h)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
+        mg.project_direct(dp, lgd, dwd, out=out, handle=h)
+    out.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert normwise(out, oracle.direct(P, l_grid=lg, l_dw=dw)) < TOL
+    P2 = syn.make_problem(160, 4, 9, seed=4, nb_prim=3)
+    dp.qt.copy_(torch.tensor(P2.qt))
+    dp.q.copy_(torch.tensor(P2.q))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert normwise(out, oracle.direct(P2, l_grid=lg, l_dw=dw)) < TOL
+    h.close()

@@ -81,3 +81,33 @@ def test_singles_fallback_is_valid(schedules):
         if w < 0:
             check(-w, header, runs)
             assert all(decode(r)[2] == 1 for r in runs)
+
+
+def test_pair_schedule(schedules):
+    """The 2-SM schedule: runs of exactly two B slots with N = 2w, where the
+    odd CTA's slot j holds B slice j + 1 (slot 4: zeros, i.e. slice 5 out of
+    range).  Every product with sa + sb <= 4 is issued exactly once; levels 0
+    and 1 stay alone on accumulators 0 and 1; anything else (levels 2 .. 5,
+    the zero slot) lands on accumulators 2 and 3; fresh runs touch only
+    untouched accumulators and all four are written."""
+    (header, runs), = [(h, r) for w, h, r in schedules if w == 0]
+    assert header & 0xFF == len(runs) == 9 and (header >> 8) & 0xFF == 4
+    wanted = {(s, t) for s in range(SLICES) for t in range(SLICES) if s + t <= MAXLEV}
+    seen, fresh = [], set(range(4))
+    for r in runs:
+        sa, j, n, a0, is_fresh = decode(r)
+        assert n == 2 and 0 <= j < SLICES and a0 + 2 <= 4
+        accs = {a0, a0 + 1}
+        assert (accs <= fresh) if is_fresh else not (accs & fresh)
+        fresh -= accs
+        for t, sb in enumerate((j, j + 1)):      # even CTA: slice j; odd CTA: slice j + 1
+            a, lv = a0 + t, sa + sb
+            if sb >= SLICES:                     # the zero slot of the odd CTA
+                assert a >= 2
+                continue
+            seen.append((sa, sb))
+            assert a == lv if lv < 2 else a >= 2
+    assert not fresh
+    assert len(seen) == len(set(seen))
+    assert wanted <= set(seen)
+    assert all(s + t <= MAXLEV + 1 for s, t in set(seen) - wanted)  # extras: level 5 only

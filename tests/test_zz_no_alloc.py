@@ -6,8 +6,10 @@ forbids cudaMalloc, or a latency-critical loop where a cudaMalloc (which may
 synchronise the device) is not acceptable.  This entry point takes the
 caller's input and output buffers like modal_project_separable and keeps its
 scratch in a fixed-size buffer compiled into the library, so it allocates
-nothing.  The test calls it through the C ABI twice in a row and checks each
-result against modal_project_separable (same kernels, same FP64 bound).
+nothing.  The tests call it through the C ABI twice in a row and check each
+result against modal_project_separable (same kernels, same FP64 bound) and
+against the FP64 oracle; that the device's free memory does not change
+across a call; the FP32 form; and that oversized problems are refused.
 
 This file is named to be collected last.
 """
@@ -19,11 +21,13 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synthetic as syn
 
 pytestmark = pytest.mark.gpu
 
 TOL_FP64 = 1e-10
+TOL_FP32 = 2e-5
 
 
 @pytest.fixture(scope="module")
@@ -51,9 +55,11 @@ def test_noalloc_matches_separable_twice(mg):
     dp = mg.DeviceProblem.from_host(P)
     ref = mg.project_separable(dp).cpu().numpy()
     scale = np.abs(ref).max()
+    ref_oracle = oracle.separable(P)
     for _ in range(2):                       # the shared scratch keeps the last contents
         g = _noalloc(mg, dp).cpu().numpy()
         assert np.abs(g - ref).max() / scale < TOL_FP64
+        assert np.abs(g - ref_oracle).max() / np.abs(ref_oracle).max() < TOL_FP64
     # a second, different problem right after: nothing stale leaks through
     P2 = syn.make_problem(37, 7, 13, seed=8, nb_prim=3)
     dp2 = mg.DeviceProblem.from_host(P2)
@@ -61,6 +67,35 @@ def test_noalloc_matches_separable_twice(mg):
     for _ in range(2):
         g2 = _noalloc(mg, dp2).cpu().numpy()
         assert np.abs(g2 - ref2).max() / np.abs(ref2).max() < TOL_FP64
+
+
+def test_noalloc_leaves_free_memory_unchanged(mg):
+    """After a first call (which looks up the static array's address), a
+    second call into a preallocated output changes the device's free memory
+    by nothing: it allocates no device memory."""
+    P = syn.make_problem(60, 8, 6, seed=17)
+    dp = mg.DeviceProblem.from_host(P)
+    out = torch.empty(dp.n_late, dp.n_prim, dtype=torch.float64, device=dp.device)
+    _noalloc(mg, dp, out=out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    _noalloc(mg, dp, out=out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    ref = oracle.separable(P)
+    assert np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max() < TOL_FP64
+
+
+def test_noalloc_fp32_twice(mg):
+    P = syn.make_problem(48, 6, 10, seed=21, nb_prim=4)
+    dp = mg.DeviceProblem.from_host(P)
+    ref = mg.project_separable(dp, precision=mg.PREC_FP32).cpu().numpy()
+    ref_oracle = oracle.separable(P)
+    for _ in range(2):
+        g = _noalloc(mg, dp, precision=mg.PREC_FP32).cpu().numpy()
+        assert np.abs(g - ref).max() / np.abs(ref).max() < TOL_FP32
+        assert np.abs(g - ref_oracle).max() / np.abs(ref_oracle).max() < TOL_FP32
 
 
 def test_noalloc_rejects_oversized_problem(mg):
