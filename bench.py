@@ -44,8 +44,8 @@ TC_SLICE_PRODUCTS = 15       # BF16 slice products per useful MAC in the tensor-
 # capture (n_x = 4 gives one launch with the same K as every launch of the
 # 500-point step), keyed by the kernel's form.  A form that changed since its
 # capture is left out (its traffic is then reported as null).
-NCU_TRAFFIC = {("tc_gemm_triple", "single"): 5.557e9 + 48.4e6, ("tc_make_Y", "single"): 44.4e6 + 5.245e9,
-               ("tc_make_Y", "pair"): 44.4e6 + 5.245e9}
+NCU_TRAFFIC = {("tc_gemm_triple", "single"): 5.562e9 + 48.6e6, ("tc_make_Y", "single"): 44.3e6 + 5.245e9,
+               ("tc_make_Y", "pair"): 44.3e6 + 5.245e9, ("tc_make_Y", "queue"): 44.3e6 + 5.245e9}
 # kernels inside one profiler scope (the library counts kernels; a roofline
 # divides the scope's time by its scope count)
 SCOPE_KERNELS = {"tc_make_Y": 2, "tc_prep_M": 2}
@@ -79,7 +79,9 @@ def parse():
                     help="none: one independent problem per rank (weak scaling); x: the radial "
                          "points of one problem split over the ranks, Gamma' summed by an "
                          "all-reduce (strong scaling)")
-    ap.add_argument("--tc-pair", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--tc-queue", type=int, default=0, choices=[0, 1],
+                    help="tensor-core triple product GEMM as a persistent kernel over a work queue: 1")
+    ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1],
                     help="tensor-core triple product GEMM on CTA pairs (2-SM MMA): 1, or single CTAs: 0")
     ap.add_argument("--once", action="store_true",
                     help="run one projection and exit (a small case for profiler captures)")
@@ -244,6 +246,7 @@ def run_ours(args):
     h = mg.Handle(dev)
     mg.set_option(mg.OPT_TC_TRIPLE_FUSED, args.tc_fused, handle=h)
     mg.set_option(mg.OPT_TC_PAIR, args.tc_pair, handle=h)
+    mg.set_option(mg.OPT_TC_QUEUE, args.tc_queue, handle=h)
     dp = mg.DeviceProblem.from_host(P, device=dev, handle=h)
     gamma = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream(dev)
@@ -293,7 +296,7 @@ def run_ours(args):
     # ---- rooflines: the dominant kernel, and every tensor / HBM kernel ------
     peaks, src = measured_peaks()
     launches_per_step = {k: max(1, v[0] // args.steps) for k, v in prof.items()}
-    form = "pair" if args.tc_pair else "single"
+    form = "pair" if args.tc_pair else "queue" if args.tc_queue else "single"
     rooflines = {k: kernel_roofline(k, prof[k], launches_per_step[k], P, prec_name, peaks, src, args.steps, ms,
                                     form) for k in prof}
     rooflines = {k: v for k, v in rooflines.items() if v is not None}
@@ -355,7 +358,8 @@ def run_ours(args):
                        "n_mu": P.n_mu, "slices": P.slices, "precision": prec_name,
                        "n_modes": P.n_late, "tc_triple": ["Y through HBM", "shared-memory Y",
                                                           "shared-memory Y (16 warps)"][args.tc_fused],
-                       "tc_gemm": "CTA pairs (2-SM MMA)" if args.tc_pair else "single CTAs",
+                       "tc_gemm": ("CTA pairs (2-SM MMA)" if args.tc_pair else
+                                   "persistent work queue" if args.tc_queue else "one CTA per tile"),
                        "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)",
                        "parallelism": (f"x-sharded over {ws} ranks, FP64 all-reduce of Gamma'" if sharded
                                        else f"{ws} independent problem(s)")},
@@ -469,6 +473,7 @@ def run_once(args):
     P = syn.planck_size(n_x=args.n_x)
     mg.set_option(mg.OPT_TC_TRIPLE_FUSED, args.tc_fused)
     mg.set_option(mg.OPT_TC_PAIR, args.tc_pair)
+    mg.set_option(mg.OPT_TC_QUEUE, args.tc_queue)
     g = mg.project_separable(mg.DeviceProblem.from_host(P), precision=prec)
     if prec == PREC["ozaki"]:
         mg.handle_status()
@@ -572,6 +577,8 @@ def run_extra(args):
         "fp32" if args.workload == "grad" else "ozaki")
     prec = PREC[prec_name]
     h = mg.Handle(dev)
+    mg.set_option(mg.OPT_TC_PAIR, args.tc_pair, handle=h)
+    mg.set_option(mg.OPT_TC_QUEUE, args.tc_queue, handle=h)
     st = torch.cuda.current_stream(dev)
     unit = "slices/s"
     if args.workload == "grad":
@@ -649,6 +656,8 @@ def run_extra(args):
     if prec == PREC["ozaki"]:
         mg.handle_status(handle=h)
     ms = e0.elapsed_time(e1) / args.steps
+    if args.workload == "batched":
+        cfg["fp64_sequential"] = fp64_sequential(probs, dps, slices / (ms * 1e-3), dev, h)
     if args.workload == "full":
         cfg["parts_ms"] = {}
         for name, f in parts.items():
@@ -666,6 +675,35 @@ def run_extra(args):
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "dtype": dtype, "data": "synthetic",
                       "config": cfg}), flush=True)
+
+
+def fp64_sequential(probs, dps, batched_value, dev, h, n_pts: int = 2):
+    """The same models as 64 sequential plain FP64 calls (modal_project_separable,
+    MODAL_PREC_FP64), each timed on its first ``n_pts`` radial points (after a
+    warm-up call) and scaled by its radial point count -- the FP64 path's time
+    is linear in the number of slices; the per-call tables (GL nodes, Legendre
+    table) are inside every timed call."""
+    import torch
+    import paper_1503_08809_gb300 as mg
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms, sampled = 0.0, 0
+    for P, dp in zip(probs, dps):
+        sub = mg.shard_problem(dp, 0, max(1, P.n_x // n_pts))      # the first ~n_pts radial points
+        mg.project_separable(sub, precision=PREC["fp64"], handle=h)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        mg.project_separable(sub, precision=PREC["fp64"], handle=h)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        total_ms += e0.elapsed_time(e1) * P.n_x / sub.n_x
+        sampled += sub.n_x * P.n_mu
+    slices = sum(P.slices for P in probs)
+    value = slices / (total_ms * 1e-3)
+    return {"value": value, "unit": "slices/s", "ms_extrapolated": total_ms,
+            "sample": f"each of the {len(probs)} models on its first ~{n_pts} radial points "
+                      f"({sampled} slices timed), scaled by its radial point count",
+            "speedup_of_batched": batched_value / value}
 
 
 INTEGRATOR_NX = (27, 54, 108, 216, 432, 864)

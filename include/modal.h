@@ -136,6 +136,11 @@ int modal_handle_status(modal_handle *h);
  * MODAL_OPT_TC_PAIR: 1 runs the triple-product GEMM of MODAL_OPT_TC_TRIPLE_FUSED = 0
  *   on CTA pairs (clusters of two, 2-SM tcgen05 MMA with M = 256: each SM
  *   reads half of the B operand); 0 on single CTAs.  Same results to rounding.
+ * MODAL_OPT_TC_QUEUE: 1 runs that GEMM as a persistent kernel (one CTA per
+ *   SM) whose CTAs take work items -- (G tile, range of exact K chunks) --
+ *   from a device queue in order of decreasing modelled cost; tiles are split
+ *   into K ranges (summed with FP64 atomics) when there are fewer than two per
+ *   SM.  0: one CTA per tile.  Same results to rounding.
  * MODAL_OPT_BATCH_STREAMS: concurrent streams of modal_project_separable_batched
  *   (1 .. 8), or 0 (default): the first call for a problem set captures one
  *   graph each for 1, 2, 4 and 8 streams (as far as their scratch fits),
@@ -144,6 +149,7 @@ int modal_handle_status(modal_handle *h);
 #define MODAL_OPT_TC_SPLIT_K 2
 #define MODAL_OPT_BATCH_STREAMS 3
 #define MODAL_OPT_TC_PAIR 4
+#define MODAL_OPT_TC_QUEUE 5
 int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value);
 
 /* Bound (in SM clock cycles) of those device-side waits for later calls on

@@ -9,7 +9,7 @@ _PKG = Path(__file__).resolve().parent
 MODAL_OK, MODAL_EINVAL, MODAL_ENOMEM, MODAL_ECUDA, MODAL_ETIMEOUT, MODAL_EUNSUPPORTED = range(6)
 PREC_FP64, PREC_FP32, PREC_OZAKI_BF16, PREC_TF32, PREC_BF16X3 = 0, 1, 2, 3, 4
 XW_TRAPEZOID, XW_HERMITE = 0, 1
-OPT_TC_TRIPLE_FUSED, OPT_TC_SPLIT_K, OPT_BATCH_STREAMS, OPT_TC_PAIR = 1, 2, 3, 4
+OPT_TC_TRIPLE_FUSED, OPT_TC_SPLIT_K, OPT_BATCH_STREAMS, OPT_TC_PAIR, OPT_TC_QUEUE = 1, 2, 3, 4, 5
 W_EXACT_3J, W_SMOOTH_GOSPER = 0, 1
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}

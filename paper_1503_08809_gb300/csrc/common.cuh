@@ -117,6 +117,17 @@ struct GLayout {
   }
   __host__ __device__ int64_t size() const { return offset(nbl); }
   __host__ __device__ int64_t index(int a, int b, int uv, int c, int t) const {
+#ifdef MODAL_DEBUG
+    return checked_index(a, b, uv, c, t);
+#else
+    return offset(b) + ((int64_t)a * P2 + uv) * cols(b) + (int64_t)(c - b) * nbp + t;
+#endif
+  }
+  // index() with every argument checked: 0 <= a <= b <= c < nbl,
+  // 0 <= uv < P2, 0 <= t < nbp; -1 otherwise.  index() itself checks only in
+  // builds with MODAL_DEBUG defined (callers then skip a negative index).
+  __host__ __device__ int64_t checked_index(int a, int b, int uv, int c, int t) const {
+    if (a < 0 || a > b || b > c || c >= nbl || uv < 0 || uv >= P2 || t < 0 || t >= nbp) return -1;
     return offset(b) + ((int64_t)a * P2 + uv) * cols(b) + (int64_t)(c - b) * nbp + t;
   }
 };

@@ -40,9 +40,12 @@ __global__ void k_scatter_gbar(GLayout g, const double *__restrict__ gbar, const
   if (b > c) { int z = b; b = c; c = z; }
   if (a > b) { int z = a; a = b; b = z; }
   double v = scale * gbar[idx];
-  atomicAdd(Gbar + g.index(a, b, pair_index(p, r), c, t), v);
-  atomicAdd(Gbar + g.index(a, b, pair_index(p, t), c, r), v);
-  atomicAdd(Gbar + g.index(a, b, pair_index(r, t), c, p), v);
+  const int64_t i1 = g.index(a, b, pair_index(p, r), c, t), i2 = g.index(a, b, pair_index(p, t), c, r),
+                i3 = g.index(a, b, pair_index(r, t), c, p);
+  if (i1 < 0 || i2 < 0 || i3 < 0) return;  // only in MODAL_DEBUG builds (checked index helpers)
+  atomicAdd(Gbar + i1, v);
+  atomicAdd(Gbar + i2, v);
+  atomicAdd(Gbar + i3, v);
 }
 
 // ---- 2. dL/dM for a chunk of KS slices per CTA ------------------------------

@@ -378,9 +378,13 @@ __global__ void k_gather(GLayout g, const double *__restrict__ G, const int *__r
   if (a > b) { int z = a; a = b; b = z; }
   if (b > c) { int z = b; b = c; c = z; }
   if (a > b) { int z = a; a = b; b = z; }
-  double v = G[g.index(a, b, pair_index(p, r), c, t)] + G[g.index(a, b, pair_index(p, t), c, r)] +
-             G[g.index(a, b, pair_index(r, t), c, p)];
-  gamma[idx] = scale * v;
+  const int64_t i1 = g.index(a, b, pair_index(p, r), c, t), i2 = g.index(a, b, pair_index(p, t), c, r),
+                i3 = g.index(a, b, pair_index(r, t), c, p);
+  if (i1 < 0 || i2 < 0 || i3 < 0) {  // only in MODAL_DEBUG builds (checked index helpers)
+    gamma[idx] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
+  gamma[idx] = scale * (G[i1] + G[i2] + G[i3]);
 }
 
 cudaError_t launch_gather(const SepShape &s, const double *G, const int *late, const int *prim,

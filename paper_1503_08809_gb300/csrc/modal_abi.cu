@@ -41,6 +41,7 @@ struct modal_handle {
   int opt_triple_variant = TC_TRIPLE_MATERIALISED;
   int opt_split_k = 0;
   int opt_pair = 0;               // the triple GEMM on CTA pairs (2-SM MMA)
+  int opt_queue = 0;              // the triple GEMM as a persistent kernel over a work queue
   int opt_batch_streams = 0;      // 0: chosen by timing on the first call for a problem set
   Profiler prof;
   // batched calls: graphs of all launches, keyed by the problem set; the
@@ -276,6 +277,10 @@ int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value) {
       if (value < 0 || value > 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_PAIR takes 0 or 1");
       h->opt_pair = (int)value;
       return MODAL_OK;
+    case MODAL_OPT_TC_QUEUE:
+      if (value < 0 || value > 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_QUEUE takes 0 or 1");
+      h->opt_queue = (int)value;
+      return MODAL_OK;
     case MODAL_OPT_BATCH_STREAMS:
       if (value < 0 || value > MAX_BATCH_STREAMS)
         return fail(h, MODAL_EINVAL, "MODAL_OPT_BATCH_STREAMS takes 0 .. %d", MAX_BATCH_STREAMS);
@@ -394,7 +399,9 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   pl.variant = h ? h->opt_triple_variant : TC_TRIPLE_MATERIALISED;
   if (pl.variant == TC_TRIPLE_FUSED2 && !tc_fused2_fits(p->nb_late, p->nb_prim)) pl.variant = TC_TRIPLE_MATERIALISED;
   if (pl.variant == TC_TRIPLE_MATERIALISED && h && h->opt_pair) pl.variant = TC_TRIPLE_PAIR;
-  const bool y_hbm = pl.variant == TC_TRIPLE_MATERIALISED || pl.variant == TC_TRIPLE_PAIR;
+  else if (pl.variant == TC_TRIPLE_MATERIALISED && h && h->opt_queue) pl.variant = TC_TRIPLE_QUEUE;
+  const bool y_hbm = pl.variant == TC_TRIPLE_MATERIALISED || pl.variant == TC_TRIPLE_PAIR ||
+                     pl.variant == TC_TRIPLE_QUEUE;
   int n_mu, prec, xch;
   if (int r = resolve_opts(h, p, o, n_mu, prec, xch)) return r;
   pl.s = SepShape{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};
@@ -784,6 +791,7 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
   key = fnv1a(key, &h->opt_triple_variant, sizeof(int));
   key = fnv1a(key, &h->opt_split_k, sizeof(int));
   key = fnv1a(key, &h->opt_pair, sizeof(int));
+  key = fnv1a(key, &h->opt_queue, sizeof(int));
   key = fnv1a(key, &h->opt_batch_streams, sizeof(int));
   key = fnv1a(key, &h->wait_cycles, sizeof(long long));
   auto it = h->graphs.find(key);

@@ -32,7 +32,9 @@
 
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -793,6 +795,317 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OZ_THREADS, 1)
   if (warp == 1) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc_pair(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The triple GEMM as a persistent kernel draining a device work queue.
+//
+// Work items are (G tile, K range) pairs: a tile of a G block (128 rows x
+// w columns, as in k_ozaki_gemm<1>) over a whole number of exact K chunks.
+// The host lists them in order of decreasing modelled cost (longest first);
+// each CTA's producer thread takes the next item with an atomic fetch-add on
+// a counter in device memory and hands its number to the MMA thread and the
+// eight drain warps through a four-slot ring in shared memory (mbarriers
+// "item full" / "item empty", bounded waits), then streams the item's
+// operands.  The TMEM accumulators and the TMA ring carry on from item to
+// item, so one item's drain and write-out overlap the next item's MMAs.  A
+// tile split into several K ranges is summed into G with FP64 atomic adds.
+// No CTA ever waits for another CTA: the grid need not be resident at once.
+// ---------------------------------------------------------------------------
+constexpr int Q_ITEMS_MAX = 4096;  // items of the in-parameter queue table
+constexpr int Q_RING = 4;          // item slots between the producer and the consumers
+struct QueueParams {
+  OzParams o;
+  int n_items;       // items in the queue
+  int nkr;           // K ranges per tile (1: tiles are not split)
+  int chunks_per_kr; // exact K chunks per range (the last range may be shorter)
+  int *head;         // device counter of taken items (zero before the launch)
+  uint32_t item[Q_ITEMS_MAX];  // tile << 8 | K range, in the order of taking
+};
+
+// tile t of the triple product's block structure (tiles of 128 rows x w columns)
+__device__ __forceinline__ void q_tile(const GLayout &g, int t, int &bblk, int &rt, int &ct, int64_t &rowoff) {
+  rowoff = 0;
+  for (bblk = 0; bblk < g.nbl; ++bblk) {
+    const int nrt = (int)cdiv64(g.rows(bblk), OZ_BM), nct = (int)cdiv64(g.cols(bblk), OZ_BN);
+    if (t < nrt * nct) {
+      rt = t / nct;
+      ct = t % nct;
+      return;
+    }
+    t -= nrt * nct;
+    rowoff += g.rows(bblk);
+  }
+}
+
+struct QItem {
+  int64_t a_row0, b_row0, R, C, out_base, ldo;
+  int ntile, c0, c1;  // MMA width; K chunks [c0, c1)
+  bool lead, split;
+};
+
+__device__ __forceinline__ QItem q_decode(const QueueParams &Q, uint32_t code) {
+  QItem it;
+  const int t = (int)(code >> 8), kr = (int)(code & 0xffu);
+  int bblk, rt, ct;
+  int64_t rowoff;
+  q_tile(Q.o.g, t, bblk, rt, ct, rowoff);
+  it.ntile = g_tile_width(Q.o.g.cols(bblk));
+  it.a_row0 = rowoff + (int64_t)rt * OZ_BM;
+  it.b_row0 = (int64_t)bblk * Q.o.g.nbp + (int64_t)ct * it.ntile;
+  it.R = min((int64_t)OZ_BM, Q.o.g.rows(bblk) - (int64_t)rt * OZ_BM);
+  it.C = min((int64_t)it.ntile, Q.o.g.cols(bblk) - (int64_t)ct * it.ntile);
+  it.ldo = Q.o.g.cols(bblk);
+  it.out_base = Q.o.g.offset(bblk) + (int64_t)rt * OZ_BM * it.ldo + (int64_t)ct * it.ntile;
+  it.c0 = kr * Q.chunks_per_kr;
+  it.c1 = min(Q.o.nchunks, it.c0 + Q.chunks_per_kr);
+  it.lead = ct == 0 && kr == 0;
+  it.split = Q.nkr > 1;
+  return it;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_ozaki_gemm_q(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ BMaps bmaps,
+                   const __grid_constant__ QueueParams Q) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  float *lo_s = (float *)(sm + OZ_STAGES * OZ_STAGE_BYTES);  // [col][row]
+  uint64_t *full = (uint64_t *)(sm + OZ_STAGES * OZ_STAGE_BYTES + OZ_LO_BYTES);
+  uint64_t *empty = full + OZ_STAGES;
+  uint64_t *acc_full = empty + OZ_STAGES;
+  uint64_t *acc_empty = acc_full + 1;
+  uint64_t *mma_done = acc_empty + 1;
+  uint64_t *item_full = mma_done + 1;
+  uint64_t *item_empty = item_full + Q_RING;
+  uint32_t *tmem_slot = (uint32_t *)(item_empty + Q_RING);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+  volatile int *item_ring = (volatile int *)(tmem_slot + 2);  // [Q_RING]
+  const OzParams &P = Q.o;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(acc_full, 1);
+    ptx::mbar_init(acc_empty, OZ_EPI_WARPS);  // one arrival per drain warp
+    ptx::mbar_init(mma_done, 1);
+    for (int r = 0; r < Q_RING; ++r) {
+      ptx::mbar_init(&item_full[r], 1);
+      ptx::mbar_init(&item_empty[r], 1 + OZ_EPI_WARPS);  // the MMA thread and every drain warp
+    }
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_slot, 512);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int steps_per_chunk = OZ_KC / OZ_BK;
+  const int ksteps = P.Kpad / OZ_BK;
+
+  if (warp == 0) {
+    // ================= queue + TMA producer =================
+    if (lane == 0) {
+      ptx::prefetch_tmap(&tmA);
+      int issued = 0;  // stages issued by this CTA over all its items
+      for (int j = 0;; ++j) {
+        const int slot = j % Q_RING;
+        if (!ptx::mbar_wait(&item_empty[slot], (uint32_t)(((j / Q_RING) & 1) ^ 1), abort_flag, P.wait_cycles)) break;
+        const int it_no = atomicAdd(Q.head, 1);
+        const int code = it_no < Q.n_items ? (int)Q.item[it_no] : -1;
+        item_ring[slot] = code;
+        ptx::mbar_arrive(&item_full[slot]);  // release: the slot is written
+        if (code < 0) break;
+        const QItem it = q_decode(Q, (uint32_t)code);
+        const CUtensorMap *tmB = &bmaps.m[it.ntile / 16 - 1];
+        const uint32_t stage_bytes = (uint32_t)(OZ_A_BYTES + OZ_SLICES * it.ntile * OZ_ROWB);
+        const int i0 = it.c0 * steps_per_chunk, i1 = min(ksteps, it.c1 * steps_per_chunk);
+        const int ar = (int)it.a_row0;
+        if (it.lead)
+          for (int i = i0; i < i0 + OZ_PREFETCH && i < i1; ++i) ptx::tma_prefetch_3d(&tmA, i * OZ_BK, ar, 0);
+        bool stop = false;
+        for (int i = i0; i < i1; ++i) {
+          const int s = issued % OZ_STAGES;
+          const uint32_t ph = (uint32_t)((issued / OZ_STAGES) & 1);
+          if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_cycles)) {
+            stop = true;
+            break;
+          }
+          unsigned char *st = sm + s * OZ_STAGE_BYTES;
+          ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
+          ptx::tma_load_3d(st, &tmA, &full[s], i * OZ_BK, ar, 0);
+          ptx::tma_load_3d(st + OZ_A_BYTES, tmB, &full[s], i * OZ_BK, (int)it.b_row0, 0);
+          if (it.lead && i + OZ_PREFETCH < i1) ptx::tma_prefetch_3d(&tmA, (i + OZ_PREFETCH) * OZ_BK, ar, 0);
+          ++issued;
+        }
+        if (stop) break;
+      }
+      if (*abort_flag) {  // the copies in flight land before shared memory is released
+        for (int i = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); i < issued; ++i) {
+          volatile int dummy = 0;
+          ptx::mbar_wait(&full[i % OZ_STAGES], (uint32_t)((i / OZ_STAGES) & 1), &dummy, OZ_WAIT_CYCLES);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ================= MMA issuer =================
+    if (lane == 0) {
+      const uint32_t idesc0 = ptx::idesc_bf16_f32(OZ_BM, 0);
+      const uint32_t sbase = ptx::smem_u32(sm);
+      int g = 0;      // stages consumed over all items
+      int chunk = 0;  // chunks over all items (accumulator phases)
+      for (int j = 0;; ++j) {
+        const int slot = j % Q_RING;
+        if (!ptx::mbar_wait(&item_full[slot], (uint32_t)((j / Q_RING) & 1), abort_flag, P.wait_cycles)) break;
+        const int code = item_ring[slot];
+        ptx::mbar_arrive(&item_empty[slot]);
+        if (code < 0) break;
+        const QItem it = q_decode(Q, (uint32_t)code);
+        const uint32_t *plan = P.plan[it.ntile / 16 - 1];
+        const int nruns = (int)(plan[0] & 0xffu);
+        const int i0 = it.c0 * steps_per_chunk, i1 = min(ksteps, it.c1 * steps_per_chunk);
+        bool stop = false;
+        for (int i = i0; i < i1; ++i, ++g) {
+          const int s = g % OZ_STAGES;
+          const uint32_t ph = (uint32_t)((g / OZ_STAGES) & 1);
+          const bool chunk_start = ((i - i0) % steps_per_chunk) == 0;
+          if (chunk_start && chunk > 0 &&
+              !ptx::mbar_wait(acc_empty, (uint32_t)((chunk - 1) & 1), abort_flag, P.wait_cycles)) {
+            stop = true;
+            break;
+          }
+          if (!ptx::mbar_wait(&full[s], ph, abort_flag, P.wait_cycles)) {
+            stop = true;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t a0 = sbase + s * OZ_STAGE_BYTES;
+          const uint64_t ad0 = ptx::smem_desc(a0, 16, 8 * OZ_ROWB, ptx::SW_64B);
+          const uint64_t bd0 = ptx::smem_desc(a0 + OZ_A_BYTES, 16, 8 * OZ_ROWB, ptx::SW_64B);
+#pragma unroll
+          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+#pragma unroll
+            for (int r = 0; r < OZ_PLAN_MAX; ++r) {
+              if (r >= nruns) break;
+              const uint32_t e = plan[1 + r];
+              const uint32_t sa = e & 15u, sb = (e >> 4) & 15u, n = (e >> 8) & 15u, acc = (e >> 12) & 15u;
+              const bool first = chunk_start && kk == 0 && ((e >> 16) & 1u);
+              const uint32_t N = n * (uint32_t)it.ntile;
+              const uint64_t ad = ad0 + (uint64_t)((sa * OZ_BM * OZ_ROWB + kk * 32) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((sb * (uint32_t)it.ntile * OZ_ROWB + kk * 32) >> 4);
+              ptx::mma_bf16(tmem + acc * (uint32_t)it.ntile, ad, bd, idesc0 | ((N >> 3) << 17), first ? 0u : 1u);
+            }
+          }
+          ptx::mma_commit(&empty[s]);
+          if (((i - i0 + 1) % steps_per_chunk) == 0 || i + 1 == i1) {
+            ptx::mma_commit(acc_full);
+            ++chunk;
+          }
+        }
+        if (stop) break;
+      }
+      ptx::mma_commit(mma_done);
+      volatile int dummy = 0;
+      ptx::mbar_wait(mma_done, 0, &dummy, OZ_WAIT_CYCLES);
+    }
+  } else {
+    // ================= drain each chunk into double-FP32; write the item out =================
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int chalf = ew >> 2;
+    const int row = quarter * 32 + lane;
+    const int col0 = chalf * 64;
+    const int emA = *P.emaxA, emB = *P.emaxB;
+    const int ebias = emA + emB + 40;
+    float hi[64];
+    int chunk = 0;
+    bool ok = true;
+    for (int j = 0; ok; ++j) {
+      const int slot = j % Q_RING;
+      const bool got_item = ptx::mbar_wait(&item_full[slot], (uint32_t)((j / Q_RING) & 1), abort_flag, P.wait_cycles);
+      if (!__all_sync(0xffffffffu, got_item)) break;
+      const int code = item_ring[slot];
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&item_empty[slot]);
+      if (code < 0) break;
+      const QItem it = q_decode(Q, (uint32_t)code);
+      const int nacc = (int)((P.plan[it.ntile / 16 - 1][0] >> 8) & 0xffu);
+#pragma unroll
+      for (int c = 0; c < 64; ++c) {
+        hi[c] = 0.f;
+        lo_s[(col0 + c) * OZ_BM + row] = 0.f;
+      }
+      for (int ch = it.c0; ch < it.c1; ++ch, ++chunk) {
+        const bool got = ptx::mbar_wait(acc_full, (uint32_t)(chunk & 1), abort_flag, P.wait_cycles);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const int ea = (it.a_row0 + row < P.rowsA) ? P.eA[(int64_t)ch * P.rowsA + it.a_row0 + row] : -100000;
+        const float fa = pow2f_or0(ea - emA);
+        float fbl[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t bcol = it.b_row0 + col0 + h * 32 + lane;
+          const int eb = (bcol < P.rowsB) ? __ldg(P.eB + (int64_t)ch * P.rowsB + bcol) : -100000;
+          fbl[h] = pow2f_or0(eb - emB - 2 * OZ_BETA - 40);
+        }
+        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+        for (int cb = 0; cb < 16; ++cb) {
+          if (col0 + cb * 4 >= it.ntile) break;  // columns beyond the MMA width (warp-uniform)
+          float v0[4], v1[4], v2[4], v3[4], v4[4];
+          const uint32_t cc = (uint32_t)(col0 + cb * 4);
+          const uint32_t w = (uint32_t)it.ntile;
+          ptx::tmem_ld4(tl + cc, v0);
+          ptx::tmem_ld4(tl + w + cc, v1);
+          ptx::tmem_ld4(tl + 2 * w + cc, v2);
+          ptx::tmem_ld4(tl + 3 * w + cc, v3);
+          if (nacc > 4) ptx::tmem_ld4(tl + 4 * w + cc, v4);
+          ptx::tmem_ld_wait();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v2[k] += nacc > 4 ? v3[k] + v4[k] : v3[k];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int c = cb * 4 + k;
+            const float f = fa * __shfl_sync(0xffffffffu, fbl[c >> 5], c & 31);
+            float s = v0[k] + v1[k];
+            float bb = s - v0[k];
+            float e = (v0[k] - (s - bb)) + (v1[k] - bb);
+            e += v2[k];
+            float lo = lo_s[(col0 + c) * OZ_BM + row];
+            df_add(hi[c], lo, s * f, e * f);
+            lo_s[(col0 + c) * OZ_BM + row] = lo;
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(acc_empty);
+      }
+      if (ok && !*abort_flag && row < it.R) {
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          const int col = col0 + c;
+          if (col < it.C) {
+            const double v = f32_scaled_f64(hi[c], ebias) + f32_scaled_f64(lo_s[(col0 + c) * OZ_BM + row], ebias);
+            double *d = P.out + it.out_base + (int64_t)row * it.ldo + col;
+            if (it.split) atomicAdd(d, v);  // other K ranges of the tile add concurrently
+            else *d += v;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(P.err, ERR_TIMEOUT);
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 512);
   }
 }
 
@@ -1958,9 +2271,10 @@ size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
   b += up256((size_t)Kpad * nblp * 8) + up256((size_t)nch * nblp * 8); // Mdf, column maxima
   b += up256((size_t)nch * nblp * 8) + up256((size_t)nch * nblp * 4);  // mxW, eB
   b += up256((size_t)OZ_SLICES * nblp * Kpad * 2);                     // Bt
-  if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR || variant == TC_TRIPLE_FUSED2)
+  const bool y_hbm = variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR || variant == TC_TRIPLE_QUEUE;
+  if (y_hbm || variant == TC_TRIPLE_FUSED2)
     b += up256((size_t)nch * y_rows(s) * 4);                            // eY
-  if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR)
+  if (y_hbm)
     b += up256((size_t)OZ_SLICES * y_rows(s) * Kpad * 2);               // Y slices
   return b;
 }
@@ -1991,6 +2305,77 @@ static int make_mt_map(CUtensorMap *m, const void *base, int64_t rows, int Kpad,
   if (r != CUDA_SUCCESS) {
     snprintf(g_tc_err, sizeof g_tc_err, "cuTensorMapEncodeTiled (M~) failed (%d)", (int)r);
     return MODAL_EINVAL;
+  }
+  return MODAL_OK;
+}
+
+// Modelled issue cost (clocks) of one 16-deep K step of a tile of width w:
+// max(80, N/2) per MMA of its schedule (mma_plan.h).
+static double plan_step_cost(const uint32_t (&plan)[1 + OZ_PLAN_MAX], int w) {
+  double c = 0.0;
+  for (int r = 0; r < (int)(plan[0] & 0xffu); ++r) {
+    const double N = (double)(((plan[1 + r] >> 8) & 15u) * (uint32_t)w);
+    c += N / 2.0 > 80.0 ? N / 2.0 : 80.0;
+  }
+  return c;
+}
+
+// The persistent queue GEMM: items (tile, K range) in order of decreasing
+// modelled cost; tiles are split into K ranges when there are too few of
+// them to give every SM two; grid = min(items, SMs).  Returns MODAL_EUNSUPPORTED
+// (the caller falls back to one CTA per tile) beyond the queue table's size.
+static int launch_queue_gemm(OzParams &P, const CUtensorMap &ta, const BMaps &tb, int nbl, int num_sms,
+                             int *head, cudaStream_t st, Profiler *prof) {
+  static QueueParams Q;  // host staging of the (large) parameter block
+  static std::mutex qm;
+  std::lock_guard<std::mutex> lock(qm);
+  Q.o = P;
+  fill_mma_plans(Q.o.plan);
+  struct It {
+    double cost;
+    uint32_t code;
+  };
+  std::vector<It> tiles;
+  for (int b = 0, t = 0; b < nbl; ++b) {
+    const int w = g_tile_width(P.g.cols(b));
+    const double c = plan_step_cost(Q.o.plan[w / 16 - 1], w);
+    const int n = (int)(cdiv64(P.g.rows(b), OZ_BM) * cdiv64(P.g.cols(b), OZ_BN));
+    for (int i = 0; i < n; ++i, ++t) tiles.push_back({c, (uint32_t)t});
+  }
+  const int ntiles = (int)tiles.size();
+  int nkr = 1;
+  if (ntiles < 2 * num_sms) nkr = (int)cdiv64(2 * num_sms, ntiles);
+  if (nkr > P.nchunks) nkr = P.nchunks;
+  if (nkr > 255) nkr = 255;
+  if (nkr < 1) nkr = 1;
+  const int cpk = (int)cdiv64(P.nchunks, nkr);
+  nkr = (int)cdiv64(P.nchunks, cpk);
+  if ((int64_t)ntiles * nkr > Q_ITEMS_MAX) return MODAL_EUNSUPPORTED;
+  std::vector<It> items;
+  for (auto &t : tiles)
+    for (int k = 0; k < nkr; ++k) {
+      const int nc = (k + 1) * cpk <= P.nchunks ? cpk : P.nchunks - k * cpk;
+      items.push_back({t.cost * nc, t.code << 8 | (uint32_t)k});
+    }
+  std::stable_sort(items.begin(), items.end(), [](const It &a, const It &b) { return a.cost > b.cost; });
+  Q.n_items = (int)items.size();
+  Q.nkr = nkr;
+  Q.chunks_per_kr = cpk;
+  Q.head = head;
+  for (int i = 0; i < Q.n_items; ++i) Q.item[i] = items[i].code;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(head, 0, sizeof(int), st)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_ozaki_gemm_q, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
+          cudaSuccess) {
+    snprintf(g_tc_err, sizeof g_tc_err, "queue GEMM set-up: %s", cudaGetErrorString(e));
+    return MODAL_ECUDA;
+  }
+  const int grid = Q.n_items < num_sms ? Q.n_items : num_sms;
+  ProfScope ps(prof, "tc_gemm_triple", st);
+  k_ozaki_gemm_q<<<grid, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, Q);
+  if ((e = cudaGetLastError()) != cudaSuccess) {
+    snprintf(g_tc_err, sizeof g_tc_err, "queue GEMM launch: %s", cudaGetErrorString(e));
+    return MODAL_ECUDA;
   }
   return MODAL_OK;
 }
@@ -2068,7 +2453,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
     return MODAL_OK;
   }
-  if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR) {
+  if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR || variant == TC_TRIPLE_QUEUE) {
     // Y slices through HBM, then the TMA-fed GEMM for both operands (single
     // CTAs, or CTA pairs with the 2-SM MMA)
     const int64_t rowsY = y_rows(s);
@@ -2109,6 +2494,10 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     P.err = words;
     P.g = make_glayout(s.nbl, s.nbp);
     P.wait_cycles = wait_cycles;
+    if (variant == TC_TRIPLE_QUEUE) {
+      const int r = launch_queue_gemm(P, ta, tb, s.nbl, num_sms, words + 16, st, prof);
+      if (r != MODAL_EUNSUPPORTED) return r;  // else (more items than the table holds): one CTA per tile
+    }
     if (variant == TC_TRIPLE_PAIR) {
       // one schedule for every width (pair_plan), two 128-row tiles per cluster
       for (int i = 0; i < OZ_BN / 16; ++i) plan::pair_plan(P.plan[i]);

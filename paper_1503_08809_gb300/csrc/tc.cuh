@@ -9,7 +9,8 @@ namespace modal {
 constexpr int TC_TRIPLE_MATERIALISED = 0;
 constexpr int TC_TRIPLE_FUSED = 1;
 constexpr int TC_TRIPLE_FUSED2 = 2;
-constexpr int TC_TRIPLE_PAIR = 3;  // Y through HBM, GEMM on CTA pairs (2-SM MMA)
+constexpr int TC_TRIPLE_PAIR = 3;   // Y through HBM, GEMM on CTA pairs (2-SM MMA)
+constexpr int TC_TRIPLE_QUEUE = 4;  // Y through HBM, persistent GEMM over a work queue
 // whether the second fused form can serve a basis (its M~ tile per stage)
 bool tc_fused2_fits(int nbl, int nbp);
 // scratch for l-contraction chunks of nxl radial points and triple-product

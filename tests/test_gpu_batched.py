@@ -91,3 +91,22 @@ def test_batched_bounded_wait_status_from_every_stream(mg):
     for g, P in zip(gs, probs):
         assert normwise(g, oracle.separable(P)) < 1e-8
     h.close()
+
+
+def test_batched_larger_bases_against_oracle(mg):
+    """Bases of 12 to 20 functions (up to 1540 modes a side) in one batched
+    call, in the plain FP64 form and the tensor-core form: every result
+    against the oracle at that form's bound."""
+    probs = [syn.make_problem(40, 12, 4, seed=61, nb_prim=12),
+             syn.make_problem(52, 16, 3, seed=62, nb_prim=14),
+             syn.make_problem(36, 20, 3, seed=63, nb_prim=20)]
+    refs = [oracle.separable(P) for P in probs]
+    for precision, tol in ((0, 1e-10), (2, 1e-8)):
+        h = mg.Handle()
+        dps = [mg.DeviceProblem.from_host(P, handle=h) for P in probs]
+        gs = mg.project_separable_batched(dps, precision=precision, handle=h)
+        if precision == 2:
+            mg.handle_status(handle=h)
+        for g, ref in zip(gs, refs):
+            assert normwise(g, ref) < tol
+        h.close()
