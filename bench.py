@@ -81,6 +81,8 @@ def parse():
                          "all-reduce (strong scaling)")
     ap.add_argument("--tc-queue", type=int, default=0, choices=[0, 1],
                     help="tensor-core triple product GEMM as a persistent kernel over a work queue: 1")
+    ap.add_argument("--tc-overlap", type=int, default=0,
+                    help="SMs left to the Y pass running beside the queue GEMM (0: no overlap)")
     ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1],
                     help="tensor-core triple product GEMM on CTA pairs (2-SM MMA): 1, or single CTAs: 0")
     ap.add_argument("--once", action="store_true",
@@ -247,6 +249,7 @@ def run_ours(args):
     mg.set_option(mg.OPT_TC_TRIPLE_FUSED, args.tc_fused, handle=h)
     mg.set_option(mg.OPT_TC_PAIR, args.tc_pair, handle=h)
     mg.set_option(mg.OPT_TC_QUEUE, args.tc_queue, handle=h)
+    mg.set_option(mg.OPT_TC_OVERLAP, args.tc_overlap, handle=h)
     dp = mg.DeviceProblem.from_host(P, device=dev, handle=h)
     gamma = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream(dev)
@@ -296,7 +299,7 @@ def run_ours(args):
     # ---- rooflines: the dominant kernel, and every tensor / HBM kernel ------
     peaks, src = measured_peaks()
     launches_per_step = {k: max(1, v[0] // args.steps) for k, v in prof.items()}
-    form = "pair" if args.tc_pair else "queue" if args.tc_queue else "single"
+    form = "pair" if args.tc_pair else "queue" if (args.tc_queue or args.tc_overlap) else "single"
     rooflines = {k: kernel_roofline(k, prof[k], launches_per_step[k], P, prec_name, peaks, src, args.steps, ms,
                                     form) for k in prof}
     rooflines = {k: v for k, v in rooflines.items() if v is not None}
@@ -359,6 +362,8 @@ def run_ours(args):
                        "n_modes": P.n_late, "tc_triple": ["Y through HBM", "shared-memory Y",
                                                           "shared-memory Y (16 warps)"][args.tc_fused],
                        "tc_gemm": ("CTA pairs (2-SM MMA)" if args.tc_pair else
+                                   f"persistent work queue on {152 - args.tc_overlap} SMs, Y pass beside it"
+                                   if args.tc_overlap else
                                    "persistent work queue" if args.tc_queue else "one CTA per tile"),
                        "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)",
                        "parallelism": (f"x-sharded over {ws} ranks, FP64 all-reduce of Gamma'" if sharded
@@ -474,6 +479,7 @@ def run_once(args):
     mg.set_option(mg.OPT_TC_TRIPLE_FUSED, args.tc_fused)
     mg.set_option(mg.OPT_TC_PAIR, args.tc_pair)
     mg.set_option(mg.OPT_TC_QUEUE, args.tc_queue)
+    mg.set_option(mg.OPT_TC_OVERLAP, args.tc_overlap)
     g = mg.project_separable(mg.DeviceProblem.from_host(P), precision=prec)
     if prec == PREC["ozaki"]:
         mg.handle_status()

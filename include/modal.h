@@ -141,6 +141,18 @@ int modal_handle_status(modal_handle *h);
  *   from a device queue in order of decreasing modelled cost; tiles are split
  *   into K ranges (summed with FP64 atomics) when there are fewer than two per
  *   SM.  0: one CTA per tile.  Same results to rounding.
+ * MODAL_OPT_TC_AUTOTUNE: 1 (default): the first batched call for a problem
+ *   set times the tensor-core triple GEMM's tile shapes -- one CTA per tile,
+ *   or the queue form with column tiles of at most 128 or 64 and with or
+ *   without K splits -- on one radial chunk of the first problem of each
+ *   bucket (l_max in steps of 250, both basis sizes, n_x in steps of 100)
+ *   that has no choice yet, keeps the fastest per bucket on the handle and
+ *   blocks until done; later calls (batched or single) of a bucket use it.
+ *   0: no timing, the other options decide (and the choices are dropped).
+ * MODAL_OPT_TC_OVERLAP: n > 0 runs the Y pass of each radial chunk on a
+ *   second stream beside the previous chunk's GEMM, which then runs as the
+ *   queue form on all but n SMs (two scratch sets; single-problem calls
+ *   without error_estimate; implies MODAL_OPT_TC_QUEUE).  0 (default): off.
  * MODAL_OPT_BATCH_STREAMS: concurrent streams of modal_project_separable_batched
  *   (1 .. 8), or 0 (default): the first call for a problem set captures one
  *   graph each for 1, 2, 4 and 8 streams (as far as their scratch fits),
@@ -150,6 +162,8 @@ int modal_handle_status(modal_handle *h);
 #define MODAL_OPT_BATCH_STREAMS 3
 #define MODAL_OPT_TC_PAIR 4
 #define MODAL_OPT_TC_QUEUE 5
+#define MODAL_OPT_TC_AUTOTUNE 6
+#define MODAL_OPT_TC_OVERLAP 7
 int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value);
 
 /* Bound (in SM clock cycles) of those device-side waits for later calls on

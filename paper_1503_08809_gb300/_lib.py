@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 _PKG = Path(__file__).resolve().parent
@@ -9,7 +10,7 @@ _PKG = Path(__file__).resolve().parent
 MODAL_OK, MODAL_EINVAL, MODAL_ENOMEM, MODAL_ECUDA, MODAL_ETIMEOUT, MODAL_EUNSUPPORTED = range(6)
 PREC_FP64, PREC_FP32, PREC_OZAKI_BF16, PREC_TF32, PREC_BF16X3 = 0, 1, 2, 3, 4
 XW_TRAPEZOID, XW_HERMITE = 0, 1
-OPT_TC_TRIPLE_FUSED, OPT_TC_SPLIT_K, OPT_BATCH_STREAMS, OPT_TC_PAIR, OPT_TC_QUEUE = 1, 2, 3, 4, 5
+OPT_TC_TRIPLE_FUSED, OPT_TC_SPLIT_K, OPT_BATCH_STREAMS, OPT_TC_PAIR, OPT_TC_QUEUE, OPT_TC_AUTOTUNE, OPT_TC_OVERLAP = 1, 2, 3, 4, 5, 6, 7
 W_EXACT_3J, W_SMOOTH_GOSPER = 0, 1
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
@@ -50,7 +51,8 @@ class Opts(ctypes.Structure):
 
 
 def lib_path() -> Path:
-    return _PKG / "_build" / "libmodal.so"
+    debug = os.environ.get("MODAL_DEBUG", "") not in ("", "0")   # the checked-index build
+    return _PKG / ("_build_debug" if debug else "_build") / "libmodal.so"
 
 
 _LIB = None

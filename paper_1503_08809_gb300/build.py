@@ -15,12 +15,16 @@ from pathlib import Path
 PKG = Path(__file__).resolve().parent
 ROOT = PKG.parent
 CSRC = PKG / "csrc"
-BUILD = PKG / "_build"
+# MODAL_DEBUG=1 in the environment builds (and _lib loads) a separate
+# library with -DMODAL_DEBUG: the triple-product table's index helper checks
+# every argument and the gather/scatter kernels skip a rejected index.
+DEBUG = os.environ.get("MODAL_DEBUG", "") not in ("", "0")
+BUILD = PKG / ("_build_debug" if DEBUG else "_build")
 LIB = BUILD / "libmodal.so"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-Xptxas", "-warn-spills", "-I", str(ROOT / "include")]
+         "-Xptxas", "-warn-spills", "-I", str(ROOT / "include")] + (["-DMODAL_DEBUG"] if DEBUG else [])
 
 
 def nvcc() -> str:

@@ -42,6 +42,14 @@ struct modal_handle {
   int opt_split_k = 0;
   int opt_pair = 0;               // the triple GEMM on CTA pairs (2-SM MMA)
   int opt_queue = 0;              // the triple GEMM as a persistent kernel over a work queue
+  int opt_autotune = 1;           // batched calls time the triple GEMM's tile shapes per bucket
+  int opt_overlap = 0;            // SMs left to the Y pass beside the queue GEMM (0: no overlap)
+  cudaStream_t ovl_stream = nullptr;
+  cudaEvent_t ovl_ev[6] = {};     // fork, l contraction done, side done, prep[2] / gemm[2] (below)
+  cudaEvent_t ovl_prep[2] = {}, ovl_gemm[2] = {};
+  // tile shape chosen per problem bucket (tile_bucket): 0 = one CTA per tile,
+  // 1 + tune = the queue form with that tile shape
+  std::unordered_map<uint64_t, int> tile_choice;
   int opt_batch_streams = 0;      // 0: chosen by timing on the first call for a problem set
   Profiler prof;
   // batched calls: graphs of all launches, keyed by the problem set; the
@@ -206,6 +214,13 @@ int modal_handle_destroy(modal_handle *h) {
     if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
   }
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->ovl_stream) cudaStreamDestroy(h->ovl_stream);
+  for (int i = 0; i < 6; ++i)
+    if (h->ovl_ev[i]) cudaEventDestroy(h->ovl_ev[i]);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ovl_prep[i]) cudaEventDestroy(h->ovl_prep[i]);
+    if (h->ovl_gemm[i]) cudaEventDestroy(h->ovl_gemm[i]);
+  }
   if (h->err_event) cudaEventDestroy(h->err_event);
   if (h->pinned_i64) cudaFreeHost(h->pinned_i64);
   tc_release(h->device);
@@ -280,6 +295,16 @@ int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value) {
     case MODAL_OPT_TC_QUEUE:
       if (value < 0 || value > 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_QUEUE takes 0 or 1");
       h->opt_queue = (int)value;
+      return MODAL_OK;
+    case MODAL_OPT_TC_AUTOTUNE:
+      if (value < 0 || value > 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_AUTOTUNE takes 0 or 1");
+      h->opt_autotune = (int)value;
+      if (!value) h->tile_choice.clear();
+      return MODAL_OK;
+    case MODAL_OPT_TC_OVERLAP:
+      if (value < 0 || value > h->num_sms / 2)
+        return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_OVERLAP takes 0 .. %d", h->num_sms / 2);
+      h->opt_overlap = (int)value;
       return MODAL_OK;
     case MODAL_OPT_BATCH_STREAMS:
       if (value < 0 || value > MAX_BATCH_STREAMS)
@@ -385,6 +410,8 @@ struct SepPlan {
   SepShape s;
   int prec;
   int variant;  // tensor-core triple-product variant
+  int tune = 0; // tile shape of the queue variant (tc.cuh tune_wmax / tune_split)
+  int overlap = 0;  // > 0: Y pass beside the queue GEMM, which keeps num_sms - overlap SMs
   int nxl;      // radial points per l-contraction chunk (tensor-core form; = nxc otherwise)
   int nxc;      // radial points per chunk
   int ksplit;   // K split of the SIMT triple product
@@ -394,12 +421,26 @@ struct SepPlan {
   size_t bytes;
 };
 
+// Bucket of a problem for the tile autotuner: l_max in steps of 250, both
+// basis sizes, and the radial count in steps of 100.
+static uint64_t tile_bucket(const modal_problem *p) {
+  return (uint64_t)(p->l_max / 250) << 40 | (uint64_t)p->nb_late << 28 | (uint64_t)p->nb_prim << 16 |
+         (uint64_t)(p->n_x / 100);
+}
+
 static int plan_separable(modal_handle *h, const modal_problem *p, const modal_opts *o, SepPlan &pl,
                           int num_sms) {
   pl.variant = h ? h->opt_triple_variant : TC_TRIPLE_MATERIALISED;
   if (pl.variant == TC_TRIPLE_FUSED2 && !tc_fused2_fits(p->nb_late, p->nb_prim)) pl.variant = TC_TRIPLE_MATERIALISED;
   if (pl.variant == TC_TRIPLE_MATERIALISED && h && h->opt_pair) pl.variant = TC_TRIPLE_PAIR;
-  else if (pl.variant == TC_TRIPLE_MATERIALISED && h && h->opt_queue) pl.variant = TC_TRIPLE_QUEUE;
+  else if (pl.variant == TC_TRIPLE_MATERIALISED && h && (h->opt_queue || h->opt_overlap)) pl.variant = TC_TRIPLE_QUEUE;
+  if ((pl.variant == TC_TRIPLE_MATERIALISED || pl.variant == TC_TRIPLE_QUEUE) && h && h->opt_autotune) {
+    auto it = h->tile_choice.find(tile_bucket(p));
+    if (it != h->tile_choice.end()) {  // the autotuner's choice for this bucket
+      pl.variant = it->second == 0 ? TC_TRIPLE_MATERIALISED : TC_TRIPLE_QUEUE;
+      pl.tune = it->second == 0 ? 0 : it->second - 1;
+    }
+  }
   const bool y_hbm = pl.variant == TC_TRIPLE_MATERIALISED || pl.variant == TC_TRIPLE_PAIR ||
                      pl.variant == TC_TRIPLE_QUEUE;
   int n_mu, prec, xch;
@@ -456,9 +497,64 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   b += align256(sizeof(double) * (size_t)pl.Gsize);               // G
   if (pl.est) b += align256(sizeof(double) * (size_t)pl.Gsize);   // G of |M| (error scale)
   if (need_part) b += align256(sizeof(double) * (size_t)pl.Gsize * pl.ksplit);
-  if (prec == MODAL_PREC_OZAKI_BF16) b += tc_scratch_bytes(pl.s, pl.nxl, pl.nxc, pl.variant);
+  pl.overlap = (prec == MODAL_PREC_OZAKI_BF16 && pl.variant == TC_TRIPLE_QUEUE && h && h->opt_overlap > 0 &&
+                !pl.est) ? h->opt_overlap : 0;
+  if (prec == MODAL_PREC_OZAKI_BF16)
+    b += pl.overlap ? tc_ovl_scratch_bytes(pl.s, pl.nxl, pl.nxc) : tc_scratch_bytes(pl.s, pl.nxl, pl.nxc, pl.variant);
   if (prec == MODAL_PREC_TF32 || prec == MODAL_PREC_BF16X3) b += fa_scratch_bytes(pl.s, pl.nxc);
   pl.bytes = b + 1024;
+  return MODAL_OK;
+}
+
+// The tensor-core form with the Y pass of each radial chunk beside the GEMM
+// of the previous one: the l contraction and the queue GEMM (on
+// num_sms - overlap SMs) on the call's stream, the operand passes (column
+// statistics, M~ and B slices, Y slices) on a second stream, two scratch
+// sets alternating between chunks:
+//   main: [l contraction L] -> GEMM(c) after prep(c)      (records gemm[c % 2])
+//   side: prep(c) after the l contraction of its l-chunk and after GEMM(c - 2)
+//   main waits for the side's last prep of l-chunk L before l contraction L + 1.
+static int run_tc_overlap(modal_handle *h, int num_sms, const modal_problem *p, const SepPlan &pl, void *tcs,
+                          double *M, const double *om, const double *A, double *G, cudaStream_t st,
+                          bool first_in_call) {
+  const SepShape &s = pl.s;
+  if (!h->ovl_stream) CK(cudaStreamCreateWithFlags(&h->ovl_stream, cudaStreamNonBlocking));
+  for (int i = 0; i < 3; ++i)
+    if (!h->ovl_ev[i]) CK(cudaEventCreateWithFlags(&h->ovl_ev[i], cudaEventDisableTiming));
+  for (int i = 0; i < 2; ++i) {
+    if (!h->ovl_prep[i]) CK(cudaEventCreateWithFlags(&h->ovl_prep[i], cudaEventDisableTiming));
+    if (!h->ovl_gemm[i]) CK(cudaEventCreateWithFlags(&h->ovl_gemm[i], cudaEventDisableTiming));
+  }
+  cudaStream_t side = h->ovl_stream;
+  Profiler *prof = h->prof.on ? &h->prof : nullptr;
+  const long long wc = h->wait_cycles;
+  const int grid_sms = num_sms - pl.overlap;
+  if (int r = tc_prepare_l(s, A, p->q, tcs, pl.nxl, st, prof, first_in_call))
+    return fail(h, r, "tensor-core operand split failed: %s", tc_last_error());
+  int gc = 0;  // chunk count
+  for (int x0 = 0; x0 < p->n_x; x0 += pl.nxl) {
+    const int nl = (p->n_x - x0) < pl.nxl ? (p->n_x - x0) : pl.nxl;
+    if (x0 > 0) CK(cudaStreamWaitEvent(st, h->ovl_ev[2], 0));  // the side has read the previous M
+    if (int r = tc_contract_l(s, p->qt, x0, nl, pl.nxl, M, tcs, wc, st, prof))
+      return fail(h, r, "tensor-core l contraction failed: %s", tc_last_error());
+    CK(cudaEventRecord(h->ovl_ev[1], st));
+    CK(cudaStreamWaitEvent(side, h->ovl_ev[1], 0));
+    for (int xs = x0; xs < x0 + nl; xs += pl.nxc, ++gc) {
+      const int ns = (x0 + nl - xs) < pl.nxc ? (x0 + nl - xs) : pl.nxc;
+      const int set = gc & 1;
+      const double *Ms = M + (size_t)(xs - x0) * s.n_mu * s.nbl * s.nbp;
+      if (gc >= 2) CK(cudaStreamWaitEvent(side, h->ovl_gemm[set], 0));  // GEMM(gc - 2) used this set
+      if (int r = tc_triple_prep(s, Ms, om, p->x_w, xs, ns, pl.nxl, pl.nxc, tcs, set, side, prof))
+        return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
+      CK(cudaEventRecord(h->ovl_prep[set], side));
+      CK(cudaStreamWaitEvent(st, h->ovl_prep[set], 0));
+      if (int r = tc_triple_gemm(s, ns, pl.nxl, pl.nxc, G, gc > 0, tcs, set, wc, grid_sms, pl.tune, st, prof))
+        return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
+      CK(cudaEventRecord(h->ovl_gemm[set], st));
+    }
+    CK(cudaEventRecord(h->ovl_ev[2], side));
+  }
+  CK(cudaStreamWaitEvent(st, h->ovl_ev[2], 0));  // nothing of the side stream outlives the call
   return MODAL_OK;
 }
 
@@ -472,7 +568,8 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
   const bool fa = pl.prec == MODAL_PREC_TF32 || pl.prec == MODAL_PREC_BF16X3;
   const int fa_kind = pl.prec == MODAL_PREC_TF32 ? TC_FORM_TF32 : TC_FORM_BF16X3;
   void *tcs = (pl.prec == MODAL_PREC_OZAKI_BF16)
-                  ? bp.take<char>(tc_scratch_bytes(s, pl.nxl, pl.nxc, pl.variant))
+                  ? bp.take<char>(pl.overlap ? tc_ovl_scratch_bytes(s, pl.nxl, pl.nxc)
+                                             : tc_scratch_bytes(s, pl.nxl, pl.nxc, pl.variant))
                   : fa ? bp.take<char>(fa_scratch_bytes(s, pl.nxc)) : nullptr;
   double *mu = bp.take<double>(s.n_mu), *om = bp.take<double>(s.n_mu);
   double *A = bp.take<double>((size_t)s.n_mu * s.L);
@@ -541,6 +638,10 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
     } else {
       // tensor-core form: the l contraction over an l-chunk of nxl points,
       // then the triple product over its chunks of nxc points
+      if (pl.overlap && h && !capturing) {  // every chunk, Y pass beside the GEMM
+        if (int r = run_tc_overlap(h, num_sms, p, pl, tcs, (double *)M, om, A, G, st, first_in_call)) return r;
+        break;
+      }
       if (x0 % pl.nxl != 0) continue;
       Profiler *prof = (h && h->prof.on && !capturing) ? &h->prof : nullptr;
       if (c == 0) {
@@ -555,11 +656,11 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
         const int ns = (x0 + nl - xs) < pl.nxc ? (x0 + nl - xs) : pl.nxc;
         const double *Ms = (const double *)M + (size_t)(xs - x0) * s.n_mu * s.nbl * s.nbp;
         int r = tc_triple_chunk(s, Ms, om, p->x_w, xs, ns, pl.nxl, G, xs > 0, tcs, wc, num_sms, pl.variant,
-                                h ? h->opt_split_k : 0, st, prof);
+                                h ? h->opt_split_k : 0, st, prof, false, pl.tune);
         if (r) return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
         if (Gabs) {
           r = tc_triple_chunk(s, Ms, om, p->x_w, xs, ns, pl.nxl, Gabs, xs > 0, tcs, wc, num_sms, pl.variant,
-                              h ? h->opt_split_k : 0, st, prof, true);
+                              h ? h->opt_split_k : 0, st, prof, true, pl.tune);
           if (r) return fail(h, r, "tensor-core triple product (error scale) failed: %s", tc_last_error());
         }
       }
@@ -742,6 +843,53 @@ static int capture_batch(modal_handle *h, int n, const modal_problem *probs, con
   return MODAL_OK;
 }
 
+// The tile autotuner: times the triple GEMM's candidate shapes -- one CTA
+// per tile; the queue form with column tiles of at most 128 (K split, or
+// not) or 64 -- on one radial chunk of problem p (second of two runs each,
+// CUDA events on the call's stream, blocking) and keeps the fastest for p's
+// bucket.  gamma (p's output) receives scratch results.
+static int tune_tiles(modal_handle *h, const modal_problem *p, const modal_opts *o, double *gamma,
+                      cudaStream_t st) {
+  static const int cands[] = {0, 1 + 0, 1 + (8 | 16), 1 + 4};
+  modal_problem sub = *p;
+  SepPlan pl;
+  if (int r = plan_separable(h, &sub, o, pl, h->num_sms)) return r;
+  sub.n_x = pl.nxc < p->n_x ? pl.nxc : p->n_x;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_c = 0, rr = MODAL_OK;
+  for (int c : cands) {
+    SepPlan q;
+    if ((rr = plan_separable(h, &sub, o, q, h->num_sms)) != MODAL_OK) break;
+    q.variant = c == 0 ? TC_TRIPLE_MATERIALISED : TC_TRIPLE_QUEUE;
+    q.tune = c == 0 ? 0 : c - 1;
+    void *scr;
+    if ((rr = ws_get(h, 0, q.bytes, &scr)) != MODAL_OK) break;
+    if ((rr = run_separable(h, h->num_sms, &sub, q, gamma, st, scr)) != MODAL_OK) break;
+    cudaError_t ce = cudaEventRecord(e0, st);
+    if (ce == cudaSuccess && (rr = run_separable(h, h->num_sms, &sub, q, gamma, st, scr)) != MODAL_OK) break;
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce != cudaSuccess) {
+      rr = fail(h, MODAL_ECUDA, "timing the tile shapes: %s", cudaGetErrorString(ce));
+      break;
+    }
+    if (ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rr != MODAL_OK) return rr;
+  h->tile_choice[tile_bucket(p)] = best_c;
+  return MODAL_OK;
+}
+
 int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_problem *probs,
                                     const modal_opts *o, double *const *gammas, modal_stream_t stream) {
   if (int r = check_handle(h)) return r;
@@ -760,6 +908,23 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
       return fail(h, MODAL_EINVAL, "null gamma for problem %d", i);
     any_tc = any_tc || plans[i].prec == MODAL_PREC_OZAKI_BF16 || plans[i].prec == MODAL_PREC_TF32 ||
              plans[i].prec == MODAL_PREC_BF16X3;  // their status word heads each stream's scratch
+  }
+  // tile shapes: time the buckets that have no choice yet, then plan with the choices
+  if (h->opt_autotune) {
+    bool tuned = false;
+    for (int i = 0; i < n; ++i) {
+      const modal_problem &pp = probs[i];
+      if (plans[i].prec != MODAL_PREC_OZAKI_BF16) continue;
+      if (plans[i].variant != TC_TRIPLE_MATERIALISED && plans[i].variant != TC_TRIPLE_QUEUE) continue;
+      if ((int64_t)pp.n_late * pp.n_prim == 0 || pp.n_x == 0) continue;
+      if (h->tile_choice.count(tile_bucket(&pp))) continue;
+      if (int r = tune_tiles(h, &pp, o, gammas[i], st)) return fail(h, r, "tile autotuner, problem %d: %s", i,
+                                                                    h->err.c_str());
+      tuned = true;
+    }
+    if (tuned)
+      for (int i = 0; i < n; ++i)
+        if (int r = plan_separable(h, &probs[i], o, plans[i], h->num_sms)) return r;
   }
   // stream counts to consider: the fixed option, or 1, 2, 4, 8 (at most n)
   // while their scratch fits in half of the free device memory
@@ -792,6 +957,10 @@ int modal_project_separable_batched(modal_handle *h, int32_t n, const modal_prob
   key = fnv1a(key, &h->opt_split_k, sizeof(int));
   key = fnv1a(key, &h->opt_pair, sizeof(int));
   key = fnv1a(key, &h->opt_queue, sizeof(int));
+  for (int i = 0; i < n; ++i) {  // the tile shapes chosen per problem
+    key = fnv1a(key, &plans[i].variant, sizeof(int));
+    key = fnv1a(key, &plans[i].tune, sizeof(int));
+  }
   key = fnv1a(key, &h->opt_batch_streams, sizeof(int));
   key = fnv1a(key, &h->wait_cycles, sizeof(long long));
   auto it = h->graphs.find(key);

@@ -250,6 +250,11 @@ __host__ __device__ inline int g_tile_width(int64_t cols) {
   const int64_t nct = cdiv64(cols, OZ_BN);
   return (int)(cdiv64(cdiv64(cols, nct), 16) * 16);
 }
+// the same with column tiles of at most `cap` (a multiple of 16, <= OZ_BN)
+__host__ __device__ inline int g_tile_width_cap(int64_t cols, int cap) {
+  const int64_t nct = cdiv64(cols, cap);
+  return (int)(cdiv64(cdiv64(cols, nct), 16) * 16);
+}
 
 // Tensor maps of the B operand with boxes of 16, 32, ..., 128 rows: a tile of
 // MMA width N loads only its N rows of B (slices then lie N * 64 bytes apart).
@@ -817,6 +822,7 @@ constexpr int Q_ITEMS_MAX = 4096;  // items of the in-parameter queue table
 constexpr int Q_RING = 4;          // item slots between the producer and the consumers
 struct QueueParams {
   OzParams o;
+  int wmax;          // column tiles of at most wmax (a multiple of 16, <= OZ_BN)
   int n_items;       // items in the queue
   int nkr;           // K ranges per tile (1: tiles are not split)
   int chunks_per_kr; // exact K chunks per range (the last range may be shorter)
@@ -824,11 +830,12 @@ struct QueueParams {
   uint32_t item[Q_ITEMS_MAX];  // tile << 8 | K range, in the order of taking
 };
 
-// tile t of the triple product's block structure (tiles of 128 rows x w columns)
-__device__ __forceinline__ void q_tile(const GLayout &g, int t, int &bblk, int &rt, int &ct, int64_t &rowoff) {
+// tile t of the triple product's block structure (tiles of 128 rows x w columns, w <= wmax)
+__device__ __forceinline__ void q_tile(const GLayout &g, int wmax, int t, int &bblk, int &rt, int &ct,
+                                       int64_t &rowoff) {
   rowoff = 0;
   for (bblk = 0; bblk < g.nbl; ++bblk) {
-    const int nrt = (int)cdiv64(g.rows(bblk), OZ_BM), nct = (int)cdiv64(g.cols(bblk), OZ_BN);
+    const int nrt = (int)cdiv64(g.rows(bblk), OZ_BM), nct = (int)cdiv64(g.cols(bblk), wmax);
     if (t < nrt * nct) {
       rt = t / nct;
       ct = t % nct;
@@ -850,8 +857,8 @@ __device__ __forceinline__ QItem q_decode(const QueueParams &Q, uint32_t code) {
   const int t = (int)(code >> 8), kr = (int)(code & 0xffu);
   int bblk, rt, ct;
   int64_t rowoff;
-  q_tile(Q.o.g, t, bblk, rt, ct, rowoff);
-  it.ntile = g_tile_width(Q.o.g.cols(bblk));
+  q_tile(Q.o.g, Q.wmax, t, bblk, rt, ct, rowoff);
+  it.ntile = g_tile_width_cap(Q.o.g.cols(bblk), Q.wmax);
   it.a_row0 = rowoff + (int64_t)rt * OZ_BM;
   it.b_row0 = (int64_t)bblk * Q.o.g.nbp + (int64_t)ct * it.ntile;
   it.R = min((int64_t)OZ_BM, Q.o.g.rows(bblk) - (int64_t)rt * OZ_BM);
@@ -968,8 +975,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         ptx::mbar_arrive(&item_empty[slot]);
         if (code < 0) break;
         const QItem it = q_decode(Q, (uint32_t)code);
+        // the width's schedule in registers (the issue loop is this thread's critical path)
         const uint32_t *plan = P.plan[it.ntile / 16 - 1];
         const int nruns = (int)(plan[0] & 0xffu);
+        uint32_t run[OZ_PLAN_MAX];
+#pragma unroll
+        for (int r = 0; r < OZ_PLAN_MAX; ++r) run[r] = plan[1 + r];
         const int i0 = it.c0 * steps_per_chunk, i1 = min(ksteps, it.c1 * steps_per_chunk);
         bool stop = false;
         for (int i = i0; i < i1; ++i, ++g) {
@@ -994,7 +1005,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
             for (int r = 0; r < OZ_PLAN_MAX; ++r) {
               if (r >= nruns) break;
-              const uint32_t e = plan[1 + r];
+              const uint32_t e = run[r];
               const uint32_t sa = e & 15u, sb = (e >> 4) & 15u, n = (e >> 8) & 15u, acc = (e >> 12) & 15u;
               const bool first = chunk_start && kk == 0 && ((e >> 16) & 1u);
               const uint32_t N = n * (uint32_t)it.ntile;
@@ -2325,7 +2336,7 @@ static double plan_step_cost(const uint32_t (&plan)[1 + OZ_PLAN_MAX], int w) {
 // them to give every SM two; grid = min(items, SMs).  Returns MODAL_EUNSUPPORTED
 // (the caller falls back to one CTA per tile) beyond the queue table's size.
 static int launch_queue_gemm(OzParams &P, const CUtensorMap &ta, const BMaps &tb, int nbl, int num_sms,
-                             int *head, cudaStream_t st, Profiler *prof) {
+                             int wmax, bool split, int *head, cudaStream_t st, Profiler *prof) {
   static QueueParams Q;  // host staging of the (large) parameter block
   static std::mutex qm;
   std::lock_guard<std::mutex> lock(qm);
@@ -2336,15 +2347,16 @@ static int launch_queue_gemm(OzParams &P, const CUtensorMap &ta, const BMaps &tb
     uint32_t code;
   };
   std::vector<It> tiles;
+  Q.wmax = wmax;
   for (int b = 0, t = 0; b < nbl; ++b) {
-    const int w = g_tile_width(P.g.cols(b));
+    const int w = g_tile_width_cap(P.g.cols(b), wmax);
     const double c = plan_step_cost(Q.o.plan[w / 16 - 1], w);
-    const int n = (int)(cdiv64(P.g.rows(b), OZ_BM) * cdiv64(P.g.cols(b), OZ_BN));
+    const int n = (int)(cdiv64(P.g.rows(b), OZ_BM) * cdiv64(P.g.cols(b), wmax));
     for (int i = 0; i < n; ++i, ++t) tiles.push_back({c, (uint32_t)t});
   }
   const int ntiles = (int)tiles.size();
   int nkr = 1;
-  if (ntiles < 2 * num_sms) nkr = (int)cdiv64(2 * num_sms, ntiles);
+  if (split && ntiles < 2 * num_sms) nkr = (int)cdiv64(2 * num_sms, ntiles);
   if (nkr > P.nchunks) nkr = P.nchunks;
   if (nkr > 255) nkr = 255;
   if (nkr < 1) nkr = 1;
@@ -2382,7 +2394,7 @@ static int launch_queue_gemm(OzParams &P, const CUtensorMap &ta, const BMaps &tb
 
 int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
                     int nxl_max, double *G, bool accumulate, void *scratch, long long wait_cycles, int num_sms,
-                    int variant, int split_k, cudaStream_t st, Profiler *prof, bool absM) {
+                    int variant, int split_k, cudaStream_t st, Profiler *prof, bool absM, int tune) {
   LScratch ls = l_scratch(scratch, s, nxl_max);
   char *w = ls.end;
   int *words = ls.words;
@@ -2495,7 +2507,13 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     P.g = make_glayout(s.nbl, s.nbp);
     P.wait_cycles = wait_cycles;
     if (variant == TC_TRIPLE_QUEUE) {
-      const int r = launch_queue_gemm(P, ta, tb, s.nbl, num_sms, words + 16, st, prof);
+      const int wmax = tune_wmax(tune);
+      if (wmax != OZ_BN) {  // B maps for the capped widths
+        unsigned used2 = 0;
+        for (int b = 0; b < s.nbl; ++b) used2 |= 1u << (g_tile_width_cap(P.g.cols(b), wmax) / 16 - 1);
+        if (int r = make_bmaps(&tb, Bt, nblp, Kpad, used2)) return r;
+      }
+      const int r = launch_queue_gemm(P, ta, tb, s.nbl, num_sms, wmax, tune_split(tune), words + 16, st, prof);
       if (r != MODAL_EUNSUPPORTED) return r;  // else (more items than the table holds): one CTA per tile
     }
     if (variant == TC_TRIPLE_PAIR) {
@@ -2563,6 +2581,159 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
 cuda_fail:
   snprintf(g_tc_err, sizeof g_tc_err, "triple product: %s", cudaGetErrorString(e));
   return MODAL_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// The Y-through-HBM triple product in two phases on two streams, so that the
+// Y pass of one radial chunk runs beside the GEMM of the previous one.  Two
+// scratch sets alternate between chunks; each set has its own exponent
+// maxima and queue counter (the l contraction's words are not touched):
+//   set words: [0] max B exponent, [1] max Y exponent, [2] bound of max |M~|,
+//   [3] queue counter.
+// ---------------------------------------------------------------------------
+constexpr int SET_WORDS_BYTES = 256;
+
+static size_t set_bytes(const SepShape &s, int nxc_max) {
+  return SET_WORDS_BYTES + tc_triple_scratch_bytes(s, nxc_max, TC_TRIPLE_MATERIALISED);
+}
+
+size_t tc_ovl_scratch_bytes(const SepShape &s, int nxl, int nxc) {
+  LScratch r = l_scratch(nullptr, s, nxl);
+  return (size_t)(r.end - (char *)nullptr) + 2 * set_bytes(s, nxc) + 1024;
+}
+
+__global__ void k_init_set_words(int *w) {
+  if (threadIdx.x < 3) w[threadIdx.x] = -100000;
+  else if (threadIdx.x == 3) w[3] = 0;
+}
+
+struct SetScratch {
+  int *sw;
+  f2 *Mdf;
+  unsigned *colmax;
+  double *mxW;
+  int *eB, *eY;
+  __nv_bfloat16 *Bt, *Ysl;
+};
+static SetScratch set_scratch(void *scratch, const SepShape &s, int nxl_max, int nxc_max, int set, int nxc) {
+  LScratch ls = l_scratch(scratch, s, nxl_max);
+  char *w = ls.end + (size_t)set * set_bytes(s, nxc_max);
+  const int64_t K = (int64_t)nxc * s.n_mu;
+  const int Kpad = (int)(cdiv64(K, 64) * 64);
+  const int nblp = s.nbl * s.nbp;
+  const int nch = (int)cdiv64(K, OZ_KC);
+  SetScratch r;
+  r.sw = (int *)w; w += SET_WORDS_BYTES;
+  r.Mdf = (f2 *)w; w += up256((size_t)Kpad * nblp * 8);
+  r.colmax = (unsigned *)w; w += up256((size_t)nch * nblp * 8);
+  r.mxW = (double *)w; w += up256((size_t)nch * nblp * 8);
+  r.eB = (int *)w; w += up256((size_t)nch * nblp * 4);
+  r.Bt = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * nblp * Kpad * 2);
+  r.eY = (int *)w; w += up256((size_t)nch * y_rows(s) * 4);
+  r.Ysl = (__nv_bfloat16 *)w;
+  return r;
+}
+
+int tc_triple_prep(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
+                   int nxl_max, int nxc_max, void *scratch, int set, cudaStream_t st, Profiler *prof) {
+  LScratch ls = l_scratch(scratch, s, nxl_max);
+  SetScratch r = set_scratch(scratch, s, nxl_max, nxc_max, set, nxc);
+  const int64_t K = (int64_t)nxc * s.n_mu;
+  const int Kpad = (int)(cdiv64(K, 64) * 64);
+  const int nblp = s.nbl * s.nbp;
+  const int nch = (int)cdiv64(K, OZ_KC);
+  const int P2 = s.nbp * (s.nbp + 1) / 2;
+  const int64_t rowsY = y_rows(s);
+  cudaError_t e;
+  {
+    ProfScope ps(prof, "tc_prep_M", st, 3);
+    k_init_set_words<<<1, 32, 0, st>>>(r.sw);
+    if ((e = cudaMemsetAsync(r.colmax, 0, (size_t)nch * nblp * 8, st)) != cudaSuccess) goto cuda_fail;
+    k_tp_col_max<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)cdiv64(K, 128)), 256, 0, st>>>(
+        K, nblp, s.n_mu, x0, M, om, xw, r.colmax);
+    k_tp_split_cols<<<dim3((unsigned)cdiv(nblp, TP_COLS), (unsigned)(Kpad / 32)), 256, 0, st>>>(
+        K, Kpad, nblp, s.n_mu, x0, M, om, xw, r.colmax, r.Mdf, r.mxW, r.eB, r.Bt, r.sw, ls.words, 0);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  {
+    ProfScope ps(prof, "tc_make_Y", st, 2);
+    k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(rowsY, s.nbp, nblp, P2, r.mxW,
+                                                                                r.eY, r.sw + 1);
+    const size_t smy = ty_smem_bytes(s.nbp);
+    if ((e = cudaFuncSetAttribute(k_tp_make_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) !=
+        cudaSuccess)
+      goto cuda_fail;
+    const int npairs = s.nbl * (s.nbl + 1) / 2;
+    k_tp_make_y<<<dim3((unsigned)npairs, (unsigned)cdiv64(Kpad, TY_K)), 32 * TY_WARPS, smy, st>>>(
+        rowsY, K, Kpad, s.nbp, nblp, P2, r.Mdf, r.eY, r.Ysl);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  return MODAL_OK;
+cuda_fail:
+  snprintf(g_tc_err, sizeof g_tc_err, "triple product (operands): %s", cudaGetErrorString(e));
+  return MODAL_ECUDA;
+}
+
+int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double *G, bool accumulate,
+                   void *scratch, int set, long long wait_cycles, int grid_sms, int tune, cudaStream_t st,
+                   Profiler *prof) {
+  LScratch ls = l_scratch(scratch, s, nxl_max);
+  SetScratch r = set_scratch(scratch, s, nxl_max, nxc_max, set, nxc);
+  const int64_t K = (int64_t)nxc * s.n_mu;
+  const int Kpad = (int)(cdiv64(K, 64) * 64);
+  const int nblp = s.nbl * s.nbp;
+  const int nch = (int)cdiv64(K, OZ_KC);
+  const int64_t rowsY = y_rows(s);
+  cudaError_t e;
+  if (!accumulate) {
+    ProfScope ps(prof, "zero_G", st);
+    GLayout g = make_glayout(s.nbl, s.nbp);
+    if ((e = launch_zero(G, (size_t)g.size(), st)) != cudaSuccess) {
+      snprintf(g_tc_err, sizeof g_tc_err, "triple product: %s", cudaGetErrorString(e));
+      return MODAL_ECUDA;
+    }
+  }
+  CUtensorMap ta;
+  BMaps tb;
+  const GLayout gl = make_glayout(s.nbl, s.nbp);
+  const int wmax = tune_wmax(tune);
+  unsigned used = 0;
+  for (int b = 0; b < s.nbl; ++b) used |= 1u << (g_tile_width_cap(gl.cols(b), wmax) / 16 - 1);
+  if (int rr = make_slices_map(&ta, r.Ysl, rowsY, Kpad, OZ_BM)) return rr;
+  if (int rr = make_bmaps(&tb, r.Bt, nblp, Kpad, used)) return rr;
+  OzParams P{};
+  P.rowsA = rowsY;
+  P.rowsB = nblp;
+  P.Kpad = Kpad;
+  P.nchunks = nch;
+  P.eA = r.eY;
+  P.eB = r.eB;
+  P.emaxA = r.sw + 1;
+  P.emaxB = r.sw;
+  P.out = G;
+  P.err = ls.words;
+  P.g = gl;
+  P.wait_cycles = wait_cycles;
+  const int rq = launch_queue_gemm(P, ta, tb, s.nbl, grid_sms, wmax, tune_split(tune), r.sw + 3, st, prof);
+  if (rq != MODAL_EUNSUPPORTED) return rq;
+  // more items than the queue table holds: one CTA per tile
+  unsigned used1 = 0;
+  for (int b = 0; b < s.nbl; ++b) used1 |= 1u << (g_tile_width(gl.cols(b)) / 16 - 1);
+  if (int rr = make_bmaps(&tb, r.Bt, nblp, Kpad, used1)) return rr;
+  fill_mma_plans(P.plan);
+  int64_t tiles = 0;
+  for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(gl.rows(b), OZ_BM) * cdiv64(gl.cols(b), OZ_BN);
+  if ((e = cudaFuncSetAttribute(k_ozaki_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) ==
+      cudaSuccess) {
+    ProfScope ps(prof, "tc_gemm_triple", st);
+    k_ozaki_gemm<1><<<(unsigned)tiles, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    snprintf(g_tc_err, sizeof g_tc_err, "triple product: %s", cudaGetErrorString(e));
+    return MODAL_ECUDA;
+  }
+  return MODAL_OK;
 }
 
 int *tc_error_word(void *scratch) { return (int *)scratch; }

@@ -27,9 +27,25 @@ int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_
                   long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
 // Triple product of one radial chunk [x0, x0 + nxc) whose M (FP64,
 // [xl][j][a][p]) starts at M: G (+)= sum over its slices.
+// Tile shape of the queue form (TC_TRIPLE_QUEUE): column tiles of at most
+// wmax and K ranges split to give every SM two items (split) or not.
+// tune = 0: wmax 128, split; else bits 0-3 = wmax / 16, bit 4 = no split.
+inline int tune_wmax(int tune) { return tune ? 16 * (tune & 15) : 128; }
+inline bool tune_split(int tune) { return !(tune & 16); }
 int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
                     int nxl_max, double *G, bool accumulate, void *scratch, long long wait_cycles, int num_sms,
-                    int variant, int split_k, cudaStream_t st, Profiler *prof = nullptr, bool absM = false);
+                    int variant, int split_k, cudaStream_t st, Profiler *prof = nullptr, bool absM = false,
+                    int tune = 0);
+// The triple product of one radial chunk in two phases (operands incl. the Y
+// slices; the persistent queue GEMM on at most grid_sms SMs) with two
+// alternating scratch sets, so that the phases of neighbouring chunks can
+// run on two streams at once.  Scratch: tc_ovl_scratch_bytes.
+size_t tc_ovl_scratch_bytes(const SepShape &s, int nxl, int nxc);
+int tc_triple_prep(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
+                   int nxl_max, int nxc_max, void *scratch, int set, cudaStream_t st, Profiler *prof = nullptr);
+int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double *G, bool accumulate,
+                   void *scratch, int set, long long wait_cycles, int grid_sms, int tune, cudaStream_t st,
+                   Profiler *prof = nullptr);
 // device status word of the tensor-core scratch (bit 0: a bounded wait gave up,
 // bit 1: a value outside the FP32 exponent range of the split operands)
 int *tc_error_word(void *scratch);

@@ -85,6 +85,7 @@ def test_queue_batched(mg):
     probs = [syn.make_problem(40, 12, 4, seed=71, nb_prim=12), syn.make_problem(90, 5, 6, seed=72),
              syn.make_problem(30, 16, 3, seed=73, nb_prim=9), syn.make_problem(150, 3, 5, seed=74)]
     h = queue_handle(mg)
+    mg.set_option(mg.OPT_TC_AUTOTUNE, 0, handle=h)    # keep the queue form for every problem
     dps = [mg.DeviceProblem.from_host(P, handle=h) for P in probs]
     gs = mg.project_separable_batched(dps, precision=mg.PREC_OZAKI_BF16, handle=h)
     mg.handle_status(handle=h)
@@ -108,4 +109,67 @@ def test_queue_planck_sampled(mg):
     g0 = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, handle=h).cpu().numpy()
     mg.handle_status(handle=h)
     assert normwise(g, g0) < 1e-12
+    h.close()
+
+
+def test_batched_tile_autotuner(mg):
+    """The first batched call times the triple GEMM's tile shapes per bucket
+    (MODAL_OPT_TC_AUTOTUNE, on by default) and keeps the fastest: results
+    against the oracle; a replay, and single-problem calls that reuse the
+    buckets' choices, give the same Gamma' to the FP64 sums' rounding."""
+    probs = [syn.make_problem(40, 12, 4, seed=81, nb_prim=12), syn.make_problem(260, 5, 6, seed=82),
+             syn.make_problem(45, 12, 3, seed=83, nb_prim=12)]       # the first and last share a bucket
+    h = mg.Handle()
+    dps = [mg.DeviceProblem.from_host(P, handle=h) for P in probs]
+    gs = [g.clone() for g in mg.project_separable_batched(dps, precision=mg.PREC_OZAKI_BF16, handle=h)]
+    mg.handle_status(handle=h)
+    for P, g in zip(probs, gs):
+        assert normwise(g, oracle.separable(P)) < TOL_MIXED
+    gs2 = mg.project_separable_batched(dps, precision=mg.PREC_OZAKI_BF16, handle=h)
+    mg.handle_status(handle=h)
+    for g, g2 in zip(gs, gs2):
+        assert normwise(g2, g.cpu().numpy()) < 1e-12
+    for dp, g in zip(dps, gs):
+        single = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, handle=h)
+        mg.handle_status(handle=h)
+        assert normwise(single, g.cpu().numpy()) < 1e-12
+    h.close()
+
+
+@pytest.mark.parametrize("shape,x_chunk", [((48, 5, 5, 24), 3), ((40, 4, 4, 70), 5), ((37, 21, 21, 3), 1),
+                                           ((300, 10, 10, 6), 0)])
+def test_overlap_separable(mg, shape, x_chunk):
+    """The Y pass of each radial chunk on a second stream beside the previous
+    chunk's queue GEMM (MODAL_OPT_TC_OVERLAP): several l-chunks and chunks,
+    alternating scratch sets, against the oracle and the plain form."""
+    lmax, nbl, nbp, nx = shape
+    P = syn.make_problem(lmax, nbl, nx, seed=91, nb_prim=nbp)
+    h = mg.Handle()
+    mg.set_option(mg.OPT_TC_OVERLAP, 24, handle=h)
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    g = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, x_chunk=x_chunk, handle=h)
+    mg.handle_status(handle=h)
+    assert normwise(g, oracle.separable(P)) < TOL_MIXED
+    mg.set_option(mg.OPT_TC_OVERLAP, 0, handle=h)
+    g0 = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, x_chunk=x_chunk, handle=h).cpu().numpy()
+    mg.handle_status(handle=h)
+    assert normwise(g, g0) < 1e-12
+    h.close()
+
+
+def test_overlap_planck(mg):
+    P = syn.planck_size()
+    h = mg.Handle()
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    g0 = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, handle=h).cpu().numpy()
+    mg.handle_status(handle=h)
+    mg.set_option(mg.OPT_TC_OVERLAP, 32, handle=h)
+    g = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, handle=h)
+    mg.handle_status(handle=h)
+    assert normwise(g, g0) < 1e-12
+    late_pick = np.array([i for i, m in enumerate(P.late_modes) if set(m) <= {2, 9, 16}])
+    prim_pick = np.array([i for i, m in enumerate(P.prim_modes) if set(m) <= {4, 13, 18}])
+    ref = oracle.separable(P, late=P.late_modes[late_pick], prim=P.prim_modes[prim_pick])
+    got = g.cpu().numpy()[np.ix_(late_pick, prim_pick)]
+    assert np.abs(got - ref).max() / np.abs(ref).max() < TOL_MIXED
     h.close()
