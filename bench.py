@@ -592,7 +592,7 @@ def run_extra(args):
         dp = mg.DeviceProblem.from_host(P, device=dev, handle=h)
         gbar = torch.tensor(syn.random_cotangent(P.n_late, P.n_prim, seed=4), device=dev)
         slices = P.slices
-        bprec = PREC["fp32"] if prec_name == "ozaki" else prec
+        bprec = prec          # the adjoint in the same form (tensor-core adjoint for ozaki)
 
         def step():
             mg.project_separable(dp, precision=prec, handle=h)
@@ -664,6 +664,21 @@ def run_extra(args):
     ms = e0.elapsed_time(e1) / args.steps
     if args.workload == "batched":
         cfg["fp64_sequential"] = fp64_sequential(probs, dps, slices / (ms * 1e-3), dev, h)
+    if args.workload == "grad":             # forward alone, and the error of the adjoint vs FP64
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        for _ in range(args.steps):
+            mg.project_separable(dp, precision=prec, handle=h)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        cfg["forward_ms"] = e0.elapsed_time(e1) / args.steps
+        cfg["adjoint_ms"] = ms - cfg["forward_ms"]
+        dqt, dq = mg.project_backward(dp, gbar, precision=bprec, handle=h)
+        if bprec == PREC["ozaki"]:
+            mg.handle_status(handle=h)
+        dqt64, dq64 = mg.project_backward(dp, gbar, handle=h)
+        nw = lambda a, b: float((a - b).abs().max() / b.abs().max())
+        cfg["adjoint_error_vs_fp64"] = {"dqt_normwise": nw(dqt, dqt64), "dq_normwise": nw(dq, dq64)}
     if args.workload == "full":
         cfg["parts_ms"] = {}
         for name, f in parts.items():

@@ -249,8 +249,15 @@ int modal_project_direct(modal_handle *h, const modal_problem *prob, const int32
  * Eq. 2D and Eq. legendre): given dL_dgamma = dL/dGamma' (device
  * [n_late][n_prim]) writes dL/dq~ (device [n_x][nb_prim][L], overwritten)
  * and, if dL_dq is not NULL, dL/dq (device [nb_late][L], overwritten).
- * M slices are recomputed, not stored.  opts as for the forward call
- * (MODAL_PREC_OZAKI_BF16 is served by the FP32 adjoint). */
+ * M slices are recomputed, not stored.  opts as for the forward call:
+ * MODAL_PREC_FP64 and MODAL_PREC_FP32 run on CUDA cores;
+ * MODAL_PREC_OZAKI_BF16 runs the three contractions on tcgen05 with the
+ * forward's exact slicing -- dL/dM as one GEMM per radial chunk over the
+ * 2 x 2 minors of the permanent (dL/dM_xy = sum over the minors' rows
+ * (a <= b, {u, v}) of Gfull[row][(x, y)] w (M_au M_bv + M_av M_bu), Gfull
+ * collecting dL/dGamma' / (48 pi) over the nine positions of (x, y) in each
+ * mode pair), then dL/dq~ and dL/dq -- and reports device-side status
+ * through modal_handle_status; TF32 and BF16X3 use the FP32 adjoint. */
 int modal_project_backward(modal_handle *h, const modal_problem *prob, const modal_opts *opts,
                            const double *dL_dgamma, double *dL_dqt, double *dL_dq,
                            modal_stream_t stream);

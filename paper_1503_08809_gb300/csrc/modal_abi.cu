@@ -692,7 +692,8 @@ int modal_workspace_size(const modal_problem *p, const modal_opts *o, int for_ba
   if (int r = plan_separable(nullptr, p, o, pl, sms)) return r;
   size_t b = pl.bytes;
   if (for_backward) {
-    size_t bb = backward_scratch_bytes(pl.s, pl.nxc, pl.prec);
+    size_t bb = pl.prec == MODAL_PREC_OZAKI_BF16 ? tc_backward_scratch_bytes(pl.s, tc_backward_nxc(pl.s))
+                                                 : backward_scratch_bytes(pl.s, pl.nxc, pl.prec);
     b = bb > b ? bb : b;
   }
   *bytes = b;
@@ -1241,11 +1242,27 @@ int modal_project_backward(modal_handle *h, const modal_problem *p, const modal_
   if (!dL_dgamma || !dL_dqt) return fail(h, MODAL_EINVAL, "null dL_dgamma or dL_dqt");
   SepPlan pl;
   if (int r = plan_separable(h, p, o, pl, h->num_sms)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (pl.prec == MODAL_PREC_OZAKI_BF16) {  // the adjoint's three contractions on the tensor cores
+    int nxc = tc_backward_nxc(pl.s);
+    if (o && o->x_chunk > 0 && o->x_chunk < nxc) nxc = o->x_chunk;  // a smaller chunk on request
+    void *scratch;
+    if (int r = ws_get(h, 0, tc_backward_scratch_bytes(pl.s, nxc), &scratch)) return r;
+    Profiler *prof = h->prof.on ? &h->prof : nullptr;
+    if (int r = tc_backward(pl.s, nxc, p, dL_dgamma, dL_dqt, dL_dq, scratch, h->wait_cycles, st, prof))
+      return fail(h, r, "tensor-core adjoint failed: %s", tc_last_error());
+    if (pl.s.n_x > 0 && (int64_t)p->n_late * p->n_prim > 0) {
+      CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(scratch), sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaEventRecord(h->err_event, st));
+      h->n_err_words = 1;
+      h->err_pending = true;
+    }
+    return MODAL_OK;
+  }
   size_t bytes = backward_scratch_bytes(pl.s, pl.nxc, pl.prec);
   void *scratch;
   if (int r = ws_get(h, 0, bytes, &scratch)) return r;
-  int r = run_backward(pl.s, pl.nxc, pl.prec, p, dL_dgamma, dL_dqt, dL_dq, scratch, h->num_sms,
-                       (cudaStream_t)stream);
+  int r = run_backward(pl.s, pl.nxc, pl.prec, p, dL_dgamma, dL_dqt, dL_dq, scratch, h->num_sms, st);
   if (r) return fail(h, r, "adjoint failed: %s", backward_last_error());
   return MODAL_OK;
 }

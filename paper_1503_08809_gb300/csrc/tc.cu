@@ -240,6 +240,9 @@ struct OzParams {
   // OUT_MODE 1
   GLayout g;
   long long wait_cycles;
+  // OUT_MODE 2: dense C[r][c] at out[r * ld_r + c * ld_c], stored or added
+  int64_t ld_r, ld_c;
+  int out_accumulate;
 };
 
 
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   int ntile = OZ_BN;  // MMA N of this tile (a multiple of 16)
   int ntt = 1;  // tiles of this CTA (OUT_MODE 0: row tiles of one column tile)
   bool lead = true;  // the first column tile of its row tile: it prefetches A
-  if (OUT_MODE == 0) {
+  if (OUT_MODE != 1) {
     // column tiles vary fastest, so the CTAs that share a row tile of A run
     // together and A is read from HBM about once; each CTA then moves on to
     // the next row tile, so its set-up, pipeline fill and last drain are
@@ -454,7 +457,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     bool ok = true;
     for (int tt = 0; tt < ntt && ok; ++tt) {
     const int64_t ar0 = a_row0 + (int64_t)tt * OZ_BM;  // this tile's first row of A
-    const int64_t Rt = OUT_MODE == 0 ? min((int64_t)OZ_BM, P.rowsA - ar0) : R;
+    const int64_t Rt = OUT_MODE != 1 ? min((int64_t)OZ_BM, P.rowsA - ar0) : R;
 #pragma unroll
     for (int c = 0; c < 64; ++c) {
       hi[c] = 0.f;
@@ -529,6 +532,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const double v = f32_scaled_f64(hi[c], ebias) + f32_scaled_f64(lo_s[(col0 + c) * OZ_BM + row], ebias);
           if (OUT_MODE == 0) {
             P.out[xl * mx + mrow + p] = v;
+          } else if (OUT_MODE == 2) {
+            double *d = P.out + (ar0 + row) * P.ld_r + (b_row0 + col) * P.ld_c;
+            *d = P.out_accumulate ? *d + v : v;
           } else {
             double *d = P.out + out_base + (int64_t)row * P.g.cols(bblk) + col;
             *d += v;
@@ -2583,6 +2589,165 @@ cuda_fail:
   return MODAL_ECUDA;
 }
 
+// ===========================================================================
+// The adjoint (row a9) on the tensor cores.
+//
+// dL/dM through the permanent of Eq. 2D: the derivative of perm(M[L; C])
+// with respect to the entry (x, y) is the sum, over the positions i of x in
+// the late triple L and j of y in the primordial triple C, of the permanent
+// of the 2 x 2 minor left when row i and column j are struck out.  So
+//   dL/dM_{xy}(s) = sum_rows Gfull[row][(x, y)] Y_row(s),
+//   Y_row(s) = w_s (M_{a u} M_{b v} + M_{a v} M_{b u}),  row = (a <= b, {u, v}),
+// where Gfull collects gbar / (48 pi) over every (n, n') and all nine
+// (i, j): one GEMM over the Y rows per radial chunk (every row pairs with
+// every (x, y), unlike the forward's b <= c blocks).  Then
+//   T[(x, a, p)][l] = sum_j dM_{ap}(x, j) w_l P_l(mu_j)      (a second GEMM),
+//   dL/dq~_p(l, x) = sum_a q_a(l) T[(x, a, p)][l],
+//   dL/dq_a(l)     = sum_{x,p} q~_p(l, x) T[(x, a, p)][l]      (FP64 sums).
+// Both GEMMs run as A B^T on the exact-slicing GEMM kernel (dense output),
+// operands split into five exponent-aligned BF16 slices.
+// ===========================================================================
+
+// Operand rows for the slicing: value (r, k) as FP64 of a [rows][K] operand.
+struct OpGfullT {  // rows (x, y) over nblp, K = Y rows: Gfull^T stored [nblp][rowsY]
+  const double *g;
+  int64_t rowsY;
+  __device__ double val(int64_t r, int64_t k) const { return g[r * rowsY + k]; }
+};
+struct OpAt {  // rows l, K = j: the weighted Legendre table A[j][l] = w_l P_l(mu_j)
+  const double *A;
+  int L;
+  __device__ double val(int64_t r, int64_t k) const { return A[k * L + r]; }
+};
+struct OpDmT {  // rows (xl, a, p), K = j: dM[(xl n_mu + j) nblp + (a nbp + p)]
+  const double *dM;
+  int n_mu, nblp;
+  __device__ double val(int64_t r, int64_t k) const {
+    const int64_t xl = r / nblp, ap = r % nblp;
+    return dM[(xl * n_mu + k) * nblp + ap];
+  }
+};
+
+// One warp per (row, K chunk of OZ_KC): the chunk's max |x| (FP32-rounded),
+// then the five BF16 slices with that exponent; out [5][rows][Kpad], ex
+// [chunks][rows], emax = max exponent.  Zero for k in [K, Kpad).
+template <class Op>
+__global__ void k_split_op(int64_t rows, int64_t K, int Kpad, Op op, __nv_bfloat16 *__restrict__ out,
+                           int *__restrict__ ex, int *__restrict__ emax, int *__restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nch = (int)cdiv64(Kpad, OZ_KC);
+  if (w >= rows * nch) return;
+  const int64_t r = w / nch;
+  const int ch = (int)(w % nch);
+  const int64_t k0 = (int64_t)ch * OZ_KC, k1 = min(K, k0 + OZ_KC);
+  float m = 0.f;
+  for (int64_t k = k0 + lane; k < k1; k += 32) m = fmaxf(m, fabsf(__double2float_rn(op.val(r, k))));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (!(m < 1e37f)) {
+    if (lane == 0) atomicOr(err, ERR_RANGE);
+    m = 0.f;
+  }
+  const int e = exp_bound_f(m);
+  const int64_t sstride = rows * (int64_t)Kpad;
+  const int64_t kend = min((int64_t)Kpad, k0 + OZ_KC);
+  for (int64_t k = k0 + lane; k < kend; k += 32) {
+    const double v = k < K ? op.val(r, k) : 0.0;
+    const f2 vd = df_from_d_fast(v);
+    __nv_bfloat16 o[OZ_SLICES];
+    split_f2(vd.h, vd.l, e, o);
+#pragma unroll
+    for (int sl = 0; sl < OZ_SLICES; ++sl) out[sl * sstride + r * Kpad + k] = o[sl];
+  }
+  if (lane == 0) {
+    ex[(int64_t)ch * rows + r] = e;
+    if (e > -99999) atomicMax(emax, e);
+  }
+}
+
+// A operand of the dL/dM GEMM: rows = the chunk's slices s = (xl, j), K = the
+// Y rows (a <= b, {u, v}); Y_row(s) = sign(w_s) (M~_au M~_bv + M~_av M~_bu)
+// with M~ = sqrt|w_s| M in double-FP32 (as the forward's Y), exponent per
+// (slice, chunk of OZ_KC rows).  One block per slice: its M row staged in
+// shared memory; warp w takes the row chunks w, w + 8, ...
+__global__ void __launch_bounds__(256) k_adj_split_y(int64_t S, int nbl, int nbp, int n_mu, int x0,
+                                                     const double *__restrict__ M, const double *__restrict__ om,
+                                                     const double *__restrict__ xw, int64_t rowsY, int KpadY,
+                                                     __nv_bfloat16 *__restrict__ out, int *__restrict__ ex,
+                                                     int *__restrict__ emax, int *__restrict__ err) {
+  extern __shared__ __align__(16) unsigned char ay_sm[];
+  f2 *Ms = reinterpret_cast<f2 *>(ay_sm);  // [nbl * nbp]
+  const int64_t sl = blockIdx.x;
+  if (sl >= S) return;
+  const int nblp = nbl * nbp, P2 = nbp * (nbp + 1) / 2;
+  const double w = om[sl % n_mu] * xw[x0 + sl / n_mu];
+  const f2 sw = df_from_d(sqrt(fabs(w)));
+  const float sg = w < 0.0 ? -1.f : 1.f;
+  for (int c = threadIdx.x; c < nblp; c += blockDim.x) Ms[c] = df_mul(df_from_d_fast(M[sl * nblp + c]), sw);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nch = (int)cdiv64(KpadY, OZ_KC);
+  auto yval = [&](int64_t r) -> f2 {
+    int a, b, u, v;
+    y_row_decode(r, P2, b, a, u, v);
+    const f2 y = df_addv(df_mul(Ms[a * nbp + u], Ms[b * nbp + v]), df_mul(Ms[a * nbp + v], Ms[b * nbp + u]));
+    return {sg * y.h, sg * y.l};
+  };
+  const int64_t sstride = S * (int64_t)KpadY;
+  for (int ch = warp; ch < nch; ch += 8) {
+    const int64_t k0 = (int64_t)ch * OZ_KC, k1 = min(rowsY, k0 + OZ_KC), kend = min((int64_t)KpadY, k0 + OZ_KC);
+    float m = 0.f;
+    for (int64_t k = k0 + lane; k < k1; k += 32) m = fmaxf(m, fabsf(yval(k).h));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (!(m < 1e37f)) {
+      if (lane == 0) atomicOr(err, ERR_RANGE);
+      m = 0.f;
+    }
+    const int e = exp_bound_f(m);
+    for (int64_t k = k0 + lane; k < kend; k += 32) {
+      const f2 y = k < rowsY ? yval(k) : f2{0.f, 0.f};
+      __nv_bfloat16 o[OZ_SLICES];
+      split_f2(y.h, y.l, e, o);
+#pragma unroll
+      for (int q = 0; q < OZ_SLICES; ++q) out[q * sstride + sl * KpadY + k] = o[q];
+    }
+    if (lane == 0) {
+      ex[(int64_t)ch * S + sl] = e;
+      if (e > -99999) atomicMax(emax, e);
+    }
+  }
+}
+
+// Gfull^T[(x, y)][row] += gbar[n][n'] / (48 pi) for every (n, n') and each of
+// the nine positions (i, j) of the late triple L = late[n] and the
+// primordial triple C = prim[n']: (x, y) = (L_i, C_j), row = the 2 x 2
+// minor's rows (the other two late indices, sorted) and columns (the other
+// two primordial indices, unordered).
+__global__ void k_adj_scatter_gfull(int nbl, int nbp, const double *__restrict__ gbar, const int *__restrict__ late,
+                                    const int *__restrict__ prim, int n_late, int n_prim, double scale,
+                                    int64_t rowsY, double *__restrict__ GfT) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n_late * n_prim) return;
+  const int n = (int)(idx / n_prim), m = (int)(idx % n_prim);
+  const int Lt[3] = {late[3 * n], late[3 * n + 1], late[3 * n + 2]};
+  const int Ct[3] = {prim[3 * m], prim[3 * m + 1], prim[3 * m + 2]};
+  for (int i = 0; i < 3; ++i)
+    if ((unsigned)Lt[i] >= (unsigned)nbl || (unsigned)Ct[i] >= (unsigned)nbp) return;
+  const int P2 = nbp * (nbp + 1) / 2;
+  const double v = scale * gbar[idx];
+  for (int i = 0; i < 3; ++i) {
+    const int r1 = Lt[(i + 1) % 3], r2 = Lt[(i + 2) % 3];
+    const int64_t pr = pair_index(r1 < r2 ? r1 : r2, r1 < r2 ? r2 : r1);
+    for (int j = 0; j < 3; ++j) {
+      const int c1 = Ct[(j + 1) % 3], c2 = Ct[(j + 2) % 3];
+      const int64_t row = pr * P2 + pair_index(c1, c2);
+      atomicAdd(GfT + ((int64_t)Lt[i] * nbp + Ct[j]) * rowsY + row, v);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The Y-through-HBM triple product in two phases on two streams, so that the
 // Y pass of one radial chunk runs beside the GEMM of the previous one.  Two
@@ -2733,6 +2898,228 @@ int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double 
     snprintf(g_tc_err, sizeof g_tc_err, "triple product: %s", cudaGetErrorString(e));
     return MODAL_ECUDA;
   }
+  return MODAL_OK;
+}
+
+// dL/dq~ rows of the chunk and its addition to dL/dq from T (FP64):
+//   dqt[x0 + xl][p][l]  = sum_a q_a(l) T[(xl, a, p)][l]           (blocks with a == 0)
+//   dq[a][l]           += sum_{xl, p} q~_p(l, x0 + xl) T[(xl, a, p)][l]
+// one thread per (l, a).
+__global__ void k_adj_reduce_t(int nc, int nbl, int nbp, int L, int x0, const double *__restrict__ T,
+                               const double *__restrict__ q, const double *__restrict__ qt, double *__restrict__ dqt,
+                               double *__restrict__ dq) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (l >= L) return;
+  const int64_t nblp = (int64_t)nbl * nbp;
+  double sq = 0.0;
+  for (int xl = 0; xl < nc; ++xl)
+    for (int p = 0; p < nbp; ++p) {
+      if (dq) sq = fma(qt[((int64_t)(x0 + xl) * nbp + p) * L + l], T[((int64_t)xl * nblp + (int64_t)a * nbp + p) * L + l], sq);
+      if (a == 0) {
+        double st = 0.0;
+        for (int aa = 0; aa < nbl; ++aa)
+          st = fma(q[(int64_t)aa * L + l], T[((int64_t)xl * nblp + (int64_t)aa * nbp + p) * L + l], st);
+        dqt[((int64_t)(x0 + xl) * nbp + p) * L + l] = st;
+      }
+    }
+  if (dq) dq[(int64_t)a * L + l] += sq;
+}
+
+// ---------------------------------------------------------------------------
+// Host side of the tensor-core adjoint.
+// ---------------------------------------------------------------------------
+// Dense C = A B^T (out[r ld_r + c ld_c], stored or added) on the exact-slicing
+// GEMM kernel from operands already split: A [5][rowsA][Kpad] with exponents
+// eA [chunks][rowsA] and their maximum *emaxA, B likewise.
+static int dense_gemm(const __nv_bfloat16 *As, const int *eA, const int *emaxA, int64_t rowsA,
+                      const __nv_bfloat16 *Bs, const int *eB, const int *emaxB, int64_t rowsB, int Kpad, double *out,
+                      int64_t ld_r, int64_t ld_c, bool accumulate, int *err, long long wait_cycles, cudaStream_t st,
+                      Profiler *prof, const char *name) {
+  CUtensorMap ta;
+  BMaps tb;
+  if (int r = make_slices_map(&ta, As, rowsA, Kpad, OZ_BM)) return r;
+  if (int r = make_bmaps(&tb, Bs, rowsB, Kpad, 1u << (OZ_BN / 16 - 1))) return r;
+  OzParams P{};
+  P.rowsA = rowsA;
+  P.rowsB = rowsB;
+  P.Kpad = Kpad;
+  P.nchunks = (int)cdiv64(Kpad, OZ_KC);
+  P.eA = eA;
+  P.eB = eB;
+  P.emaxA = emaxA;
+  P.emaxB = emaxB;
+  P.out = out;
+  P.err = err;
+  P.wait_cycles = wait_cycles;
+  P.ld_r = ld_r;
+  P.ld_c = ld_c;
+  P.out_accumulate = accumulate ? 1 : 0;
+  fill_mma_plans(P.plan);
+  const int64_t nrt = cdiv64(rowsA, OZ_BM), nct = cdiv64(rowsB, OZ_BN);
+  int rpc = (int)(nrt * nct / (4 * 152));
+  rpc = rpc < 1 ? 1 : (rpc > 4 ? 4 : rpc);
+  P.rows_per_cta = rpc;
+  cudaError_t e = cudaFuncSetAttribute(k_ozaki_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+  if (e == cudaSuccess) {
+    ProfScope ps(prof, name, st);
+    k_ozaki_gemm<2><<<dim3((unsigned)nct, (unsigned)cdiv64(nrt, rpc)), OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    snprintf(g_tc_err, sizeof g_tc_err, "%s: %s", name, cudaGetErrorString(e));
+    return MODAL_ECUDA;
+  }
+  return MODAL_OK;
+}
+
+template <class Op>
+static int split_op(int64_t rows, int64_t K, int Kpad, const Op &op, __nv_bfloat16 *out, int *ex, int *emax,
+                    int *err, cudaStream_t st, Profiler *prof, const char *name) {
+  ProfScope ps(prof, name, st);
+  const int nch = (int)cdiv64(Kpad, OZ_KC);
+  k_split_op<Op><<<(unsigned)cdiv64(rows * nch * 32, 256), 256, 0, st>>>(rows, K, Kpad, op, out, ex, emax, err);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(g_tc_err, sizeof g_tc_err, "%s: %s", name, cudaGetErrorString(e));
+    return MODAL_ECUDA;
+  }
+  return MODAL_OK;
+}
+
+// reset words [first, first + n) of the status block to "no exponent yet"
+__global__ void k_reset_emax(int *w, int n) {
+  if ((int)threadIdx.x < n) w[threadIdx.x] = -100000;
+}
+
+static int64_t pad32(int64_t v) { return cdiv64(v, 32) * 32; }
+
+struct AdjScratch {
+  char *lreg;  // the l contraction's scratch (l_scratch layout, status words first)
+  double *mu, *om, *A, *M, *GfT, *dM, *T;
+  __nv_bfloat16 *GfTs, *AtS, *YTs, *dMTs;
+  int *eG, *eAt, *eY, *edMT;
+  char *end;
+};
+static AdjScratch adj_scratch(void *base, const SepShape &s, int nxc) {
+  const int64_t nblp = (int64_t)s.nbl * s.nbp, rowsY = y_rows(s), S = (int64_t)nxc * s.n_mu;
+  const int64_t KY = pad32(rowsY), Kj = pad32(s.n_mu);
+  auto nch = [](int64_t K) { return cdiv64(K, OZ_KC); };
+  AdjScratch r;
+  char *w = (char *)base;
+  r.lreg = w;
+  w = l_scratch(w, s, nxc).end;
+  w = (char *)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+  r.mu = (double *)w; w += up256(8 * (size_t)s.n_mu);
+  r.om = (double *)w; w += up256(8 * (size_t)s.n_mu);
+  r.A = (double *)w; w += up256(8 * (size_t)s.n_mu * s.L);
+  r.M = (double *)w; w += up256(8 * (size_t)S * nblp);
+  r.dM = (double *)w; w += up256(8 * (size_t)S * nblp);
+  r.T = (double *)w; w += up256(8 * (size_t)nxc * nblp * s.L);
+  r.GfT = (double *)w; w += up256(8 * (size_t)nblp * rowsY);
+  r.GfTs = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * nblp * KY * 2);
+  r.eG = (int *)w; w += up256(4 * (size_t)nch(KY) * nblp);
+  r.AtS = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * s.L * Kj * 2);
+  r.eAt = (int *)w; w += up256(4 * (size_t)nch(Kj) * s.L);
+  r.YTs = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * S * KY * 2);
+  r.eY = (int *)w; w += up256(4 * (size_t)nch(KY) * S);
+  r.dMTs = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * nxc * nblp * Kj * 2);
+  r.edMT = (int *)w; w += up256(4 * (size_t)nch(Kj) * nxc * nblp);
+  r.end = w;
+  return r;
+}
+
+size_t tc_backward_scratch_bytes(const SepShape &s, int nxc) {
+  return (size_t)(adj_scratch(nullptr, s, nxc).end - (char *)nullptr) + 1024;
+}
+
+// radial points per chunk of the tensor-core adjoint: its per-point buffers
+// (Y^T slices, M, dM and its slices, T) within 4 GiB, 1 .. 16
+int tc_backward_nxc(const SepShape &s) {
+  const int64_t per_x = (int64_t)s.n_mu * (10 * pad32(y_rows(s)) + 26 * (int64_t)s.nbl * s.nbp) +
+                        8 * (int64_t)s.nbl * s.nbp * s.L;
+  int64_t c = ((int64_t)4 << 30) / (per_x > 0 ? per_x : 1);
+  c = c < 1 ? 1 : (c > 16 ? 16 : c);
+  return (int)(c > s.n_x ? (s.n_x > 0 ? s.n_x : 1) : c);
+}
+
+// The adjoint on the tensor cores (see the block comment above k_adj_split_y).
+// Status words (the l contraction's block): [0] error bits; adjoint maxima at
+// [32] Y^T, [33] Gfull^T, [34] dM^T, [35] A^T.
+int tc_backward(const SepShape &s, int nxc, const modal_problem *p, const double *gbar, double *dqt, double *dq,
+                void *scratch, long long wc, cudaStream_t st, Profiler *prof) {
+  AdjScratch r = adj_scratch(scratch, s, nxc);
+  int *words = (int *)r.lreg, *aw = words + 32;
+  const int64_t nblp = (int64_t)s.nbl * s.nbp, rowsY = y_rows(s);
+  const int KY = (int)pad32(rowsY), Kj = (int)pad32(s.n_mu);
+  cudaError_t e;
+#define ADJ_CK(x)                                                                      \
+  do {                                                                                 \
+    if ((e = (x)) != cudaSuccess) {                                                    \
+      snprintf(g_tc_err, sizeof g_tc_err, "adjoint: %s: %s", #x, cudaGetErrorString(e)); \
+      return MODAL_ECUDA;                                                              \
+    }                                                                                  \
+  } while (0)
+  ADJ_CK(launch_zero(dqt, (size_t)s.n_x * s.nbp * s.L, st));
+  if (dq) ADJ_CK(launch_zero(dq, (size_t)s.nbl * s.L, st));
+  if (s.n_x == 0 || (int64_t)p->n_late * p->n_prim == 0) return MODAL_OK;
+  {
+    ProfScope ps(prof, "adj_tables", st, 2);
+    ADJ_CK(launch_gl_nodes(s.n_mu, r.mu, r.om, st));
+    ADJ_CK(launch_legendre_table(s.n_mu, r.mu, s.l_min, s.l_max, p->w_l, r.A, st));
+  }
+  // the x-independent operands: Gfull^T (rows (x, y), K = Y rows) and A q (rows l, K = (j, a))
+  if (int rr = tc_prepare_l(s, r.A, p->q, r.lreg, nxc, st, prof, true)) return rr;
+  {
+    ProfScope ps(prof, "adj_gfull", st, 3);
+    k_reset_emax<<<1, 32, 0, st>>>(aw, 8);
+    ADJ_CK(launch_zero(r.GfT, (size_t)nblp * rowsY, st));
+    const int64_t n = (int64_t)p->n_late * p->n_prim;
+    k_adj_scatter_gfull<<<(unsigned)cdiv64(n, 256), 256, 0, st>>>(s.nbl, s.nbp, gbar, p->late_modes, p->prim_modes,
+                                                                   p->n_late, p->n_prim, 1.0 / (48.0 * MODAL_PI),
+                                                                   rowsY, r.GfT);
+    ADJ_CK(cudaGetLastError());
+  }
+  if (int rr = split_op(nblp, rowsY, KY, OpGfullT{r.GfT, rowsY}, r.GfTs, r.eG, aw + 1, words, st, prof,
+                        "adj_split_gfull"))
+    return rr;
+  if (int rr = split_op((int64_t)s.L, (int64_t)s.n_mu, Kj, OpAt{r.A, s.L}, r.AtS, r.eAt, aw + 3, words, st, prof,
+                        "adj_split_a"))
+    return rr;
+  const size_t ysm = sizeof(f2) * (size_t)nblp;
+  ADJ_CK(cudaFuncSetAttribute(k_adj_split_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm));
+  for (int x0 = 0; x0 < s.n_x; x0 += nxc) {
+    const int nc = (s.n_x - x0) < nxc ? (s.n_x - x0) : nxc;
+    const int64_t S = (int64_t)nc * s.n_mu;
+    if (int rr = tc_contract_l(s, p->qt, x0, nc, nxc, r.M, r.lreg, wc, st, prof)) return rr;  // M (FP64)
+    {
+      ProfScope ps(prof, "adj_split_y", st, 2);
+      k_reset_emax<<<1, 32, 0, st>>>(aw, 1);
+      k_adj_split_y<<<(unsigned)S, 256, ysm, st>>>(S, s.nbl, s.nbp, s.n_mu, x0, r.M, r.om, p->x_w, rowsY, KY, r.YTs,
+                                                    r.eY, aw, words);
+      ADJ_CK(cudaGetLastError());
+    }
+    // dL/dM [s][(x, y)] = Y^T Gfull over the Y rows
+    if (int rr = dense_gemm(r.YTs, r.eY, aw, S, r.GfTs, r.eG, aw + 1, nblp, KY, r.dM, nblp, 1, false, words, wc, st,
+                            prof, "adj_gemm_dM"))
+      return rr;
+    // T[(xl, a, p)][l] = sum_j dM against the Legendre table, then dL/dq~ and dL/dq
+    k_reset_emax<<<1, 32, 0, st>>>(aw + 2, 1);
+    if (int rr = split_op((int64_t)nc * nblp, (int64_t)s.n_mu, Kj, OpDmT{r.dM, s.n_mu, (int)nblp}, r.dMTs, r.edMT,
+                          aw + 2, words, st, prof, "adj_split_dm"))
+      return rr;
+    if (int rr = dense_gemm(r.dMTs, r.edMT, aw + 2, (int64_t)nc * nblp, r.AtS, r.eAt, aw + 3, s.L, Kj, r.T, s.L, 1,
+                            false, words, wc, st, prof, "adj_gemm_t"))
+      return rr;
+    {
+      ProfScope ps(prof, "adj_reduce_t", st);
+      k_adj_reduce_t<<<dim3((unsigned)cdiv(s.L, 128), (unsigned)(dq ? s.nbl : 1)), 128, 0, st>>>(nc, s.nbl, s.nbp,
+                                                                                                 s.L, x0, r.T,
+                                                                                      p->q, p->qt, dqt, dq);
+      ADJ_CK(cudaGetLastError());
+    }
+  }
+#undef ADJ_CK
   return MODAL_OK;
 }
 

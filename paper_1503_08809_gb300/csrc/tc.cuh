@@ -46,6 +46,14 @@ int tc_triple_prep(const SepShape &s, const double *M, const double *om, const d
 int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double *G, bool accumulate,
                    void *scratch, int set, long long wait_cycles, int grid_sms, int tune, cudaStream_t st,
                    Profiler *prof = nullptr);
+// The adjoint of the separable form on the tensor cores (exact slicing):
+// dL/dM by one GEMM over the Y rows per radial chunk, then dL/dq~ and dL/dq
+// by two more; nxc radial points per chunk (tc_backward_nxc).  The status
+// word is tc_error_word(scratch).
+size_t tc_backward_scratch_bytes(const SepShape &s, int nxc);
+int tc_backward_nxc(const SepShape &s);
+int tc_backward(const SepShape &s, int nxc, const modal_problem *p, const double *gbar, double *dqt, double *dq,
+                void *scratch, long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
 // device status word of the tensor-core scratch (bit 0: a bounded wait gave up,
 // bit 1: a value outside the FP32 exponent range of the split operands)
 int *tc_error_word(void *scratch);

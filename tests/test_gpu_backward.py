@@ -97,3 +97,67 @@ def test_grad_config_finite_differences(mg):
     fd = float((lp - lm) / (2 * h))
     an = float((dqt * v).sum())
     assert an == pytest.approx(fd, rel=1e-4)
+
+
+TOL_TC = 1e-8
+
+
+@pytest.mark.parametrize("shape,x_chunk", [((14, 3, 3, 3), 0), ((48, 5, 5, 24), 0), ((37, 6, 4, 13), 5),
+                                           ((60, 12, 11, 7), 2), ((20, 1, 5, 3), 0)])
+def test_backward_tensor_form(mg, shape, x_chunk):
+    """The adjoint's three contractions on tcgen05 (MODAL_PREC_OZAKI_BF16):
+    dL/dM over the 2 x 2 minors of the permanent, then dL/dq~ and dL/dq,
+    against the oracle's adjoint at the tensor form's bound, 1e-8 normwise."""
+    lmax, nbl, nbp, nx = shape
+    P = syn.make_problem(lmax, nbl, nx, seed=17, nb_prim=nbp)
+    gbar = syn.random_cotangent(P.n_late, P.n_prim, seed=8)
+    dqt_ref, dq_ref = oracle.backward(P, gbar)
+    h = mg.Handle()
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    dqt, dq = mg.project_backward(dp, torch.tensor(gbar, device="cuda"), precision=mg.PREC_OZAKI_BF16,
+                                  x_chunk=x_chunk, handle=h)
+    mg.handle_status(handle=h)
+    assert normwise(dqt, dqt_ref) < TOL_TC
+    assert normwise(dq, dq_ref) < TOL_TC
+    h.close()
+
+
+def test_backward_tensor_form_grad_config(mg):
+    """The gradient workload (l_max 1000, 16 functions, 300 x) in the tensor
+    form: against the FP64 GPU adjoint at 1e-8, and the directional
+    derivative against a central difference of the FP64 forward."""
+    P = syn.grad_size()
+    h = mg.Handle()
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    gbar = torch.tensor(syn.random_cotangent(P.n_late, P.n_prim, seed=4), device="cuda")
+    dqt, dq = mg.project_backward(dp, gbar, precision=mg.PREC_OZAKI_BF16, handle=h)
+    mg.handle_status(handle=h)
+    dqt64, dq64 = mg.project_backward(dp, gbar, handle=h)
+    assert normwise(dqt, dqt64.cpu().numpy()) < TOL_TC
+    assert normwise(dq, dq64.cpu().numpy()) < TOL_TC
+    rng = np.random.default_rng(9)
+    v = torch.tensor(rng.standard_normal(P.qt.shape), device="cuda") * dp.qt.abs().max()
+    hh = 1e-6
+    lp = (gbar * mg.project_separable(dp, qt=(dp.qt + hh * v).contiguous(), handle=h)).sum()
+    lm = (gbar * mg.project_separable(dp, qt=(dp.qt - hh * v).contiguous(), handle=h)).sum()
+    fd = float((lp - lm) / (2 * hh))
+    assert float((dqt * v).sum()) == pytest.approx(fd, rel=1e-4)
+    h.close()
+
+
+def test_backward_tensor_form_bounded_wait(mg):
+    P = syn.make_problem(30, 4, 5, seed=19)
+    gbar = torch.tensor(syn.random_cotangent(P.n_late, P.n_prim, seed=2), device="cuda")
+    h = mg.Handle()
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    mg.set_wait_limit(1, handle=h)
+    mg.project_backward(dp, gbar, precision=mg.PREC_OZAKI_BF16, handle=h)
+    with pytest.raises(mg.ModalError) as ei:
+        mg.handle_status(handle=h)
+    assert ei.value.code == 4
+    mg.set_wait_limit(0, handle=h)
+    dqt, dq = mg.project_backward(dp, gbar, precision=mg.PREC_OZAKI_BF16, handle=h)
+    mg.handle_status(handle=h)
+    dqt_ref, dq_ref = oracle.backward(P, gbar.cpu().numpy())
+    assert normwise(dqt, dqt_ref) < TOL_TC and normwise(dq, dq_ref) < TOL_TC
+    h.close()
