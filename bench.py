@@ -679,6 +679,20 @@ def run_extra(args):
         dqt64, dq64 = mg.project_backward(dp, gbar, handle=h)
         nw = lambda a, b: float((a - b).abs().max() / b.abs().max())
         cfg["adjoint_error_vs_fp64"] = {"dqt_normwise": nw(dqt, dqt64), "dq_normwise": nw(dq, dq64)}
+        # per-kernel times of one step (the library's CUDA-event profiler) and
+        # the adjoint's dL/dM GEMM against the BF16 peak
+        prof = profiled(h, step, dev)
+        cfg["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
+        if "adj_gemm_dM" in prof and bprec == PREC["ozaki"]:
+            nl, tot = prof["adj_gemm_dM"]
+            p2l, p2p = P.nb_late * (P.nb_late + 1) // 2, P.nb_prim * (P.nb_prim + 1) // 2
+            macs = P.slices * P.nb_late * P.nb_prim * p2l * p2p       # per step: slices x (x,y) x Y rows
+            peaks, src = measured_peaks()
+            achieved = TC_SLICE_PRODUCTS * 2.0 * macs / (tot * 1e-3) / 1e12
+            cfg["roofline_adjoint_dM"] = {"kernel": "adj_gemm_dM", "bound": "tensor", "achieved": achieved,
+                                          "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                                          "frac": achieved / peaks["bf16_tflops"], "launches": nl,
+                                          "ms": tot, "peak_source": f"bf16 {src}"}
     if args.workload == "full":
         cfg["parts_ms"] = {}
         for name, f in parts.items():
@@ -696,6 +710,30 @@ def run_extra(args):
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "dtype": dtype, "data": "synthetic",
                       "config": cfg}), flush=True)
+
+
+def profiled(h, fn, dev):
+    """Per-kernel launches and device time (ms) of one call of fn, from the
+    library's own CUDA-event profiler."""
+    import ctypes
+    import torch
+    import paper_1503_08809_gb300 as mg
+    lib = mg.lib()
+    names = ctypes.create_string_buffer(32 * 64)
+    launches = (ctypes.c_int64 * 64)()
+    tms = (ctypes.c_double * 64)()
+    nout = ctypes.c_int32()
+    lib.modal_profile_enable(h.ptr, 1)
+    lib.modal_profile_read(h.ptr, 64, names, launches, tms, ctypes.byref(nout))  # reset
+    fn()
+    torch.cuda.synchronize(dev)
+    lib.modal_profile_read(h.ptr, 64, names, launches, tms, ctypes.byref(nout))
+    lib.modal_profile_enable(h.ptr, 0)
+    out = {}
+    for i in range(nout.value):
+        nm = names.raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
+        out[nm] = (int(launches[i]), float(tms[i]))
+    return out
 
 
 def fp64_sequential(probs, dps, batched_value, dev, h, n_pts: int = 2):

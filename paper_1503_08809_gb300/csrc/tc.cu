@@ -2668,50 +2668,95 @@ __global__ void k_split_op(int64_t rows, int64_t K, int Kpad, Op op, __nv_bfloat
 
 // A operand of the dL/dM GEMM: rows = the chunk's slices s = (xl, j), K = the
 // Y rows (a <= b, {u, v}); Y_row(s) = sign(w_s) (M~_au M~_bv + M~_av M~_bu)
-// with M~ = sqrt|w_s| M in double-FP32 (as the forward's Y), exponent per
-// (slice, chunk of OZ_KC rows).  One block per slice: its M row staged in
-// shared memory; warp w takes the row chunks w, w + 8, ...
+// with M~ = sqrt|w_s| M in double-FP32 (as the forward's Y).  One block per
+// slice: its M~ row, the per-a maxima m_a = max_u |M~_au| and the decoding
+// tables of the pair indices in shared memory; warp w takes the row chunks
+// w, w + 8, ... of OZ_KC rows.  A chunk's exponent comes from the bound
+// |Y| <= 2 m_a m_b over the pairs (a, b) it spans (no pass over the values,
+// as for the forward's Y rows); lane i forms rows 4i .. 4i + 3 of each
+// 128-row group and stores four BF16 per slice (8 bytes).
+constexpr int AY_MAXNB = 64;
+__host__ __device__ inline size_t ay_smem_bytes(int nbl, int nbp) {
+  return sizeof(f2) * (size_t)nbl * nbp + sizeof(float) * AY_MAXNB +
+         sizeof(int) * ((size_t)nbp * (nbp + 1) / 2 + (size_t)nbl * (nbl + 1) / 2);
+}
 __global__ void __launch_bounds__(256) k_adj_split_y(int64_t S, int nbl, int nbp, int n_mu, int x0,
                                                      const double *__restrict__ M, const double *__restrict__ om,
                                                      const double *__restrict__ xw, int64_t rowsY, int KpadY,
                                                      __nv_bfloat16 *__restrict__ out, int *__restrict__ ex,
                                                      int *__restrict__ emax, int *__restrict__ err) {
   extern __shared__ __align__(16) unsigned char ay_sm[];
-  f2 *Ms = reinterpret_cast<f2 *>(ay_sm);  // [nbl * nbp]
+  const int nblp = nbl * nbp, P2 = nbp * (nbp + 1) / 2, P2l = nbl * (nbl + 1) / 2;
+  f2 *Ms = reinterpret_cast<f2 *>(ay_sm);                       // [nblp]
+  float *rmax = reinterpret_cast<float *>(Ms + nblp);           // [AY_MAXNB]
+  int *uvtab = reinterpret_cast<int *>(rmax + AY_MAXNB);        // uv -> u | v << 8
+  int *prtab = uvtab + P2;                                       // pair -> a | b << 8
   const int64_t sl = blockIdx.x;
   if (sl >= S) return;
-  const int nblp = nbl * nbp, P2 = nbp * (nbp + 1) / 2;
   const double w = om[sl % n_mu] * xw[x0 + sl / n_mu];
   const f2 sw = df_from_d(sqrt(fabs(w)));
   const float sg = w < 0.0 ? -1.f : 1.f;
   for (int c = threadIdx.x; c < nblp; c += blockDim.x) Ms[c] = df_mul(df_from_d_fast(M[sl * nblp + c]), sw);
+  for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+    int u, v;
+    pair_decode(i, u, v);
+    uvtab[i] = u | v << 8;
+  }
+  for (int i = threadIdx.x; i < P2l; i += blockDim.x) {
+    int a, b;
+    pair_decode(i, a, b);
+    prtab[i] = a | b << 8;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < nbl; a += blockDim.x) {
+    float m = 0.f;
+    for (int u = 0; u < nbp; ++u) m = fmaxf(m, fabsf(Ms[a * nbp + u].h) + fabsf(Ms[a * nbp + u].l));
+    rmax[a] = m;
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nch = (int)cdiv64(KpadY, OZ_KC);
-  auto yval = [&](int64_t r) -> f2 {
-    int a, b, u, v;
-    y_row_decode(r, P2, b, a, u, v);
-    const f2 y = df_addv(df_mul(Ms[a * nbp + u], Ms[b * nbp + v]), df_mul(Ms[a * nbp + v], Ms[b * nbp + u]));
-    return {sg * y.h, sg * y.l};
-  };
   const int64_t sstride = S * (int64_t)KpadY;
+  uint2 *outq = reinterpret_cast<uint2 *>(out);
   for (int ch = warp; ch < nch; ch += 8) {
-    const int64_t k0 = (int64_t)ch * OZ_KC, k1 = min(rowsY, k0 + OZ_KC), kend = min((int64_t)KpadY, k0 + OZ_KC);
-    float m = 0.f;
-    for (int64_t k = k0 + lane; k < k1; k += 32) m = fmaxf(m, fabsf(yval(k).h));
+    const int64_t k0 = (int64_t)ch * OZ_KC, kend = min((int64_t)KpadY, k0 + OZ_KC);
+    const int64_t klast = min(rowsY, k0 + OZ_KC) - 1;
+    // bound over the pairs of rows [k0, klast]
+    float bnd = 0.f;
+    if (k0 <= klast)
+      for (int64_t pr = k0 / P2 + lane; pr <= klast / P2; pr += 32) {
+        const int ab = prtab[pr];
+        bnd = fmaxf(bnd, 2.f * rmax[ab & 255] * rmax[ab >> 8]);
+      }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (!(m < 1e37f)) {
+    for (int o = 16; o; o >>= 1) bnd = fmaxf(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
+    if (!(bnd < 1e37f)) {
       if (lane == 0) atomicOr(err, ERR_RANGE);
-      m = 0.f;
+      bnd = 0.f;
     }
-    const int e = exp_bound_f(m);
-    for (int64_t k = k0 + lane; k < kend; k += 32) {
-      const f2 y = k < rowsY ? yval(k) : f2{0.f, 0.f};
-      __nv_bfloat16 o[OZ_SLICES];
-      split_f2(y.h, y.l, e, o);
+    const int e = exp_bound_f(bnd);
+    const SplitScale sc = split_scale(e);
+    for (int64_t r0 = k0 + 4 * lane; r0 < kend; r0 += 128) {
+      float q[4][OZ_SLICES];
 #pragma unroll
-      for (int q = 0; q < OZ_SLICES; ++q) out[q * sstride + sl * KpadY + k] = o[q];
+      for (int t = 0; t < 4; ++t) {
+        const int64_t r = r0 + t;
+        float h = 0.f, l = 0.f;
+        if (r < rowsY) {
+          const int ab = prtab[r / P2], uv = uvtab[r % P2];
+          const int oa = (ab & 255) * nbp, ob = (ab >> 8) * nbp, u = uv & 255, v = uv >> 8;
+          const f2 y = df_addv(df_mul(Ms[oa + u], Ms[ob + v]), df_mul(Ms[oa + v], Ms[ob + u]));
+          h = sg * y.h;
+          l = sg * y.l;
+        }
+        const float H = sc.zero ? 0.f : (h * sc.s1) * sc.s2;
+        const float L = sc.zero ? 0.f : (l * sc.s1) * sc.s2;
+        split_hl(H, L, q[t]);
+      }
+#pragma unroll
+      for (int qq = 0; qq < OZ_SLICES; ++qq)
+        outq[(qq * sstride + sl * KpadY + r0) / 4] =
+            make_uint2(bf16x2_bits(make_float2(q[0][qq], q[1][qq])), bf16x2_bits(make_float2(q[2][qq], q[3][qq])));
     }
     if (lane == 0) {
       ex[(int64_t)ch * S + sl] = e;
@@ -3086,7 +3131,7 @@ int tc_backward(const SepShape &s, int nxc, const modal_problem *p, const double
   if (int rr = split_op((int64_t)s.L, (int64_t)s.n_mu, Kj, OpAt{r.A, s.L}, r.AtS, r.eAt, aw + 3, words, st, prof,
                         "adj_split_a"))
     return rr;
-  const size_t ysm = sizeof(f2) * (size_t)nblp;
+  const size_t ysm = ay_smem_bytes(s.nbl, s.nbp);
   ADJ_CK(cudaFuncSetAttribute(k_adj_split_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm));
   for (int x0 = 0; x0 < s.n_x; x0 += nxc) {
     const int nc = (s.n_x - x0) < nxc ? (s.n_x - x0) : nxc;
