@@ -58,8 +58,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", *PREC],
-                    help="auto: the tensor-core form (ozaki) for the headline and batched "
-                         "workloads, fp32 for the gradient workload")
+                    help="auto: the tensor-core form (ozaki) for every workload (the gradient "
+                         "workload's adjoint included)")
     ap.add_argument("--n-x", type=int, default=500, help="radial points (workload: 500)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -79,6 +79,8 @@ def parse():
                     help="none: one independent problem per rank (weak scaling); x: the radial "
                          "points of one problem split over the ranks, Gamma' summed by an "
                          "all-reduce (strong scaling)")
+    ap.add_argument("--x-chunk", type=int, default=0,
+                    help="radial points per streamed chunk (0: the library's choice)")
     ap.add_argument("--tc-queue", type=int, default=0, choices=[0, 1],
                     help="tensor-core triple product GEMM as a persistent kernel over a work queue: 1")
     ap.add_argument("--tc-overlap", type=int, default=0,
@@ -258,7 +260,7 @@ def run_ours(args):
         if sharded:
             mg.project_separable_sharded(dp, rank, ws, precision=prec, out=gamma, handle=h)
         else:
-            mg.project_separable(dp, precision=prec, out=gamma, handle=h)
+            mg.project_separable(dp, precision=prec, out=gamma, handle=h, x_chunk=args.x_chunk)
 
     for _ in range(args.warmup):
         step()
@@ -577,10 +579,8 @@ def run_extra(args):
     import paper_1503_08809_gb300 as mg
     import synthetic as syn
     dev = torch.device("cuda", 0)
-    # auto: FP32 forward and adjoint for the gradient workload, the
-    # tensor-core form for the batched one
-    prec_name = args.precision if args.precision != "auto" else (
-        "fp32" if args.workload == "grad" else "ozaki")
+    # auto: the tensor-core form (forward and adjoint) for every workload
+    prec_name = args.precision if args.precision != "auto" else "ozaki"
     prec = PREC[prec_name]
     h = mg.Handle(dev)
     mg.set_option(mg.OPT_TC_PAIR, args.tc_pair, handle=h)

@@ -3079,12 +3079,12 @@ size_t tc_backward_scratch_bytes(const SepShape &s, int nxc) {
 }
 
 // radial points per chunk of the tensor-core adjoint: its per-point buffers
-// (Y^T slices, M, dM and its slices, T) within 4 GiB, 1 .. 16
+// (Y^T slices, M, dM and its slices, T) within 8 GiB, 1 .. 32
 int tc_backward_nxc(const SepShape &s) {
   const int64_t per_x = (int64_t)s.n_mu * (10 * pad32(y_rows(s)) + 26 * (int64_t)s.nbl * s.nbp) +
                         8 * (int64_t)s.nbl * s.nbp * s.L;
-  int64_t c = ((int64_t)4 << 30) / (per_x > 0 ? per_x : 1);
-  c = c < 1 ? 1 : (c > 16 ? 16 : c);
+  int64_t c = ((int64_t)8 << 30) / (per_x > 0 ? per_x : 1);
+  c = c < 1 ? 1 : (c > 32 ? 32 : c);
   return (int)(c > s.n_x ? (s.n_x > 0 ? s.n_x : 1) : c);
 }
 
