@@ -41,11 +41,11 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (CUDA cores), nominal figure
 FP32_TFLOPS = 73.3           # GB300 FP32 FMA rate measured on this machine with an FMA-chain kernel
 TC_SLICE_PRODUCTS = 15       # BF16 slice products per useful MAC in the tensor-core form
 # DRAM bytes (read + write) per launch of the workload's size, from one ncu
-# capture (n_x = 4 gives one launch with the same K as every launch of the
+# capture (n_x = 8 gives one launch with the same K as every launch of the
 # 500-point step), keyed by the kernel's form.  A form that changed since its
 # capture is left out (its traffic is then reported as null).
-NCU_TRAFFIC = {("tc_gemm_triple", "single"): 5.562e9 + 48.6e6, ("tc_make_Y", "single"): 44.3e6 + 5.245e9,
-               ("tc_make_Y", "pair"): 44.3e6 + 5.245e9, ("tc_make_Y", "queue"): 44.3e6 + 5.245e9}
+NCU_TRAFFIC = {("tc_gemm_triple", "single"): 11.346e9 + 49.9e6, ("tc_make_Y", "single"): 88.3e6 + 10.551e9,
+               ("tc_make_Y", "pair"): 88.3e6 + 10.551e9, ("tc_make_Y", "queue"): 88.3e6 + 10.551e9}
 # kernels inside one profiler scope (the library counts kernels; a roofline
 # divides the scope's time by its scope count)
 SCOPE_KERNELS = {"tc_make_Y": 2, "tc_prep_M": 2}
