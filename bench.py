@@ -87,6 +87,8 @@ def parse():
                     help="SMs left to the Y pass running beside the queue GEMM (0: no overlap)")
     ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1],
                     help="tensor-core triple product GEMM on CTA pairs (2-SM MMA): 1, or single CTAs: 0")
+    ap.add_argument("--direct-tensor", type=int, default=0, choices=[0, 1],
+                    help="direct workload: Gamma' update on the tensor cores (BF16 slices): 1, FP64: 0")
     ap.add_argument("--once", action="store_true",
                     help="run one projection and exit (a small case for profiler captures)")
     ap.add_argument("--fp64-x", type=int, default=20,
@@ -607,10 +609,14 @@ def run_extra(args):
         slices = sparse_triples(lg)          # the unit here: (l1 <= l2 <= l3) triples
         unit = "triples/s"
 
+        mg.set_option(mg.OPT_DIRECT_TENSOR, args.direct_tensor, handle=h)
+        gdir = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device=dev)
+
         def step():
-            mg.project_direct(dp, lg, dw, handle=h)
+            mg.project_direct(dp, lg, dw, out=gdir, handle=h)
         cfg = {"workload": P.name + "_sparse_direct", "l_max": P.l_max, "nb": P.nb_late, "n_x": P.n_x,
                "grid_points": int(lg.size), "triples": slices, "weight": "exact 3j^2",
+               "gamma_update": "tensor cores, BF16 slices" if args.direct_tensor else "FP64",
                "step": "one direct projection (Eq. 3D) on the sparse grid"}
     elif args.workload == "full":
         P = syn.planck_size()
@@ -664,6 +670,15 @@ def run_extra(args):
     ms = e0.elapsed_time(e1) / args.steps
     if args.workload == "batched":
         cfg["fp64_sequential"] = fp64_sequential(probs, dps, slices / (ms * 1e-3), dev, h)
+    if args.workload == "direct":
+        prof = profiled(h, step, dev)
+        cfg["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
+        if args.direct_tensor:                  # the same call in FP64 throughout, for the error
+            mg.handle_status(handle=h)
+            g = gdir.clone()
+            mg.set_option(mg.OPT_DIRECT_TENSOR, 0, handle=h)
+            mg.project_direct(dp, lg, dw, out=gdir, handle=h)
+            cfg["error_vs_fp64"] = float((g - gdir).abs().max() / gdir.abs().max())
     if args.workload == "grad":             # forward alone, and the error of the adjoint vs FP64
         torch.cuda.synchronize(dev)
         e0.record(st)
@@ -705,7 +720,9 @@ def run_extra(args):
             cfg["parts_ms"][name] = e0.elapsed_time(e1) / args.steps
         _, info = mg.gram_solve(S, gp, handle=h, raise_if_not_pd=False)
         assert int(info.item()) == 0
-    dtype = "f64" if args.workload == "direct" else DTYPE[prec_name]   # the direct form is FP64 throughout
+    # the direct form is FP64 throughout unless its Gamma' update runs on the tensor cores
+    dtype = (("f64+bf16x(ozaki)" if args.direct_tensor else "f64") if args.workload == "direct"
+             else DTYPE[prec_name])
     print(json.dumps({"metric": METRIC, "value": slices / (ms * 1e-3), "unit": unit,
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "dtype": dtype, "data": "synthetic",

@@ -153,6 +153,12 @@ int modal_handle_status(modal_handle *h);
  *   second stream beside the previous chunk's GEMM, which then runs as the
  *   queue form on all but n SMs (two scratch sets; single-problem calls
  *   without error_estimate; implies MODAL_OPT_TC_QUEUE).  0 (default): off.
+ * MODAL_OPT_DIRECT_TENSOR: 1 runs the Gamma' update of modal_project_direct
+ *   (Gamma' += Y^T diag(z) X over each batch of triples, the reduction of
+ *   Eq. 3D) on the tensor cores with exponent-aligned BF16 slices (errors of
+ *   ~1e-10 of max|Gamma'| instead of FP64 rounding; the radial integrals X
+ *   stay FP64); the call's status then also covers that GEMM's bounded
+ *   waits (modal_handle_status).  0 (default): FP64 throughout.
  * MODAL_OPT_BATCH_STREAMS: concurrent streams of modal_project_separable_batched
  *   (1 .. 8), or 0 (default): the first call for a problem set captures one
  *   graph each for 1, 2, 4 and 8 streams (as far as their scratch fits),
@@ -164,6 +170,7 @@ int modal_handle_status(modal_handle *h);
 #define MODAL_OPT_TC_QUEUE 5
 #define MODAL_OPT_TC_AUTOTUNE 6
 #define MODAL_OPT_TC_OVERLAP 7
+#define MODAL_OPT_DIRECT_TENSOR 8
 int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value);
 
 /* Bound (in SM clock cycles) of those device-side waits for later calls on

@@ -44,6 +44,7 @@ struct modal_handle {
   int opt_queue = 0;              // the triple GEMM as a persistent kernel over a work queue
   int opt_autotune = 1;           // batched calls time the triple GEMM's tile shapes per bucket
   int opt_overlap = 0;            // SMs left to the Y pass beside the queue GEMM (0: no overlap)
+  int opt_direct_tensor = 0;      // the direct form's Gamma update on the tensor cores
   cudaStream_t ovl_stream = nullptr;
   cudaEvent_t ovl_ev[6] = {};     // fork, l contraction done, side done, prep[2] / gemm[2] (below)
   cudaEvent_t ovl_prep[2] = {}, ovl_gemm[2] = {};
@@ -305,6 +306,10 @@ int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value) {
       if (value < 0 || value > h->num_sms / 2)
         return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_OVERLAP takes 0 .. %d", h->num_sms / 2);
       h->opt_overlap = (int)value;
+      return MODAL_OK;
+    case MODAL_OPT_DIRECT_TENSOR:
+      if (value < 0 || value > 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_DIRECT_TENSOR takes 0 or 1");
+      h->opt_direct_tensor = (int)value;
       return MODAL_OK;
     case MODAL_OPT_BATCH_STREAMS:
       if (value < 0 || value > MAX_BATCH_STREAMS)
@@ -1172,8 +1177,10 @@ int modal_project_direct(modal_handle *h, const modal_problem *p, const int32_t 
   b1 += align256(sizeof(int) * 3 * (size_t)T) + align256(sizeof(double) * (size_t)T);  // batch triples, weights
   b1 += align256(sizeof(double) * (size_t)T * p->n_late) + align256(sizeof(double) * (size_t)T * p->n_prim);
   b1 += 1024;
-  void *s1;
+  void *s1, *tcs = nullptr;
   if (int r = ws_get(h, 1, b1, &s1)) return r;
+  if (h->opt_direct_tensor)
+    if (int r = ws_get(h, 0, tc_gemm_batch_scratch_bytes(p->n_late, p->n_prim, T), &tcs)) return r;
   Bump bp{(char *)s1};
   double *qtT = bp.take<double>((size_t)L * p->n_x * p->nb_prim);
   int64_t *counts = bp.take<int64_t>((size_t)npairs);
@@ -1229,8 +1236,24 @@ int modal_project_direct(modal_handle *h, const modal_problem *p, const int32_t 
                                                             p->late_modes, p->n_late, Yb);
       CK(cudaGetLastError());
     }
-    PROF(h, "direct_gemm", st);
-    CK(launch_gemm_nt_f64(p->n_late, p->n_prim, T, Yb, T, Xb, T, gamma, p->n_prim, bi > 0, st, ntri, t0));
+    if (tcs) {
+      // Gamma' += Y X^T over the batch's triples on the exact-slicing GEMM
+      // (Gamma' zeroed before the first batch; batches past the end do nothing)
+      if (bi == 0) CK(launch_zero(gamma, (size_t)p->n_late * p->n_prim, st));
+      Profiler *prof = h->prof.on ? &h->prof : nullptr;
+      if (int r = tc_gemm_batch(p->n_late, p->n_prim, T, Yb, Xb, ntri, t0, gamma, p->n_prim, tcs, bi == 0,
+                                h->wait_cycles, st, prof))
+        return fail(h, r, "tensor-core direct update failed: %s", tc_last_error());
+    } else {
+      PROF(h, "direct_gemm", st);
+      CK(launch_gemm_nt_f64(p->n_late, p->n_prim, T, Yb, T, Xb, T, gamma, p->n_prim, bi > 0, st, ntri, t0));
+    }
+  }
+  if (tcs) {
+    CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(tcs), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(h->err_event, st));
+    h->n_err_words = 1;
+    h->err_pending = true;
   }
   return MODAL_OK;
 }

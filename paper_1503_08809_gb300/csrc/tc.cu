@@ -240,9 +240,12 @@ struct OzParams {
   // OUT_MODE 1
   GLayout g;
   long long wait_cycles;
-  // OUT_MODE 2: dense C[r][c] at out[r * ld_r + c * ld_c], stored or added
+  // OUT_MODE 2: dense C[r][c] at out[r * ld_r + c * ld_c], stored or added;
+  // with kdev, no work at all when *kdev <= koff (a batch past the end)
   int64_t ld_r, ld_c;
   int out_accumulate;
+  const int64_t *kdev;
+  int64_t koff;
 };
 
 
@@ -268,6 +271,7 @@ struct BMaps {
 template <int OUT_MODE>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ BMaps bmaps, OzParams P) {
+  if (OUT_MODE == 2 && P.kdev && *P.kdev <= P.koff) return;  // the whole CTA: nothing to add
   extern __shared__ unsigned char smraw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   float *lo_s = (float *)(sm + OZ_STAGES * OZ_STAGE_BYTES);  // [col][row]
@@ -2612,20 +2616,32 @@ cuda_fail:
 struct OpGfullT {  // rows (x, y) over nblp, K = Y rows: Gfull^T stored [nblp][rowsY]
   const double *g;
   int64_t rowsY;
+  __device__ bool empty() const { return false; }
   __device__ double val(int64_t r, int64_t k) const { return g[r * rowsY + k]; }
 };
 struct OpAt {  // rows l, K = j: the weighted Legendre table A[j][l] = w_l P_l(mu_j)
   const double *A;
   int L;
+  __device__ bool empty() const { return false; }
   __device__ double val(int64_t r, int64_t k) const { return A[k * L + r]; }
 };
 struct OpDmT {  // rows (xl, a, p), K = j: dM[(xl n_mu + j) nblp + (a nbp + p)]
   const double *dM;
   int n_mu, nblp;
+  __device__ bool empty() const { return false; }
   __device__ double val(int64_t r, int64_t k) const {
     const int64_t xl = r / nblp, ap = r % nblp;
     return dM[(xl * n_mu + k) * nblp + ap];
   }
+};
+
+struct OpBatch {  // rows r, K = t: P[r * T + t] for t0 + t < *count, else 0 (a batch of the direct form)
+  const double *P;
+  int64_t T;
+  const int64_t *count;
+  int64_t t0;
+  __device__ bool empty() const { return *count <= t0; }
+  __device__ double val(int64_t r, int64_t k) const { return t0 + k < *count ? P[r * T + k] : 0.0; }
 };
 
 // One warp per (row, K chunk of OZ_KC): the chunk's max |x| (FP32-rounded),
@@ -2634,6 +2650,7 @@ struct OpDmT {  // rows (xl, a, p), K = j: dM[(xl n_mu + j) nblp + (a nbp + p)]
 template <class Op>
 __global__ void k_split_op(int64_t rows, int64_t K, int Kpad, Op op, __nv_bfloat16 *__restrict__ out,
                            int *__restrict__ ex, int *__restrict__ emax, int *__restrict__ err) {
+  if (op.empty()) return;
   const int lane = threadIdx.x & 31;
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nch = (int)cdiv64(Kpad, OZ_KC);
@@ -2980,7 +2997,7 @@ __global__ void k_adj_reduce_t(int nc, int nbl, int nbp, int L, int x0, const do
 static int dense_gemm(const __nv_bfloat16 *As, const int *eA, const int *emaxA, int64_t rowsA,
                       const __nv_bfloat16 *Bs, const int *eB, const int *emaxB, int64_t rowsB, int Kpad, double *out,
                       int64_t ld_r, int64_t ld_c, bool accumulate, int *err, long long wait_cycles, cudaStream_t st,
-                      Profiler *prof, const char *name) {
+                      Profiler *prof, const char *name, const int64_t *kdev = nullptr, int64_t koff = 0) {
   CUtensorMap ta;
   BMaps tb;
   if (int r = make_slices_map(&ta, As, rowsA, Kpad, OZ_BM)) return r;
@@ -3000,6 +3017,8 @@ static int dense_gemm(const __nv_bfloat16 *As, const int *eA, const int *emaxA, 
   P.ld_r = ld_r;
   P.ld_c = ld_c;
   P.out_accumulate = accumulate ? 1 : 0;
+  P.kdev = kdev;
+  P.koff = koff;
   fill_mma_plans(P.plan);
   const int64_t nrt = cdiv64(rowsA, OZ_BM), nct = cdiv64(rowsB, OZ_BN);
   int rpc = (int)(nrt * nct / (4 * 152));
@@ -3166,6 +3185,46 @@ int tc_backward(const SepShape &s, int nxc, const modal_problem *p, const double
   }
 #undef ADJ_CK
   return MODAL_OK;
+}
+
+// C[m][n] += sum_t A[m][t] B[n][t] over the t < *count - t0 of a batch of T
+// terms (A [m][T], B [n][T] FP64), on the exact-slicing GEMM; a batch past
+// the end does no work.  Scratch: [words 1 KB][A slices, exponents][B ...].
+static size_t tc_batch_parts(int m, int n, int T, char *base, int **words, __nv_bfloat16 **As, int **eA,
+                             __nv_bfloat16 **Bs, int **eB) {
+  const int64_t Kp = pad32(T), nch = cdiv64(Kp, OZ_KC);
+  char *w = base;
+  *words = (int *)w; w += 1024;
+  *As = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * m * Kp * 2);
+  *eA = (int *)w; w += up256(4 * (size_t)nch * m);
+  *Bs = (__nv_bfloat16 *)w; w += up256((size_t)OZ_SLICES * n * Kp * 2);
+  *eB = (int *)w; w += up256(4 * (size_t)nch * n);
+  return (size_t)(w - base);
+}
+size_t tc_gemm_batch_scratch_bytes(int m, int n, int T) {
+  int *w, *ea, *eb;
+  __nv_bfloat16 *a, *b;
+  return tc_batch_parts(m, n, T, nullptr, &w, &a, &ea, &b, &eb) + 256;
+}
+int tc_gemm_batch(int m, int n, int T, const double *A, const double *B, const int64_t *count, int64_t t0, double *C,
+                  int64_t ldc, void *scratch, bool reset_status, long long wc, cudaStream_t st, Profiler *prof) {
+  int *words, *eA, *eB;
+  __nv_bfloat16 *As, *Bs;
+  tc_batch_parts(m, n, T, (char *)scratch, &words, &As, &eA, &Bs, &eB);
+  const int Kp = (int)pad32(T);
+  if (reset_status && cudaMemsetAsync(words, 0, sizeof(int), st) != cudaSuccess) {
+    snprintf(g_tc_err, sizeof g_tc_err, "batch GEMM: status reset failed");
+    return MODAL_ECUDA;
+  }
+  k_reset_emax<<<1, 32, 0, st>>>(words + 1, 2);
+  if (int r = split_op((int64_t)m, (int64_t)T, Kp, OpBatch{A, T, count, t0}, As, eA, words + 1, words, st, prof,
+                       "direct_split"))
+    return r;
+  if (int r = split_op((int64_t)n, (int64_t)T, Kp, OpBatch{B, T, count, t0}, Bs, eB, words + 2, words, st, prof,
+                       "direct_split"))
+    return r;
+  return dense_gemm(As, eA, words + 1, m, Bs, eB, words + 2, n, Kp, C, ldc, 1, true, words, wc, st, prof,
+                    "direct_gemm_tc", count, t0);
 }
 
 int *tc_error_word(void *scratch) { return (int *)scratch; }

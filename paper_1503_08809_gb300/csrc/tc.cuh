@@ -54,6 +54,13 @@ size_t tc_backward_scratch_bytes(const SepShape &s, int nxc);
 int tc_backward_nxc(const SepShape &s);
 int tc_backward(const SepShape &s, int nxc, const modal_problem *p, const double *gbar, double *dqt, double *dq,
                 void *scratch, long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
+// C[m][n] += A B^T over one batch of T terms of the direct form (only the
+// t < *count - t0 valid ones; a batch past the end does no work), on the
+// exact-slicing GEMM.  Status word: tc_error_word(scratch).
+size_t tc_gemm_batch_scratch_bytes(int m, int n, int T);
+int tc_gemm_batch(int m, int n, int T, const double *A, const double *B, const int64_t *count, int64_t t0, double *C,
+                  int64_t ldc, void *scratch, bool reset_status, long long wait_cycles, cudaStream_t st,
+                  Profiler *prof = nullptr);
 // device status word of the tensor-core scratch (bit 0: a bounded wait gave up,
 // bit 1: a value outside the FP32 exponent range of the split operands)
 int *tc_error_word(void *scratch);

@@ -115,3 +115,67 @@ def test_direct_graph_capture(mg):
     torch.cuda.synchronize()
     assert normwise(out, oracle.direct(P2, l_grid=lg, l_dw=dw)) < TOL
     h.close()
+
+
+# The tensor-core form of the Gamma' update (MODAL_OPT_DIRECT_TENSOR): five
+# 7-bit BF16 slices per operand, products of levels <= 4 and exact level-0/1
+# sums per 1024-triple chunk leave a relative error of a few 2^-35 per term
+# against sum |Y||X|; the tolerance is the mixed-precision gate of the
+# separable path (1e-8 of max|Gamma'|).
+TOL_TC = 1e-8
+
+
+def _tensor_handle(mg):
+    h = mg.Handle()
+    mg.set_option(mg.OPT_DIRECT_TENSOR, 1, handle=h)
+    return h
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_direct_tensor_update_sparse(mg, mode):
+    P = syn.make_problem(160, 4, 9, seed=3, nb_prim=3)
+    lg, dw = syn.sparse_l_grid(160)
+    h = _tensor_handle(mg)
+    g = mg.project_direct(mg.DeviceProblem.from_host(P, handle=h), lg, dw, weight_mode=mode, handle=h)
+    assert mg.handle_status(handle=h) == 0
+    ref = oracle.direct(P, l_grid=lg, l_dw=dw, weight_mode=mode)
+    err = normwise(g, ref)
+    assert err < TOL_TC, err
+    h.close()
+
+
+def test_direct_tensor_update_dense_and_edges(mg):
+    """Dense grid (several 1024-triple chunks and a ragged last batch), then
+    an empty grid and a single-point grid on the same handle."""
+    P = syn.cpu_size()
+    h = _tensor_handle(mg)
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    g = mg.project_direct(dp, handle=h)
+    assert normwise(g, oracle.direct(P)) < TOL_TC
+    g = mg.project_direct(dp, l_grid=np.zeros(0, dtype=np.int32), handle=h)
+    assert torch.count_nonzero(g) == 0
+    g = mg.project_direct(dp, l_grid=np.array([4]), l_dw=np.array([2.5]), handle=h)
+    assert normwise(g, oracle.direct(P, l_grid=np.array([4]), l_dw=np.array([2.5]))) < TOL_TC
+    assert mg.handle_status(handle=h) == 0
+    h.close()
+
+
+def test_direct_tensor_update_planck_sparse_sampled(mg):
+    """Planck-scale sparse grid (31 batches of 32768 triples, the last one
+    ragged): sampled entries against the oracle and the whole matrix against
+    the FP64 GPU path."""
+    P = syn.planck_size()
+    lg, dw = syn.sparse_l_grid(P.l_max)
+    h = _tensor_handle(mg)
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    g = mg.project_direct(dp, lg, dw, handle=h).cpu().numpy()
+    assert mg.handle_status(handle=h) == 0
+    g64 = mg.project_direct(dp, lg, dw).cpu().numpy()
+    assert np.isfinite(g).all()
+    assert normwise(g, g64) < TOL_TC
+    rows = np.array([0, 5, 100, 777, 1539])
+    cols = np.array([3, 400, 1200])
+    ref = oracle.direct(P, l_grid=lg, l_dw=dw, late=P.late_modes[rows], prim=P.prim_modes[cols])
+    got = g[np.ix_(rows, cols)]
+    assert np.abs(got - ref).max() / np.abs(g64).max() < TOL_TC
+    h.close()
