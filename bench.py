@@ -87,8 +87,9 @@ def parse():
                     help="SMs left to the Y pass running beside the queue GEMM (0: no overlap)")
     ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1],
                     help="tensor-core triple product GEMM on CTA pairs (2-SM MMA): 1, or single CTAs: 0")
-    ap.add_argument("--direct-tensor", type=int, default=0, choices=[0, 1],
-                    help="direct workload: Gamma' update on the tensor cores (BF16 slices): 1, FP64: 0")
+    ap.add_argument("--direct-tensor", type=int, default=0, choices=[0, 1, 2],
+                    help="direct workload on the tensor cores (BF16 slices): 1 the Gamma' update, "
+                         "2 also the radial integrals; 0: FP64")
     ap.add_argument("--once", action="store_true",
                     help="run one projection and exit (a small case for profiler captures)")
     ap.add_argument("--fp64-x", type=int, default=20,
@@ -616,7 +617,7 @@ def run_extra(args):
             mg.project_direct(dp, lg, dw, out=gdir, handle=h)
         cfg = {"workload": P.name + "_sparse_direct", "l_max": P.l_max, "nb": P.nb_late, "n_x": P.n_x,
                "grid_points": int(lg.size), "triples": slices, "weight": "exact 3j^2",
-               "gamma_update": "tensor cores, BF16 slices" if args.direct_tensor else "FP64",
+               "tensor_cores": ["none", "Gamma' update", "radial integrals and Gamma' update"][args.direct_tensor],
                "step": "one direct projection (Eq. 3D) on the sparse grid"}
     elif args.workload == "full":
         P = syn.planck_size()

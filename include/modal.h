@@ -157,8 +157,12 @@ int modal_handle_status(modal_handle *h);
  *   (Gamma' += Y^T diag(z) X over each batch of triples, the reduction of
  *   Eq. 3D) on the tensor cores with exponent-aligned BF16 slices (errors of
  *   ~1e-10 of max|Gamma'| instead of FP64 rounding; the radial integrals X
- *   stay FP64); the call's status then also covers that GEMM's bounded
- *   waits (modal_handle_status).  0 (default): FP64 throughout.
+ *   stay FP64); 2 also forms the radial integrals there (triples grouped by
+ *   (l2, l3): one GEMM of the grid's q~ rows with that pair's products
+ *   W_x q~_u(l2) q~_v(l3) per pair; bases of up to 32 primordial functions,
+ *   larger ones run as 1).  The call's status then also covers those GEMMs'
+ *   bounded waits and the exponent range of their operands
+ *   (modal_handle_status).  0 (default): FP64 throughout.
  * MODAL_OPT_BATCH_STREAMS: concurrent streams of modal_project_separable_batched
  *   (1 .. 8), or 0 (default): the first call for a problem set captures one
  *   graph each for 1, 2, 4 and 8 streams (as far as their scratch fits),

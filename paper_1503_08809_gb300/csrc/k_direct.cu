@@ -50,15 +50,6 @@ __global__ void k_direct_count(int ng, const int *__restrict__ grid, int mode,
   counts[idx] = c;
 }
 
-__device__ __forceinline__ double gosper_3j2(int l1, int l2, int l3) {
-  // Section 2.1 Gosper form of h^2 divided by prod(2l+1)/(4 pi)
-  double L = (double)(l1 + l2 + l3);
-  double L1 = L - 2.0 * l1, L2 = L - 2.0 * l2, L3 = L - 2.0 * l3;
-  double v = (2.0 / MODAL_PI) * (L + 1.0 / 3.0) /
-             ((L + 1.0) * (L1 + 1.0 / 3.0) * (L2 + 1.0 / 3.0) * (L3 + 1.0 / 3.0));
-  return v * sqrt((L1 + 1.0 / 6.0) * (L2 + 1.0 / 6.0) * (L3 + 1.0 / 6.0) / (L + 1.0 / 6.0));
-}
-
 // Length of the flat triple list: the last pair's offset plus its count.
 __global__ void k_direct_total(const int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
                                int64_t npairs, int64_t *__restrict__ ntri) {
@@ -96,19 +87,10 @@ __global__ void k_direct_fill_batch(int ng, const int *__restrict__ grid, const 
     if (l3 > l1 + l2) break;
     if (mode == MODAL_W_EXACT_3J && ((l1 + l2 + l3) & 1)) continue;
     if (k-- > 0) continue;
-    double H;
-    if (mode == MODAL_W_EXACT_3J) {
-      const int g = (l1 + l2 + l3) / 2;
-      H = ctab[g - l1] * ctab[g - l2] * ctab[g - l3] / ((2.0 * g + 1.0) * ctab[g]);
-    } else {
-      H = 0.5 * gosper_3j2(l1, l2, l3);
-    }
-    const int mult = (l1 == l2 && l2 == l3) ? 1 : ((l1 == l2 || l2 == l3) ? 3 : 6);
-    const double d = (dw ? dw[i1] * dw[i2] * dw[i3] : 1.0) * w_l[l1 - l_min] * w_l[l2 - l_min] * w_l[l3 - l_min];
     tri[3 * tt] = l1;
     tri[3 * tt + 1] = l2;
     tri[3 * tt + 2] = l3;
-    z[tt] = (double)mult * d * H / (144.0 * MODAL_PI);
+    z[tt] = direct_weight(l1, l2, l3, i1, i2, i3, dw, w_l, l_min, ctab, mode);
     return;
   }
 }

@@ -308,7 +308,7 @@ int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value) {
       h->opt_overlap = (int)value;
       return MODAL_OK;
     case MODAL_OPT_DIRECT_TENSOR:
-      if (value < 0 || value > 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_DIRECT_TENSOR takes 0 or 1");
+      if (value < 0 || value > 2) return fail(h, MODAL_EINVAL, "MODAL_OPT_DIRECT_TENSOR takes 0, 1 or 2");
       h->opt_direct_tensor = (int)value;
       return MODAL_OK;
     case MODAL_OPT_BATCH_STREAMS:
@@ -1152,6 +1152,19 @@ int modal_project_direct(modal_handle *h, const modal_problem *p, const int32_t 
     return MODAL_OK;
   }
   if (!l_grid) return fail(h, MODAL_EINVAL, "null l_grid");
+  if (h->opt_direct_tensor == 2 && tc_direct_supported(p->nb_prim)) {
+    // radial integrals and Gamma' update on the tensor cores
+    void *scratch;
+    if (int r = ws_get(h, 0, tc_direct_scratch_bytes(p, ng), &scratch)) return r;
+    Profiler *prof = h->prof.on ? &h->prof : nullptr;
+    if (int r = tc_project_direct(p, l_grid, l_dw, ng, mode, gamma, scratch, h->num_sms, h->wait_cycles, st, prof))
+      return fail(h, r, "tensor-core direct form failed: %s", tc_last_error());
+    CK(cudaMemcpyAsync(h->pinned_err, tc_error_word(scratch), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(h->err_event, st));
+    h->n_err_words = 1;
+    h->err_pending = true;
+    return MODAL_OK;
+  }
   const int64_t npairs = (int64_t)ng * ng;
   const int cmax = 3 * p->l_max / 2 + 2;
   // The triple count is known only on the device.  Batches of T triples are

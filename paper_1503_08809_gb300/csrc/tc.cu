@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "direct.cuh"
 #include "kernels.cuh"
 #include "ptx.cuh"
 #include "tc.cuh"
@@ -246,6 +247,13 @@ struct OzParams {
   int out_accumulate;
   const int64_t *kdev;
   int64_t koff;
+  // OUT_MODE 3 (direct form): work items {A row, B row, first triple, n | col0 << 16},
+  // item blockIdx.x + t gridDim.x for t = 0, 1, ... below *item_count; tile row
+  // c nbp + p is function p of the item's triple c < n, stored at
+  // out[((tri0 + c) nbp + p) P2 + col0 + col] for col0 + col < P2
+  const int4 *items;
+  const int *item_count;
+  int P2, wtile;
 };
 
 
@@ -292,7 +300,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   int ntile = OZ_BN;  // MMA N of this tile (a multiple of 16)
   int ntt = 1;  // tiles of this CTA (OUT_MODE 0: row tiles of one column tile)
   bool lead = true;  // the first column tile of its row tile: it prefetches A
-  if (OUT_MODE != 1) {
+  if (OUT_MODE == 3) {
+    const int nit = *P.item_count;
+    if ((int)blockIdx.x >= nit) return;  // the whole CTA: no item
+    ntt = (nit - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    lead = false;
+    ntile = P.wtile;
+    a_row0 = b_row0 = 0;  // per item
+    R = C = 0;
+  } else if (OUT_MODE != 1) {
     // column tiles vary fastest, so the CTAs that share a row tile of A run
     // together and A is read from HBM about once; each CTA then moves on to
     // the next row tile, so its set-up, pipeline fill and last drain are
@@ -360,7 +376,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       int issued = 0;
       bool stop = false;
       for (int tt = 0; tt < ntt && !stop; ++tt) {
-        const int ar = (int)(a_row0 + (int64_t)tt * OZ_BM);
+        int ar = (int)(a_row0 + (int64_t)tt * OZ_BM), br = (int)b_row0;
+        if (OUT_MODE == 3) {
+          const int4 it = P.items[blockIdx.x + (int64_t)tt * gridDim.x];
+          ar = it.x;
+          br = it.y;
+        }
         // A tiles are pulled into L2 OZ_PREFETCH stages ahead of their loads,
         // so that the two-stage ring waits on L2 rather than on HBM latency;
         // only the first column tile of a row tile does it (the others load
@@ -379,7 +400,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           unsigned char *st = sm + s * OZ_STAGE_BYTES;
           ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
           ptx::tma_load_3d(st, &tmA, &full[s], i * OZ_BK, ar, 0);
-          ptx::tma_load_3d(st + OZ_A_BYTES, tmB, &full[s], i * OZ_BK, (int)b_row0, 0);
+          ptx::tma_load_3d(st + OZ_A_BYTES, tmB, &full[s], i * OZ_BK, br, 0);
           if (lead && i + OZ_PREFETCH < ksteps) ptx::tma_prefetch_3d(&tmA, (i + OZ_PREFETCH) * OZ_BK, ar, 0);
           ++issued;
         }
@@ -460,8 +481,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     float hi[64];  // high halves in registers, low halves in lo_s
     bool ok = true;
     for (int tt = 0; tt < ntt && ok; ++tt) {
-    const int64_t ar0 = a_row0 + (int64_t)tt * OZ_BM;  // this tile's first row of A
-    const int64_t Rt = OUT_MODE != 1 ? min((int64_t)OZ_BM, P.rowsA - ar0) : R;
+    int64_t ar0 = a_row0 + (int64_t)tt * OZ_BM;  // this tile's first row of A
+    int64_t br0 = b_row0;                         // and of B
+    int64_t Rt = OUT_MODE != 1 ? min((int64_t)OZ_BM, P.rowsA - ar0) : R;
+    int64_t Ct = C;
+    int4 it = make_int4(0, 0, 0, 0);
+    if (OUT_MODE == 3) {
+      it = P.items[blockIdx.x + (int64_t)tt * gridDim.x];
+      ar0 = it.x;
+      br0 = it.y;
+      Rt = (int64_t)(it.w & 0xffff) * P.nbp;
+      Ct = min((int64_t)ntile, (int64_t)(P.P2 - (it.w >> 16)));
+    }
 #pragma unroll
     for (int c = 0; c < 64; ++c) {
       hi[c] = 0.f;
@@ -480,7 +511,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       float fbl[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int64_t bcol = b_row0 + col0 + h * 32 + lane;
+        const int64_t bcol = br0 + col0 + h * 32 + lane;
         const int eb = (bcol < P.rowsB) ? __ldg(P.eB + (int64_t)ch * P.rowsB + bcol) : -100000;
         fbl[h] = pow2f_or0(eb - emB - 2 * OZ_BETA - 40);
       }
@@ -529,13 +560,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         xl = (int)(rB / P.nbp);
         p = (int)(rB % P.nbp);
       }
+      double *zrow = nullptr;  // OUT_MODE 3: this row's Z entries (triple c, function p)
+      if (OUT_MODE == 3)
+        zrow = P.out + ((int64_t)(it.z + row / P.nbp) * P.nbp + row % P.nbp) * P.P2 + (it.w >> 16);
 #pragma unroll  // full unroll keeps hi[]/lo[] in registers
       for (int c = 0; c < 64; ++c) {
         const int col = col0 + c;
-        if (col < C) {
+        if (col < Ct) {
           const double v = f32_scaled_f64(hi[c], ebias) + f32_scaled_f64(lo_s[(col0 + c) * OZ_BM + row], ebias);
           if (OUT_MODE == 0) {
             P.out[xl * mx + mrow + p] = v;
+          } else if (OUT_MODE == 3) {
+            zrow[col] = v;
           } else if (OUT_MODE == 2) {
             double *d = P.out + (ar0 + row) * P.ld_r + (b_row0 + col) * P.ld_c;
             *d = P.out_accumulate ? *d + v : v;
@@ -3226,6 +3262,582 @@ int tc_gemm_batch(int m, int n, int T, const double *A, const double *B, const i
   return dense_gemm(As, eA, words + 1, m, Bs, eB, words + 2, n, Kp, C, ldc, 1, true, words, wc, st, prof,
                     "direct_gemm_tc", count, t0);
 }
+
+// ===========================================================================
+// Direct form (Eq. 3D) with the radial integrals on the tensor cores.
+//
+// For a sorted triple (l1, l2, l3) the radial integral, expanded along l1 as
+// in the FP64 kernel, is
+//   Z[p][{u,v}] = sum_x q~_p(l1, x) U_uv(x),
+//   U_uv(x)     = W_x (q~_u(l2, x) q~_v(l3, x) + q~_v(l2, x) q~_u(l3, x)),
+//   X[(p,r,s)]  = Z[p][{r,s}] + Z[r][{p,s}] + Z[s][{p,r}].
+// U depends on the pair (l2, l3) only, so the triples are grouped by it.
+// The l1 that complete a pair -- grid points with l3 - l2 <= l1 <= l2 and,
+// with exact 3j weights, l1 + l2 + l3 even -- are a contiguous run of the
+// grid points of one parity class; with the q~ rows of the grid ordered by
+// class (A: rows (l1, p), K = x), the Z blocks of all of a pair's triples
+// are one product with the pair's U rows (B: rows {u,v}, K = x).  The work
+// items of that grouped GEMM (OUT_MODE 3) are tiles of cpt = 128 / nbp
+// consecutive l1 of one pair times column tiles of the {u,v} rows.
+//
+// Triples are numbered pair by pair (pairs i2 <= i3 in row-major order of
+// the grid indices, then l1 ascending) and processed in batches of at most
+// DTC_NT tiles and DTC_NP pairs, whose bounds are found on the device (a
+// cursor over the tile list); per batch:
+//   info, fill   ranges of the batch; (l1, l2, l3) and weight z per triple
+//   make_u       the U rows of the batch's pairs, sliced
+//   items, GEMM  Z of every triple of the batch
+//   X, Y         radial integrals from Z; z times the late-time products
+//   Gamma'      += Y X^T on the exact-slicing GEMM (tc_gemm_batch)
+// The host bounds the number of batches by the tile bound (the pairs plus
+// C(ng + 2, 3) / cpt) and the pair bound; batches past the end do no work.
+// ===========================================================================
+constexpr int DTC_NT = 4096;   // tiles per batch (at most)
+constexpr int DTC_NP = 1024;   // pairs per batch (at most)
+constexpr int DTC_MAXNB = 32;  // primordial functions of this form (Z block of a triple in shared memory)
+
+struct DtcBatch {
+  int64_t t0, nt;          // tiles [t0, t0 + nt) (nt = 0: past the end)
+  int64_t trip0, n_tri;    // triples [trip0, trip0 + n_tri)
+  int64_t slot0, nslots;   // pairs with tiles: slots [slot0, slot0 + nslots)
+  int n_items;             // GEMM items (nt x column tiles)
+  int pad;
+};
+
+// first class row k in [lo, hi) with grid[crow[k]] >= v (hi if none)
+__device__ __forceinline__ int dtc_lower(const int *__restrict__ grid, const int *__restrict__ crow, int lo, int hi,
+                                         int v) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (grid[crow[mid]] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// the l1 of the pair (i2 <= i3): class rows [k0, k0 + n)
+struct DtcRun {
+  int k0, n;
+};
+__device__ __forceinline__ DtcRun dtc_run(int i2, int i3, const int *__restrict__ grid, const int *__restrict__ crow,
+                                          const int *__restrict__ cls, int mode) {
+  const int l2 = grid[i2], l3 = grid[i3];
+  const int c = mode == MODAL_W_EXACT_3J ? ((l2 + l3) & 1) : 0;
+  const int base = c ? cls[0] : 0, end = base + cls[c];
+  const int k0 = dtc_lower(grid, crow, base, end, l3 - l2);
+  const int k1 = dtc_lower(grid, crow, base, end, l2 + 1);
+  return {k0, k1 > k0 ? k1 - k0 : 0};
+}
+
+// last index with off[idx] <= t (entries with zero count share the next
+// entry's offset, so this is the entry whose range holds t)
+__device__ __forceinline__ int64_t dtc_find(const int64_t *__restrict__ off, int64_t n, int64_t t) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= t) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo - 1;
+}
+
+// Grid points ordered by class: crow[k] = grid index of class row k; class 0
+// (even l with exact 3j weights, every point otherwise) first.  cls = sizes.
+__global__ void k_dtc_classes(int ng, const int *__restrict__ grid, int mode, int *__restrict__ crow,
+                              int *__restrict__ cls) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const bool par = mode == MODAL_W_EXACT_3J;
+  int k = 0;
+  for (int i = 0; i < ng; ++i)
+    if (!par || !(grid[i] & 1)) crow[k++] = i;
+  const int n0 = k;
+  if (par)
+    for (int i = 0; i < ng; ++i)
+      if (grid[i] & 1) crow[k++] = i;
+  cls[0] = n0;
+  cls[1] = k - n0;
+}
+
+// per pair index (i2, i3) (zero unless i2 <= i3): triples, tiles, has-tiles
+__global__ void k_dtc_count(int ng, const int *__restrict__ grid, const int *__restrict__ crow,
+                            const int *__restrict__ cls, int mode, int cpt, int64_t *__restrict__ tri_cnt,
+                            int64_t *__restrict__ tile_cnt, int64_t *__restrict__ nz_cnt) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ng * ng) return;
+  const int i2 = (int)(idx / ng), i3 = (int)(idx % ng);
+  int64_t n = 0;
+  if (i3 >= i2) n = dtc_run(i2, i3, grid, crow, cls, mode).n;
+  const int64_t nt = (n + cpt - 1) / cpt;
+  tri_cnt[idx] = n;
+  tile_cnt[idx] = nt;
+  nz_cnt[idx] = nt > 0;
+}
+
+// totals {triples, tiles, pairs with tiles}; the batch cursor starts at tile 0
+__global__ void k_dtc_totals(int64_t n, const int64_t *__restrict__ tri_cnt, const int64_t *__restrict__ tri_off,
+                             const int64_t *__restrict__ tile_cnt, const int64_t *__restrict__ tile_off,
+                             const int64_t *__restrict__ nz_cnt, const int64_t *__restrict__ slot_of,
+                             int64_t *__restrict__ tot) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  tot[0] = n > 0 ? tri_off[n - 1] + tri_cnt[n - 1] : 0;
+  tot[1] = n > 0 ? tile_off[n - 1] + tile_cnt[n - 1] : 0;
+  tot[2] = n > 0 ? slot_of[n - 1] + nz_cnt[n - 1] : 0;
+  tot[3] = 0;  // cursor: first tile of the next batch
+}
+
+__global__ void k_dtc_compact(int64_t n, const int64_t *__restrict__ nz_cnt, const int64_t *__restrict__ slot_of,
+                              int *__restrict__ pairs_nz) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n && nz_cnt[idx]) pairs_nz[slot_of[idx]] = (int)idx;
+}
+
+// The next batch: from the cursor, at most DTC_NT tiles and DTC_NP pairs.
+__global__ void k_dtc_info(int nct, int cpt, int64_t npairs, const int64_t *__restrict__ tile_off,
+                           const int64_t *__restrict__ tri_off, const int64_t *__restrict__ slot_of,
+                           const int *__restrict__ pairs_nz, int64_t *__restrict__ tot, DtcBatch *__restrict__ info) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int64_t ntiles = tot[1], nslots = tot[2];
+  DtcBatch r{};
+  r.t0 = tot[3];
+  if (r.t0 < ntiles) {
+    const int64_t pa = dtc_find(tile_off, npairs, r.t0);
+    r.slot0 = slot_of[pa];
+    int64_t t1 = min(r.t0 + DTC_NT, ntiles);
+    if (r.slot0 + DTC_NP < nslots) t1 = min(t1, tile_off[pairs_nz[r.slot0 + DTC_NP]]);
+    r.nt = t1 - r.t0;
+    r.trip0 = tri_off[pa] + (r.t0 - tile_off[pa]) * cpt;
+    int64_t trip1 = tot[0];
+    if (t1 < ntiles) {
+      const int64_t pb = dtc_find(tile_off, npairs, t1);
+      trip1 = tri_off[pb] + (t1 - tile_off[pb]) * cpt;
+    }
+    r.n_tri = trip1 - r.trip0;
+    r.nslots = slot_of[dtc_find(tile_off, npairs, t1 - 1)] - r.slot0 + 1;
+    r.n_items = (int)(r.nt * nct);
+    tot[3] = t1;
+  } else {
+    r.t0 = ntiles;
+  }
+  *info = r;
+}
+
+// (l1, l2, l3) and the weight z of each triple of the batch
+__global__ void k_dtc_fill(const DtcBatch *__restrict__ info, const int64_t *__restrict__ tri_off, int64_t npairs,
+                           int ng, const int *__restrict__ grid, const int *__restrict__ crow,
+                           const int *__restrict__ cls, int mode, const double *__restrict__ dw,
+                           const double *__restrict__ w_l, int l_min, const double *__restrict__ ctab,
+                           int *__restrict__ tri, double *__restrict__ z) {
+  const int64_t tb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tb >= info->n_tri) return;
+  const int64_t t = info->trip0 + tb;
+  const int64_t pr = dtc_find(tri_off, npairs, t);
+  const int i2 = (int)(pr / ng), i3 = (int)(pr % ng);
+  const DtcRun run = dtc_run(i2, i3, grid, crow, cls, mode);
+  const int i1 = crow[run.k0 + (int)(t - tri_off[pr])];
+  const int l1 = grid[i1], l2 = grid[i2], l3 = grid[i3];
+  tri[3 * tb] = l1;
+  tri[3 * tb + 1] = l2;
+  tri[3 * tb + 2] = l3;
+  z[tb] = direct_weight(l1, l2, l3, i1, i2, i3, dw, w_l, l_min, ctab, mode);
+}
+
+// A operand: q~_p(l, x) of the class-ordered grid rows, row k nbp + p
+struct OpQRows {
+  const double *qt;  // [n_x][nbp][L]
+  const int *grid, *crow;
+  int L, l_min, nbp;
+  __device__ bool empty() const { return false; }
+  __device__ double val(int64_t r, int64_t k) const {
+    const int l = grid[crow[r / nbp]];
+    return qt[(k * nbp + r % nbp) * L + (l - l_min)];
+  }
+};
+
+// double-FP32 value of a_u b_v + a_v b_u (high part and unnormalised low part)
+__device__ __forceinline__ void dtc_u_value(f2 au, f2 bv, f2 av, f2 bu, float &h, float &l) {
+  const float p1 = __fmul_rn(au.h, bv.h);
+  float e1 = fmaf(au.h, bv.h, -p1);
+  e1 = fmaf(au.h, bv.l, e1);
+  e1 = fmaf(au.l, bv.h, e1);
+  const float p2 = __fmul_rn(av.h, bu.h);
+  float e2 = fmaf(av.h, bu.h, -p2);
+  e2 = fmaf(av.h, bu.l, e2);
+  e2 = fmaf(av.l, bu.h, e2);
+  h = __fadd_rn(p1, p2);
+  const float bb = __fsub_rn(h, p1);
+  const float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(h, bb)), __fsub_rn(p2, bb));
+  l = __fadd_rn(t, __fadd_rn(e1, e2));
+}
+
+// U rows of the batch's pairs: block (slot, K chunk).  The pair's q~ rows
+// (W_x folded into those of l2) are staged as double-FP32 for xs points at
+// a time; pass 0 finds each row's maximum |U| over the chunk (one warp per
+// row, lanes over x), pass 1 recomputes U and writes the five slices with
+// that row's exponent.  Rows P2 .. urows - 1 (padding of the column tiles)
+// are zero.
+__host__ __device__ inline size_t dtc_u_smem(int nbp, int xs, int urows, int P2) {
+  return (size_t)2 * nbp * xs * sizeof(f2) + (size_t)urows * sizeof(float) + (size_t)P2 * sizeof(int);
+}
+__global__ void __launch_bounds__(256) k_dtc_make_u(const DtcBatch *__restrict__ info, const int *__restrict__ pairs_nz,
+                                                    int ng, const int *__restrict__ grid, int l_min, int L, int nbp,
+                                                    int n_x, const double *__restrict__ qt,
+                                                    const double *__restrict__ xw, int P2, int urows, int Kpad, int xs,
+                                                    int64_t rowsU, __nv_bfloat16 *__restrict__ Us,
+                                                    int *__restrict__ eU, int *__restrict__ emaxU,
+                                                    int *__restrict__ err) {
+  const int slot = blockIdx.x;
+  if (slot >= info->nslots) return;
+  extern __shared__ __align__(16) unsigned char du_sm[];
+  f2 *As = reinterpret_cast<f2 *>(du_sm);  // [nbp][xs]: W_x q~_p(l2, x)
+  f2 *Bs = As + (size_t)nbp * xs;          // [nbp][xs]: q~_p(l3, x)
+  float *rmax = reinterpret_cast<float *>(Bs + (size_t)nbp * xs);
+  int *uvt = reinterpret_cast<int *>(rmax + urows);
+  const int pair = pairs_nz[info->slot0 + slot];
+  const int c2 = grid[pair / ng] - l_min, c3 = grid[pair % ng] - l_min;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int ch = blockIdx.y;
+  for (int i = threadIdx.x; i < urows; i += blockDim.x) rmax[i] = 0.f;
+  for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+    int u, v;
+    pair_decode(i, u, v);
+    uvt[i] = u | v << 8;
+  }
+  const int k0 = ch * OZ_KC, k1 = min(n_x, k0 + OZ_KC), kend = min(Kpad, k0 + OZ_KC);
+  const int64_t rowbase = (int64_t)slot * urows;
+  const int64_t sstride = rowsU * (int64_t)Kpad;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int xb = k0; xb < kend; xb += xs) {
+      const int nx = min(xs, kend - xb);
+      __syncthreads();
+      for (int e = threadIdx.x; e < nbp * nx; e += blockDim.x) {
+        const int p = e / nx, xl = e - p * nx, x = xb + xl;
+        double a = 0.0, b = 0.0;
+        if (x < k1) {
+          const int64_t o = ((int64_t)x * nbp + p) * L;
+          a = xw[x] * qt[o + c2];
+          b = qt[o + c3];
+        }
+        As[p * xs + xl] = df_from_d_fast(a);
+        Bs[p * xs + xl] = df_from_d_fast(b);
+      }
+      __syncthreads();
+      for (int uv = warp; uv < urows; uv += nw) {
+        __nv_bfloat16 *dst = Us + (rowbase + uv) * Kpad + xb;
+        if (uv >= P2) {
+          if (pass == 1)
+            for (int xl = lane; xl < nx; xl += 32)
+#pragma unroll
+              for (int sl = 0; sl < OZ_SLICES; ++sl) dst[sl * sstride + xl] = __float2bfloat16_rn(0.f);
+          continue;
+        }
+        const int u = uvt[uv] & 0xff, v = uvt[uv] >> 8;
+        const f2 *au = As + u * xs, *av = As + v * xs, *bu = Bs + u * xs, *bv = Bs + v * xs;
+        if (pass == 0) {
+          float m = 0.f;
+          for (int xl = lane; xl < nx; xl += 32) {
+            float h, l;
+            dtc_u_value(au[xl], bv[xl], av[xl], bu[xl], h, l);
+            m = fmaxf(m, fabsf(h));
+          }
+#pragma unroll
+          for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+          if (lane == 0) rmax[uv] = fmaxf(rmax[uv], m);
+        } else {
+          const int e = exp_bound_f(rmax[uv]);
+          for (int xl = lane; xl < nx; xl += 32) {
+            float h, l;
+            dtc_u_value(au[xl], bv[xl], av[xl], bu[xl], h, l);
+            __nv_bfloat16 o[OZ_SLICES];
+            split_f2(h, l, e, o);
+#pragma unroll
+            for (int sl = 0; sl < OZ_SLICES; ++sl) dst[sl * sstride + xl] = o[sl];
+          }
+        }
+      }
+    }
+    if (pass == 0) {
+      __syncthreads();
+      for (int uv = threadIdx.x; uv < urows; uv += blockDim.x) {
+        float m = rmax[uv];
+        if (!(m < 1e37f)) {
+          atomicOr(err, ERR_RANGE);
+          m = 0.f;
+          rmax[uv] = 0.f;
+        }
+        const int e = uv < P2 ? exp_bound_f(m) : -100000;
+        eU[(int64_t)ch * rowsU + rowbase + uv] = e;
+        if (e > -99999) atomicMax(emaxU, e);
+      }
+    }
+  }
+}
+
+// work items of the batch's grouped GEMM: tile j, column tile h
+__global__ void k_dtc_items(const DtcBatch *__restrict__ info, const int64_t *__restrict__ tile_off,
+                            const int64_t *__restrict__ tri_off, const int64_t *__restrict__ slot_of, int64_t npairs,
+                            int ng, const int *__restrict__ grid, const int *__restrict__ crow,
+                            const int *__restrict__ cls, int mode, int cpt, int nbp, int nct, int wu, int urows,
+                            int4 *__restrict__ items) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= info->nt) return;
+  const int64_t T = info->t0 + j;
+  const int64_t pr = dtc_find(tile_off, npairs, T);
+  const int tl = (int)(T - tile_off[pr]);
+  const DtcRun run = dtc_run((int)(pr / ng), (int)(pr % ng), grid, crow, cls, mode);
+  const int k = run.k0 + tl * cpt, n = min(cpt, run.n - tl * cpt);
+  const int tri0 = (int)(tri_off[pr] + (int64_t)tl * cpt - info->trip0);
+  const int slot = (int)(slot_of[pr] - info->slot0);
+  for (int h = 0; h < nct; ++h)
+    items[j * nct + h] = make_int4(k * nbp, slot * urows + h * wu, tri0, n | (h * wu) << 16);
+}
+
+// X[m][tb] of the batch's triples from their Z blocks (one triple per block)
+__global__ void __launch_bounds__(256) k_dtc_x(const DtcBatch *__restrict__ info, const double *__restrict__ Z,
+                                               int nbp, int P2, const int *__restrict__ prim, int n_prim,
+                                               double *__restrict__ Xb, int64_t Tcap) {
+  const int64_t tb = blockIdx.x;
+  if (tb >= info->n_tri) return;
+  extern __shared__ double dx_sm[];  // [nbp][P2]
+  const double *zb = Z + tb * nbp * P2;
+  for (int i = threadIdx.x; i < nbp * P2; i += blockDim.x) dx_sm[i] = zb[i];
+  __syncthreads();
+  for (int m = threadIdx.x; m < n_prim; m += blockDim.x) {
+    const int p = prim[3 * m], r = prim[3 * m + 1], s = prim[3 * m + 2];
+    double v;
+    if ((unsigned)p >= (unsigned)nbp || (unsigned)r >= (unsigned)nbp || (unsigned)s >= (unsigned)nbp)
+      v = __longlong_as_double(0x7ff8000000000000LL);
+    else
+      v = dx_sm[p * P2 + pair_index(r, s)] + dx_sm[r * P2 + pair_index(p, s)] + dx_sm[s * P2 + pair_index(p, r)];
+    Xb[m * Tcap + tb] = v;
+  }
+}
+
+// The grouped GEMM: one CTA per SM, items taken in a fixed stride.
+static int grouped_gemm(const __nv_bfloat16 *As, const int *eA, const int *emaxA, int64_t rowsA,
+                        const __nv_bfloat16 *Bs, const int *eB, const int *emaxB, int64_t rowsB, int Kpad, int wtile,
+                        const int4 *items, const int *item_count, int max_items, double *Z, int nbp, int P2,
+                        int *err, long long wait_cycles, int num_sms, cudaStream_t st, Profiler *prof) {
+  CUtensorMap ta;
+  BMaps tb;
+  if (int r = make_slices_map(&ta, As, rowsA, Kpad, OZ_BM)) return r;
+  if (int r = make_bmaps(&tb, Bs, rowsB, Kpad, 1u << (wtile / 16 - 1))) return r;
+  OzParams P{};
+  P.rowsA = rowsA;
+  P.rowsB = rowsB;
+  P.Kpad = Kpad;
+  P.nchunks = (int)cdiv64(Kpad, OZ_KC);
+  P.eA = eA;
+  P.eB = eB;
+  P.emaxA = emaxA;
+  P.emaxB = emaxB;
+  P.out = Z;
+  P.err = err;
+  P.wait_cycles = wait_cycles;
+  P.nbp = nbp;
+  P.items = items;
+  P.item_count = item_count;
+  P.P2 = P2;
+  P.wtile = wtile;
+  fill_mma_plans(P.plan);
+  cudaError_t e = cudaFuncSetAttribute(k_ozaki_gemm<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+  if (e == cudaSuccess) {
+    ProfScope ps(prof, "dtc_gemm", st);
+    const int grid = max(1, min(max_items, num_sms));
+    k_ozaki_gemm<3><<<grid, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    snprintf(g_tc_err, sizeof g_tc_err, "direct grouped GEMM: %s", cudaGetErrorString(e));
+    return MODAL_ECUDA;
+  }
+  return MODAL_OK;
+}
+
+// Shapes and scratch of the form.
+struct DtcShape {
+  int ng, nbp, nbl, n_x, L, n_late, n_prim, P2, cpt, nct, wu, urows, Kx, nchx, xs, cmax;
+  int64_t npairs, Tcap, rowsA, rowsU, nbatch;
+  size_t scan_b, u_smem;
+};
+static DtcShape dtc_shape(const modal_problem *p, int ng) {
+  DtcShape d{};
+  d.ng = ng;
+  d.nbp = p->nb_prim;
+  d.nbl = p->nb_late;
+  d.n_x = p->n_x;
+  d.L = p->l_max - p->l_min + 1;
+  d.n_late = p->n_late;
+  d.n_prim = p->n_prim;
+  d.P2 = d.nbp * (d.nbp + 1) / 2;
+  d.cpt = OZ_BM / d.nbp;
+  d.nct = (int)cdiv64(d.P2, OZ_BN);
+  d.wu = g_tile_width(d.P2);
+  d.urows = d.nct * d.wu;
+  d.Kx = (int)pad32(d.n_x);
+  d.nchx = (int)cdiv64(d.Kx, OZ_KC);
+  d.xs = (int)std::min<int64_t>(OZ_KC, (160 * 1024) / (2 * (int64_t)d.nbp * (int64_t)sizeof(f2)));
+  d.cmax = 3 * p->l_max / 2 + 2;
+  d.npairs = (int64_t)ng * ng;
+  d.Tcap = (int64_t)DTC_NT * d.cpt;
+  d.rowsA = (int64_t)ng * d.nbp;
+  d.rowsU = (int64_t)DTC_NP * d.urows;
+  // batches: each ends at DTC_NT tiles, at DTC_NP pairs, or at the end
+  const int64_t pairs_sorted = (int64_t)ng * (ng + 1) / 2;
+  const int64_t tiles_bound = pairs_sorted + (int64_t)ng * (ng + 1) * (ng + 2) / 6 / d.cpt;
+  d.nbatch = cdiv64(tiles_bound, DTC_NT) + cdiv64(pairs_sorted, DTC_NP);
+  d.scan_b = scan_tmp_bytes(d.npairs);
+  d.u_smem = dtc_u_smem(d.nbp, d.xs, d.urows, d.P2);
+  return d;
+}
+
+struct DtcScratch {
+  int *words;  // [0] status (shared with the Gamma' GEMM), [3] A and [4] U exponent maxima
+  double *ctab, *Z, *z, *Xb, *Yb;
+  int *crow, *cls, *pairs_nz, *tri;
+  int64_t *tri_cnt, *tile_cnt, *nz_cnt, *tri_off, *tile_off, *slot_of, *tot;
+  DtcBatch *info;
+  int4 *items;
+  void *scan_tmp, *gscr;
+  __nv_bfloat16 *As, *Us;
+  int *eA, *eU;
+  char *end;
+};
+static DtcScratch dtc_scratch(void *base, const DtcShape &d) {
+  DtcScratch r{};
+  char *w = (char *)base;
+  r.gscr = w;  // the Gamma' GEMM's scratch first: its status word is the call's
+  w += up256(tc_gemm_batch_scratch_bytes(d.n_late, d.n_prim, (int)d.Tcap));
+  r.words = (int *)r.gscr;
+  auto take = [&](size_t bytes) {
+    char *p = w;
+    w += up256(bytes);
+    return (void *)p;
+  };
+  r.ctab = (double *)take(sizeof(double) * (d.cmax + 1));
+  r.crow = (int *)take(sizeof(int) * d.ng);
+  r.cls = (int *)take(sizeof(int) * 2);
+  r.tri_cnt = (int64_t *)take(sizeof(int64_t) * d.npairs);
+  r.tile_cnt = (int64_t *)take(sizeof(int64_t) * d.npairs);
+  r.nz_cnt = (int64_t *)take(sizeof(int64_t) * d.npairs);
+  r.tri_off = (int64_t *)take(sizeof(int64_t) * d.npairs);
+  r.tile_off = (int64_t *)take(sizeof(int64_t) * d.npairs);
+  r.slot_of = (int64_t *)take(sizeof(int64_t) * d.npairs);
+  r.pairs_nz = (int *)take(sizeof(int) * d.npairs);
+  r.tot = (int64_t *)take(sizeof(int64_t) * 4);
+  r.info = (DtcBatch *)take(sizeof(DtcBatch));
+  r.scan_tmp = take(d.scan_b);
+  r.As = (__nv_bfloat16 *)take((size_t)OZ_SLICES * d.rowsA * d.Kx * 2);
+  r.eA = (int *)take(sizeof(int) * (size_t)d.nchx * d.rowsA);
+  r.Us = (__nv_bfloat16 *)take((size_t)OZ_SLICES * d.rowsU * d.Kx * 2);
+  r.eU = (int *)take(sizeof(int) * (size_t)d.nchx * d.rowsU);
+  r.items = (int4 *)take(sizeof(int4) * (size_t)DTC_NT * d.nct);
+  r.Z = (double *)take(sizeof(double) * (size_t)d.Tcap * d.nbp * d.P2);
+  r.tri = (int *)take(sizeof(int) * 3 * (size_t)d.Tcap);
+  r.z = (double *)take(sizeof(double) * (size_t)d.Tcap);
+  r.Xb = (double *)take(sizeof(double) * (size_t)d.Tcap * d.n_prim);
+  r.Yb = (double *)take(sizeof(double) * (size_t)d.Tcap * d.n_late);
+  r.end = w;
+  return r;
+}
+
+bool tc_direct_supported(int nb_prim) { return nb_prim >= 1 && nb_prim <= DTC_MAXNB; }
+
+size_t tc_direct_scratch_bytes(const modal_problem *p, int ng) {
+  const DtcShape d = dtc_shape(p, ng);
+  return (size_t)(dtc_scratch(nullptr, d).end - (char *)nullptr) + 256;
+}
+
+#define DTC_CK(call, what)                                                         \
+  do {                                                                             \
+    const cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                       \
+      snprintf(g_tc_err, sizeof g_tc_err, "%s: %s", what, cudaGetErrorString(e_)); \
+      return MODAL_ECUDA;                                                          \
+    }                                                                              \
+  } while (0)
+
+int tc_project_direct(const modal_problem *p, const int *grid, const double *dw, int ng, int mode, double *gamma,
+                      void *scratch, int num_sms, long long wc, cudaStream_t st, Profiler *prof) {
+  if (!tc_direct_supported(p->nb_prim)) {
+    snprintf(g_tc_err, sizeof g_tc_err, "the tensor-core radial integrals take at most %d primordial functions",
+             DTC_MAXNB);
+    return MODAL_EUNSUPPORTED;
+  }
+  const DtcShape d = dtc_shape(p, ng);
+  const DtcScratch s = dtc_scratch(scratch, d);
+  int *words = s.words;
+  DTC_CK(cudaMemsetAsync(words, 0, sizeof(int), st), "status reset");
+  DTC_CK(launch_zero(gamma, (size_t)d.n_late * d.n_prim, st), "zero");
+  {
+    ProfScope ps(prof, "dtc_setup", st);
+    DTC_CK(launch_threej_table(d.cmax, s.ctab, st), "3j table");
+    k_dtc_classes<<<1, 32, 0, st>>>(ng, grid, mode, s.crow, s.cls);
+    k_dtc_count<<<(unsigned)cdiv64(d.npairs, 256), 256, 0, st>>>(ng, grid, s.crow, s.cls, mode, d.cpt, s.tri_cnt,
+                                                                  s.tile_cnt, s.nz_cnt);
+    DTC_CK(cudaGetLastError(), "count");
+    DTC_CK(scan_exclusive_i64(s.scan_tmp, d.scan_b, s.tri_cnt, s.tri_off, d.npairs, st), "scan");
+    DTC_CK(scan_exclusive_i64(s.scan_tmp, d.scan_b, s.tile_cnt, s.tile_off, d.npairs, st), "scan");
+    DTC_CK(scan_exclusive_i64(s.scan_tmp, d.scan_b, s.nz_cnt, s.slot_of, d.npairs, st), "scan");
+    k_dtc_totals<<<1, 32, 0, st>>>(d.npairs, s.tri_cnt, s.tri_off, s.tile_cnt, s.tile_off, s.nz_cnt, s.slot_of,
+                                   s.tot);
+    k_dtc_compact<<<(unsigned)cdiv64(d.npairs, 256), 256, 0, st>>>(d.npairs, s.nz_cnt, s.slot_of, s.pairs_nz);
+    DTC_CK(cudaGetLastError(), "totals");
+  }
+  // the A operand: q~ rows of the grid in class order, once per call
+  k_reset_emax<<<1, 32, 0, st>>>(words + 3, 2);
+  if (int r = split_op(d.rowsA, (int64_t)d.n_x, d.Kx, OpQRows{p->qt, grid, s.crow, d.L, p->l_min, d.nbp}, s.As,
+                       s.eA, words + 3, words, st, prof, "dtc_split_q"))
+    return r;
+  DTC_CK(cudaFuncSetAttribute(k_dtc_make_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.u_smem), "attr");
+  const size_t x_smem = sizeof(double) * (size_t)d.nbp * d.P2;
+  DTC_CK(cudaFuncSetAttribute(k_dtc_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x_smem), "attr");
+  for (int64_t b = 0; b < d.nbatch; ++b) {
+    {
+      ProfScope ps(prof, "dtc_fill", st, 2);
+      k_dtc_info<<<1, 32, 0, st>>>(d.nct, d.cpt, d.npairs, s.tile_off, s.tri_off, s.slot_of, s.pairs_nz, s.tot,
+                                   s.info);
+      k_dtc_fill<<<(unsigned)cdiv64(d.Tcap, 256), 256, 0, st>>>(s.info, s.tri_off, d.npairs, ng, grid, s.crow, s.cls,
+                                                                 mode, dw, p->w_l, p->l_min, s.ctab, s.tri, s.z);
+      DTC_CK(cudaGetLastError(), "fill");
+    }
+    {
+      ProfScope ps(prof, "dtc_make_u", st, 2);
+      k_reset_emax<<<1, 32, 0, st>>>(words + 4, 1);
+      k_dtc_make_u<<<dim3(DTC_NP, d.nchx), 256, d.u_smem, st>>>(s.info, s.pairs_nz, ng, grid, p->l_min, d.L, d.nbp,
+                                                                 d.n_x, p->qt, p->x_w, d.P2, d.urows, d.Kx, d.xs,
+                                                                 d.rowsU, s.Us, s.eU, words + 4, words);
+      DTC_CK(cudaGetLastError(), "make_u");
+    }
+    {
+      ProfScope ps(prof, "dtc_items", st);
+      k_dtc_items<<<(unsigned)cdiv64(DTC_NT, 128), 128, 0, st>>>(s.info, s.tile_off, s.tri_off, s.slot_of, d.npairs,
+                                                                   ng, grid, s.crow, s.cls, mode, d.cpt, d.nbp, d.nct,
+                                                                   d.wu, d.urows, s.items);
+      DTC_CK(cudaGetLastError(), "items");
+    }
+    if (int r = grouped_gemm(s.As, s.eA, words + 3, d.rowsA, s.Us, s.eU, words + 4, d.rowsU, d.Kx, d.wu, s.items,
+                             &s.info->n_items, DTC_NT * d.nct, s.Z, d.nbp, d.P2, words, wc, num_sms, st, prof))
+      return r;
+    {
+      ProfScope ps(prof, "dtc_x", st);
+      k_dtc_x<<<(unsigned)d.Tcap, 256, x_smem, st>>>(s.info, s.Z, d.nbp, d.P2, p->prim_modes, d.n_prim, s.Xb,
+                                                      d.Tcap);
+      DTC_CK(cudaGetLastError(), "X");
+    }
+    {
+      ProfScope ps(prof, "direct_Y", st);
+      const int64_t ny = (int64_t)d.n_late * d.Tcap;
+      k_direct_Y<<<(unsigned)cdiv64(ny, 256), 256, 0, st>>>(d.nbl, d.L, p->l_min, p->q, s.tri, s.z, 0, (int)d.Tcap,
+                                                            &s.info->n_tri, 0, p->late_modes, d.n_late, s.Yb);
+      DTC_CK(cudaGetLastError(), "Y");
+    }
+    if (int r = tc_gemm_batch(d.n_late, d.n_prim, (int)d.Tcap, s.Yb, s.Xb, &s.info->n_tri, 0, gamma, d.n_prim,
+                              s.gscr, false, wc, st, prof))
+      return r;
+  }
+  return MODAL_OK;
+}
+#undef DTC_CK
 
 int *tc_error_word(void *scratch) { return (int *)scratch; }
 

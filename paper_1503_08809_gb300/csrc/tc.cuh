@@ -61,6 +61,14 @@ size_t tc_gemm_batch_scratch_bytes(int m, int n, int T);
 int tc_gemm_batch(int m, int n, int T, const double *A, const double *B, const int64_t *count, int64_t t0, double *C,
                   int64_t ldc, void *scratch, bool reset_status, long long wait_cycles, cudaStream_t st,
                   Profiler *prof = nullptr);
+// The direct form (Eq. 3D) with its radial integrals and its Gamma' update on
+// the tensor cores (exact-slicing GEMMs; pairs (l2, l3) grouped, see tc.cu):
+// gamma overwritten; status word tc_error_word(scratch).  Bases of at most 32
+// primordial functions (tc_direct_supported).
+bool tc_direct_supported(int nb_prim);
+size_t tc_direct_scratch_bytes(const modal_problem *p, int ng);
+int tc_project_direct(const modal_problem *p, const int *grid, const double *dw, int ng, int mode, double *gamma,
+                      void *scratch, int num_sms, long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
 // device status word of the tensor-core scratch (bit 0: a bounded wait gave up,
 // bit 1: a value outside the FP32 exponent range of the split operands)
 int *tc_error_word(void *scratch);

@@ -125,17 +125,20 @@ def test_direct_graph_capture(mg):
 TOL_TC = 1e-8
 
 
-def _tensor_handle(mg):
+def _tensor_handle(mg, level=1):
     h = mg.Handle()
-    mg.set_option(mg.OPT_DIRECT_TENSOR, 1, handle=h)
+    mg.set_option(mg.OPT_DIRECT_TENSOR, level, handle=h)
     return h
 
 
+# level 1: the Gamma' update on the tensor cores; level 2: the radial
+# integrals too (pairs (l2, l3) grouped into one GEMM each)
+@pytest.mark.parametrize("level", [1, 2])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_direct_tensor_update_sparse(mg, mode):
+def test_direct_tensor_update_sparse(mg, mode, level):
     P = syn.make_problem(160, 4, 9, seed=3, nb_prim=3)
     lg, dw = syn.sparse_l_grid(160)
-    h = _tensor_handle(mg)
+    h = _tensor_handle(mg, level)
     g = mg.project_direct(mg.DeviceProblem.from_host(P, handle=h), lg, dw, weight_mode=mode, handle=h)
     assert mg.handle_status(handle=h) == 0
     ref = oracle.direct(P, l_grid=lg, l_dw=dw, weight_mode=mode)
@@ -144,11 +147,13 @@ def test_direct_tensor_update_sparse(mg, mode):
     h.close()
 
 
-def test_direct_tensor_update_dense_and_edges(mg):
+@pytest.mark.parametrize("level", [1, 2])
+def test_direct_tensor_update_dense_and_edges(mg, level):
     """Dense grid (several 1024-triple chunks and a ragged last batch), then
-    an empty grid and a single-point grid on the same handle."""
+    an empty grid, a single-point grid and a grid whose triples all break
+    the triangle condition on the same handle."""
     P = syn.cpu_size()
-    h = _tensor_handle(mg)
+    h = _tensor_handle(mg, level)
     dp = mg.DeviceProblem.from_host(P, handle=h)
     g = mg.project_direct(dp, handle=h)
     assert normwise(g, oracle.direct(P)) < TOL_TC
@@ -156,17 +161,37 @@ def test_direct_tensor_update_dense_and_edges(mg):
     assert torch.count_nonzero(g) == 0
     g = mg.project_direct(dp, l_grid=np.array([4]), l_dw=np.array([2.5]), handle=h)
     assert normwise(g, oracle.direct(P, l_grid=np.array([4]), l_dw=np.array([2.5]))) < TOL_TC
+    g = mg.project_direct(dp, l_grid=np.array([2, 9]), l_dw=np.ones(2), handle=h)
+    ref = oracle.direct(P, l_grid=np.array([2, 9]), l_dw=np.ones(2))
+    assert np.abs(g.cpu().numpy() - ref).max() <= TOL_TC * np.abs(ref).max()
     assert mg.handle_status(handle=h) == 0
     h.close()
 
 
-def test_direct_tensor_update_planck_sparse_sampled(mg):
-    """Planck-scale sparse grid (31 batches of 32768 triples, the last one
-    ragged): sampled entries against the oracle and the whole matrix against
-    the FP64 GPU path."""
+@pytest.mark.parametrize("nb", [1, 32])
+def test_direct_tensor_integrals_basis_sizes(mg, nb):
+    """The radial integrals on the tensor cores at the smallest basis and at
+    the largest this form takes (32 functions: 5 column tiles of the {u,v}
+    rows, 4 triples per tile), against the oracle on few modes."""
+    P = syn.make_problem(60, 3 if nb == 32 else 2, 7, seed=11, nb_prim=nb)
+    lg, dw = syn.sparse_l_grid(60)
+    h = _tensor_handle(mg, 2)
+    g = mg.project_direct(mg.DeviceProblem.from_host(P, handle=h), lg, dw, handle=h).cpu().numpy()
+    assert mg.handle_status(handle=h) == 0
+    cols = np.unique(np.linspace(0, P.n_prim - 1, 40).astype(int))
+    ref = oracle.direct(P, l_grid=lg, l_dw=dw, prim=P.prim_modes[cols])
+    assert np.abs(g[:, cols] - ref).max() < TOL_TC * np.abs(ref).max()
+    h.close()
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_direct_tensor_update_planck_sparse_sampled(mg, level):
+    """Planck-scale sparse grid (many batches, the last one ragged): sampled
+    entries against the oracle and the whole matrix against the FP64 GPU
+    path."""
     P = syn.planck_size()
     lg, dw = syn.sparse_l_grid(P.l_max)
-    h = _tensor_handle(mg)
+    h = _tensor_handle(mg, level)
     dp = mg.DeviceProblem.from_host(P, handle=h)
     g = mg.project_direct(dp, lg, dw, handle=h).cpu().numpy()
     assert mg.handle_status(handle=h) == 0
