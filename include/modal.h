@@ -159,8 +159,9 @@ int modal_handle_status(modal_handle *h);
  *   ~1e-10 of max|Gamma'| instead of FP64 rounding; the radial integrals X
  *   stay FP64); 2 also forms the radial integrals there (triples grouped by
  *   (l2, l3): one GEMM of the grid's q~ rows with that pair's products
- *   W_x q~_u(l2) q~_v(l3) per pair; bases of up to 32 primordial functions,
- *   larger ones run as 1).  The call's status then also covers those GEMMs'
+ *   W_x q~_u(l2) q~_v(l3) per pair, and the l1 sums of each pair before a
+ *   GEMM over pairs; bases of up to 32 functions on either side, larger
+ *   ones run as 1).  The call's status then also covers those GEMMs'
  *   bounded waits and the exponent range of their operands
  *   (modal_handle_status).  0 (default): FP64 throughout.
  * MODAL_OPT_BATCH_STREAMS: concurrent streams of modal_project_separable_batched

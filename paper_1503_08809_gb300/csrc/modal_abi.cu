@@ -1152,7 +1152,7 @@ int modal_project_direct(modal_handle *h, const modal_problem *p, const int32_t 
     return MODAL_OK;
   }
   if (!l_grid) return fail(h, MODAL_EINVAL, "null l_grid");
-  if (h->opt_direct_tensor == 2 && tc_direct_supported(p->nb_prim)) {
+  if (h->opt_direct_tensor == 2 && tc_direct_supported(p->nb_late, p->nb_prim)) {
     // radial integrals and Gamma' update on the tensor cores
     void *scratch;
     if (int r = ws_get(h, 0, tc_direct_scratch_bytes(p, ng), &scratch)) return r;

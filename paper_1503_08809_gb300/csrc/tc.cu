@@ -3280,6 +3280,15 @@ int tc_gemm_batch(int m, int n, int T, const double *A, const double *B, const i
 // items of that grouped GEMM (OUT_MODE 3) are tiles of cpt = 128 / nbp
 // consecutive l1 of one pair times column tiles of the {u,v} rows.
 //
+// The late-time side is expanded along l1 as well:
+//   sum_perm q_a q_b q_c = q_a(l1) S_bc + q_b(l1) S_ac + q_c(l1) S_ab,
+//   S_bc = q_b(l2) q_c(l3) + q_c(l2) q_b(l3)   (a function of the pair),
+// so with W_pair[a][n'] = sum over the pair's triples of z q_a(l1) X[n'],
+//   Gu[{b,c}][(a, n')] = sum over pairs of S_bc W_pair[a][n'],
+//   Gamma'[(a,b,c)][n'] = Gu[{b,c}][(a,n')] + Gu[{a,c}][(b,n')] + Gu[{a,b}][(c,n')]:
+// the l1 sum runs at the width of the basis (nb_late x n_prim per triple)
+// and the large GEMM runs over pairs, not triples.
+//
 // Triples are numbered pair by pair (pairs i2 <= i3 in row-major order of
 // the grid indices, then l1 ascending) and processed in batches of at most
 // DTC_NT tiles and DTC_NP pairs, whose bounds are found on the device (a
@@ -3287,14 +3296,16 @@ int tc_gemm_batch(int m, int n, int T, const double *A, const double *B, const i
 //   info, fill   ranges of the batch; (l1, l2, l3) and weight z per triple
 //   make_u       the U rows of the batch's pairs, sliced
 //   items, GEMM  Z of every triple of the batch
-//   X, Y         radial integrals from Z; z times the late-time products
-//   Gamma'      += Y X^T on the exact-slicing GEMM (tc_gemm_batch)
-// The host bounds the number of batches by the tile bound (the pairs plus
-// C(ng + 2, 3) / cpt) and the pair bound; batches past the end do no work.
+//   X            radial integrals from Z
+//   W            the l1 sums of the batch's pairs (double-FP32)
+//   Gu          += S^T W over the batch's pairs (exact-slicing GEMM)
+// then Gamma' from Gu.  The host bounds the number of batches by the tile
+// bound (the pairs plus C(ng + 2, 3) / cpt) and the pair bound; batches
+// past the end do no work.
 // ===========================================================================
 constexpr int DTC_NT = 4096;   // tiles per batch (at most)
 constexpr int DTC_NP = 1024;   // pairs per batch (at most)
-constexpr int DTC_MAXNB = 32;  // primordial functions of this form (Z block of a triple in shared memory)
+constexpr int DTC_MAXNB = 32;  // basis functions of this form (Z block of a triple in shared memory; W sums)
 
 struct DtcBatch {
   int64_t t0, nt;          // tiles [t0, t0 + nt) (nt = 0: past the end)
@@ -3591,10 +3602,10 @@ __global__ void k_dtc_items(const DtcBatch *__restrict__ info, const int64_t *__
     items[j * nct + h] = make_int4(k * nbp, slot * urows + h * wu, tri0, n | (h * wu) << 16);
 }
 
-// X[m][tb] of the batch's triples from their Z blocks (one triple per block)
+// X[tb][m] of the batch's triples from their Z blocks (one triple per block)
 __global__ void __launch_bounds__(256) k_dtc_x(const DtcBatch *__restrict__ info, const double *__restrict__ Z,
                                                int nbp, int P2, const int *__restrict__ prim, int n_prim,
-                                               double *__restrict__ Xb, int64_t Tcap) {
+                                               double *__restrict__ Xb) {
   const int64_t tb = blockIdx.x;
   if (tb >= info->n_tri) return;
   extern __shared__ double dx_sm[];  // [nbp][P2]
@@ -3608,8 +3619,142 @@ __global__ void __launch_bounds__(256) k_dtc_x(const DtcBatch *__restrict__ info
       v = __longlong_as_double(0x7ff8000000000000LL);
     else
       v = dx_sm[p * P2 + pair_index(r, s)] + dx_sm[r * P2 + pair_index(p, s)] + dx_sm[s * P2 + pair_index(p, r)];
-    Xb[m * Tcap + tb] = v;
+    Xb[tb * n_prim + m] = v;
   }
+}
+
+// acc += c x in double-FP32 (c, x double-FP32; acc unnormalised)
+__device__ __forceinline__ void dtc_df_fma(f2 &acc, f2 c, f2 x) {
+  const float p = __fmul_rn(c.h, x.h);
+  const float e = fmaf(c.h, x.l, fmaf(c.l, x.h, fmaf(c.h, x.h, -p)));
+  const float t = __fadd_rn(acc.h, p);
+  const float bb = __fsub_rn(t, acc.h);
+  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
+  acc.h = t;
+}
+
+// W[(a, m)][s] = sum over the batch's triples of pair slot s of z q_a(l1) X[tb][m]:
+// block (slot, DTC_WTH modes m); the weights z q_a(l1) of DTC_WCH triples at
+// a time in shared memory, the nb_late sums of each m in registers, the X
+// values of four triples loaded ahead of their use.
+// NB = nb_late rounded up to a multiple of 4 (weights of the extra rows are 0).
+constexpr int DTC_WCH = 64, DTC_WTH = 256;
+template <int NB>
+__device__ __forceinline__ void dtc_w_step(f2 (&acc)[NB], const f2 *c, double xd) {
+  const f2 x = df_from_d_fast(xd);
+#pragma unroll
+  for (int a = 0; a < NB; ++a) dtc_df_fma(acc[a], c[a], x);
+}
+template <int NB>
+__global__ void __launch_bounds__(DTC_WTH) k_dtc_w(const DtcBatch *__restrict__ info,
+                                                   const int *__restrict__ pairs_nz,
+                                                   const int64_t *__restrict__ tri_off,
+                                                   const int64_t *__restrict__ tri_cnt, const int *__restrict__ tri,
+                                                   const double *__restrict__ z, const double *__restrict__ q, int L,
+                                                   int l_min, int nbl, const double *__restrict__ X, int n_prim,
+                                                   double *__restrict__ W, int NPK, int *__restrict__ err) {
+  const int s = blockIdx.x;
+  if (s >= info->nslots) return;
+  __shared__ f2 cs[DTC_WCH][DTC_MAXNB];
+  const int pair = pairs_nz[info->slot0 + s];
+  const int64_t b0 = info->trip0, b1 = b0 + info->n_tri;
+  const int64_t g0 = max(tri_off[pair], b0), g1 = min(tri_off[pair] + tri_cnt[pair], b1);
+  const int m = blockIdx.y * DTC_WTH + threadIdx.x;
+  const int mc = min(m, n_prim - 1);  // threads past n_prim load a valid address and store nothing
+  f2 acc[NB];
+#pragma unroll
+  for (int a = 0; a < NB; ++a) acc[a] = f2{0.f, 0.f};
+  for (int64_t c0 = g0; c0 < g1; c0 += DTC_WCH) {
+    const int nc = (int)min((int64_t)DTC_WCH, g1 - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * NB; e += blockDim.x) {
+      const int j = e / NB, a = e - j * NB;
+      const int64_t tb = c0 + j - b0;
+      cs[j][a] = a < nbl ? df_from_d_fast(z[tb] * q[(int64_t)a * L + (tri[3 * tb] - l_min)]) : f2{0.f, 0.f};
+    }
+    __syncthreads();
+    const double *xr = X + (c0 - b0) * n_prim + mc;
+    int j = 0;
+    for (; j + 4 <= nc; j += 4) {
+      const double x0 = __ldg(xr + (int64_t)j * n_prim), x1 = __ldg(xr + (int64_t)(j + 1) * n_prim);
+      const double x2 = __ldg(xr + (int64_t)(j + 2) * n_prim), x3 = __ldg(xr + (int64_t)(j + 3) * n_prim);
+      dtc_w_step<NB>(acc, cs[j], x0);
+      dtc_w_step<NB>(acc, cs[j + 1], x1);
+      dtc_w_step<NB>(acc, cs[j + 2], x2);
+      dtc_w_step<NB>(acc, cs[j + 3], x3);
+    }
+    for (; j < nc; ++j) dtc_w_step<NB>(acc, cs[j], __ldg(xr + (int64_t)j * n_prim));
+  }
+  if (m < n_prim) {
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+      if (a < nbl) {
+        bad = bad || !(fabsf(acc[a].h) < 1e37f);
+        W[((int64_t)a * n_prim + m) * NPK + s] = (double)acc[a].h + (double)acc[a].l;
+      }
+    if (bad) atomicOr(err, ERR_RANGE);
+  }
+}
+
+using DtcWKernel = void (*)(const DtcBatch *, const int *, const int64_t *, const int64_t *, const int *,
+                            const double *, const double *, int, int, int, const double *, int, double *, int, int *);
+static DtcWKernel dtc_w_kernel(int nbl) {
+  switch ((nbl + 3) / 4) {
+    case 1: return k_dtc_w<4>;
+    case 2: return k_dtc_w<8>;
+    case 3: return k_dtc_w<12>;
+    case 4: return k_dtc_w<16>;
+    case 5: return k_dtc_w<20>;
+    case 6: return k_dtc_w<24>;
+    case 7: return k_dtc_w<28>;
+    default: return k_dtc_w<32>;
+  }
+}
+
+// Operands of the Gu GEMM: rows {b, c} of S over the batch's pair slots, and
+// the rows (a, m) of W; zero beyond the batch's slots.
+struct OpSPairs {
+  const DtcBatch *info;
+  const int *pairs_nz, *grid;
+  const double *q;
+  int ng, L, l_min;
+  __device__ bool empty() const { return info->nslots <= 0; }
+  __device__ double val(int64_t r, int64_t k) const {
+    if (k >= info->nslots) return 0.0;
+    const int pair = pairs_nz[info->slot0 + k];
+    int b, c;
+    pair_decode((int)r, b, c);
+    const int k2 = grid[pair / ng] - l_min, k3 = grid[pair % ng] - l_min;
+    const double *qb = q + (int64_t)b * L, *qc = q + (int64_t)c * L;
+    return qb[k2] * qc[k3] + qc[k2] * qb[k3];
+  }
+};
+struct OpWRows {
+  const DtcBatch *info;
+  const double *W;
+  int NPK;
+  __device__ bool empty() const { return info->nslots <= 0; }
+  __device__ double val(int64_t r, int64_t k) const { return k < info->nslots ? W[r * NPK + k] : 0.0; }
+};
+
+// Gamma'[n][m] = Gu[{b,c}][(a,m)] + Gu[{a,c}][(b,m)] + Gu[{a,b}][(c,m)] for late mode n = (a, b, c)
+__global__ void k_dtc_gather(const double *__restrict__ Gu, int nbl, int n_prim, const int *__restrict__ late,
+                             int n_late, double *__restrict__ gamma) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n_late * n_prim) return;
+  const int n = (int)(idx / n_prim), m = (int)(idx % n_prim);
+  const int a = late[3 * n], b = late[3 * n + 1], c = late[3 * n + 2];
+  double v;
+  if ((unsigned)a >= (unsigned)nbl || (unsigned)b >= (unsigned)nbl || (unsigned)c >= (unsigned)nbl) {
+    v = __longlong_as_double(0x7ff8000000000000LL);
+  } else {
+    const int64_t rw = (int64_t)nbl * n_prim;
+    v = Gu[pair_index(b, c) * rw + (int64_t)a * n_prim + m] + Gu[pair_index(a, c) * rw + (int64_t)b * n_prim + m] +
+        Gu[pair_index(a, b) * rw + (int64_t)c * n_prim + m];
+  }
+  gamma[idx] = v;
 }
 
 // The grouped GEMM: one CTA per SM, items taken in a fixed stride.
@@ -3655,8 +3800,8 @@ static int grouped_gemm(const __nv_bfloat16 *As, const int *eA, const int *emaxA
 
 // Shapes and scratch of the form.
 struct DtcShape {
-  int ng, nbp, nbl, n_x, L, n_late, n_prim, P2, cpt, nct, wu, urows, Kx, nchx, xs, cmax;
-  int64_t npairs, Tcap, rowsA, rowsU, nbatch;
+  int ng, nbp, nbl, n_x, L, n_late, n_prim, P2, P2l, cpt, nct, wu, urows, Kx, nchx, xs, cmax;
+  int64_t npairs, Tcap, rowsA, rowsU, rowsW, nbatch;
   size_t scan_b, u_smem;
 };
 static DtcShape dtc_shape(const modal_problem *p, int ng) {
@@ -3669,6 +3814,7 @@ static DtcShape dtc_shape(const modal_problem *p, int ng) {
   d.n_late = p->n_late;
   d.n_prim = p->n_prim;
   d.P2 = d.nbp * (d.nbp + 1) / 2;
+  d.P2l = d.nbl * (d.nbl + 1) / 2;
   d.cpt = OZ_BM / d.nbp;
   d.nct = (int)cdiv64(d.P2, OZ_BN);
   d.wu = g_tile_width(d.P2);
@@ -3681,6 +3827,7 @@ static DtcShape dtc_shape(const modal_problem *p, int ng) {
   d.Tcap = (int64_t)DTC_NT * d.cpt;
   d.rowsA = (int64_t)ng * d.nbp;
   d.rowsU = (int64_t)DTC_NP * d.urows;
+  d.rowsW = (int64_t)d.nbl * d.n_prim;
   // batches: each ends at DTC_NT tiles, at DTC_NP pairs, or at the end
   const int64_t pairs_sorted = (int64_t)ng * (ng + 1) / 2;
   const int64_t tiles_bound = pairs_sorted + (int64_t)ng * (ng + 1) * (ng + 2) / 6 / d.cpt;
@@ -3691,23 +3838,22 @@ static DtcShape dtc_shape(const modal_problem *p, int ng) {
 }
 
 struct DtcScratch {
-  int *words;  // [0] status (shared with the Gamma' GEMM), [3] A and [4] U exponent maxima
-  double *ctab, *Z, *z, *Xb, *Yb;
+  int *words;  // [0] status, exponent maxima: [3] q~ rows, [4] U, [5] S, [6] W
+  double *ctab, *Z, *z, *Xb, *W, *Gu;
   int *crow, *cls, *pairs_nz, *tri;
   int64_t *tri_cnt, *tile_cnt, *nz_cnt, *tri_off, *tile_off, *slot_of, *tot;
   DtcBatch *info;
   int4 *items;
-  void *scan_tmp, *gscr;
-  __nv_bfloat16 *As, *Us;
-  int *eA, *eU;
+  void *scan_tmp;
+  __nv_bfloat16 *As, *Us, *Ss, *Ws;
+  int *eA, *eU, *eS, *eW;
   char *end;
 };
 static DtcScratch dtc_scratch(void *base, const DtcShape &d) {
   DtcScratch r{};
   char *w = (char *)base;
-  r.gscr = w;  // the Gamma' GEMM's scratch first: its status word is the call's
-  w += up256(tc_gemm_batch_scratch_bytes(d.n_late, d.n_prim, (int)d.Tcap));
-  r.words = (int *)r.gscr;
+  r.words = (int *)w;
+  w += 1024;
   auto take = [&](size_t bytes) {
     char *p = w;
     w += up256(bytes);
@@ -3735,12 +3881,20 @@ static DtcScratch dtc_scratch(void *base, const DtcShape &d) {
   r.tri = (int *)take(sizeof(int) * 3 * (size_t)d.Tcap);
   r.z = (double *)take(sizeof(double) * (size_t)d.Tcap);
   r.Xb = (double *)take(sizeof(double) * (size_t)d.Tcap * d.n_prim);
-  r.Yb = (double *)take(sizeof(double) * (size_t)d.Tcap * d.n_late);
+  r.W = (double *)take(sizeof(double) * (size_t)d.rowsW * DTC_NP);
+  r.Ss = (__nv_bfloat16 *)take((size_t)OZ_SLICES * d.P2l * DTC_NP * 2);
+  r.eS = (int *)take(sizeof(int) * (size_t)d.P2l);
+  r.Ws = (__nv_bfloat16 *)take((size_t)OZ_SLICES * d.rowsW * DTC_NP * 2);
+  r.eW = (int *)take(sizeof(int) * (size_t)d.rowsW);
+  r.Gu = (double *)take(sizeof(double) * (size_t)d.P2l * d.rowsW);
   r.end = w;
   return r;
 }
 
-bool tc_direct_supported(int nb_prim) { return nb_prim >= 1 && nb_prim <= DTC_MAXNB; }
+static_assert(DTC_NP % OZ_BK == 0 && DTC_NP <= OZ_KC, "the pair slots of a batch are one exact K chunk");
+bool tc_direct_supported(int nb_late, int nb_prim) {
+  return nb_late >= 1 && nb_late <= DTC_MAXNB && nb_prim >= 1 && nb_prim <= DTC_MAXNB;
+}
 
 size_t tc_direct_scratch_bytes(const modal_problem *p, int ng) {
   const DtcShape d = dtc_shape(p, ng);
@@ -3758,8 +3912,8 @@ size_t tc_direct_scratch_bytes(const modal_problem *p, int ng) {
 
 int tc_project_direct(const modal_problem *p, const int *grid, const double *dw, int ng, int mode, double *gamma,
                       void *scratch, int num_sms, long long wc, cudaStream_t st, Profiler *prof) {
-  if (!tc_direct_supported(p->nb_prim)) {
-    snprintf(g_tc_err, sizeof g_tc_err, "the tensor-core radial integrals take at most %d primordial functions",
+  if (!tc_direct_supported(p->nb_late, p->nb_prim)) {
+    snprintf(g_tc_err, sizeof g_tc_err, "the tensor-core direct form takes bases of at most %d functions",
              DTC_MAXNB);
     return MODAL_EUNSUPPORTED;
   }
@@ -3767,7 +3921,7 @@ int tc_project_direct(const modal_problem *p, const int *grid, const double *dw,
   const DtcScratch s = dtc_scratch(scratch, d);
   int *words = s.words;
   DTC_CK(cudaMemsetAsync(words, 0, sizeof(int), st), "status reset");
-  DTC_CK(launch_zero(gamma, (size_t)d.n_late * d.n_prim, st), "zero");
+  DTC_CK(launch_zero(s.Gu, (size_t)d.P2l * d.rowsW, st), "zero");
   {
     ProfScope ps(prof, "dtc_setup", st);
     DTC_CK(launch_threej_table(d.cmax, s.ctab, st), "3j table");
@@ -3820,20 +3974,33 @@ int tc_project_direct(const modal_problem *p, const int *grid, const double *dw,
       return r;
     {
       ProfScope ps(prof, "dtc_x", st);
-      k_dtc_x<<<(unsigned)d.Tcap, 256, x_smem, st>>>(s.info, s.Z, d.nbp, d.P2, p->prim_modes, d.n_prim, s.Xb,
-                                                      d.Tcap);
+      k_dtc_x<<<(unsigned)d.Tcap, 256, x_smem, st>>>(s.info, s.Z, d.nbp, d.P2, p->prim_modes, d.n_prim, s.Xb);
       DTC_CK(cudaGetLastError(), "X");
     }
     {
-      ProfScope ps(prof, "direct_Y", st);
-      const int64_t ny = (int64_t)d.n_late * d.Tcap;
-      k_direct_Y<<<(unsigned)cdiv64(ny, 256), 256, 0, st>>>(d.nbl, d.L, p->l_min, p->q, s.tri, s.z, 0, (int)d.Tcap,
-                                                            &s.info->n_tri, 0, p->late_modes, d.n_late, s.Yb);
-      DTC_CK(cudaGetLastError(), "Y");
+      ProfScope ps(prof, "dtc_w", st);
+      dtc_w_kernel(d.nbl)<<<dim3(DTC_NP, (unsigned)cdiv64(d.n_prim, DTC_WTH)), DTC_WTH, 0, st>>>(
+          s.info, s.pairs_nz, s.tri_off, s.tri_cnt, s.tri, s.z, p->q, d.L, p->l_min, d.nbl, s.Xb, d.n_prim, s.W,
+          DTC_NP, words);
+      DTC_CK(cudaGetLastError(), "W");
     }
-    if (int r = tc_gemm_batch(d.n_late, d.n_prim, (int)d.Tcap, s.Yb, s.Xb, &s.info->n_tri, 0, gamma, d.n_prim,
-                              s.gscr, false, wc, st, prof))
+    k_reset_emax<<<1, 32, 0, st>>>(words + 5, 2);
+    if (int r = split_op((int64_t)d.P2l, (int64_t)DTC_NP, DTC_NP,
+                         OpSPairs{s.info, s.pairs_nz, grid, p->q, ng, d.L, p->l_min}, s.Ss, s.eS, words + 5, words,
+                         st, prof, "dtc_split_sw"))
       return r;
+    if (int r = split_op(d.rowsW, (int64_t)DTC_NP, DTC_NP, OpWRows{s.info, s.W, DTC_NP}, s.Ws, s.eW, words + 6,
+                         words, st, prof, "dtc_split_sw"))
+      return r;
+    if (int r = dense_gemm(s.Ss, s.eS, words + 5, d.P2l, s.Ws, s.eW, words + 6, d.rowsW, DTC_NP, s.Gu, d.rowsW, 1,
+                           true, words, wc, st, prof, "dtc_gemm_gu", &s.info->nslots, 0))
+      return r;
+  }
+  {
+    ProfScope ps(prof, "dtc_gather", st);
+    k_dtc_gather<<<(unsigned)cdiv64((int64_t)d.n_late * d.n_prim, 256), 256, 0, st>>>(s.Gu, d.nbl, d.n_prim,
+                                                                                     p->late_modes, d.n_late, gamma);
+    DTC_CK(cudaGetLastError(), "gather");
   }
   return MODAL_OK;
 }

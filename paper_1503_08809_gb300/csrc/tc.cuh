@@ -64,8 +64,8 @@ int tc_gemm_batch(int m, int n, int T, const double *A, const double *B, const i
 // The direct form (Eq. 3D) with its radial integrals and its Gamma' update on
 // the tensor cores (exact-slicing GEMMs; pairs (l2, l3) grouped, see tc.cu):
 // gamma overwritten; status word tc_error_word(scratch).  Bases of at most 32
-// primordial functions (tc_direct_supported).
-bool tc_direct_supported(int nb_prim);
+// functions on either side (tc_direct_supported).
+bool tc_direct_supported(int nb_late, int nb_prim);
 size_t tc_direct_scratch_bytes(const modal_problem *p, int ng);
 int tc_project_direct(const modal_problem *p, const int *grid, const double *dw, int ng, int mode, double *gamma,
                       void *scratch, int num_sms, long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
