@@ -93,7 +93,8 @@ def parse():
     ap.add_argument("--once", action="store_true",
                     help="run one projection and exit (a small case for profiler captures)")
     ap.add_argument("--fp64-x", type=int, default=20,
-                    help="radial points of the plain-FP64 comparison run (0: skip)")
+                    help="radial points of the plain-FP64 comparison run (0: skip; for the direct "
+                         "workload, 0 skips its FP64 comparison call)")
     return ap.parse_args()
 
 
@@ -674,7 +675,7 @@ def run_extra(args):
     if args.workload == "direct":
         prof = profiled(h, step, dev)
         cfg["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
-        if args.direct_tensor:                  # the same call in FP64 throughout, for the error
+        if args.direct_tensor and args.fp64_x:  # the same call in FP64 throughout, for the error
             mg.handle_status(handle=h)
             g = gdir.clone()
             mg.set_option(mg.OPT_DIRECT_TENSOR, 0, handle=h)

@@ -240,15 +240,29 @@ __global__ void k_x_weights(int kind, int n, const double *__restrict__ x, doubl
 // Ratio table c_n = prod_{k=1..n} (1 - 1/(2k)), n = 0..nmax, each entry in
 // double-double then rounded: (l1 l2 l3;000)^2 = c_{g-l1} c_{g-l2} c_{g-l3} /
 // ((2g+1) c_g) with 2g = l1 + l2 + l3 (the factorial form, Section 2.1).
-__global__ void k_threej_table(int nmax, double *__restrict__ c) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n > nmax) return;
-  dd p = {1.0, 0.0};
-  for (int k = 1; k <= n; ++k) {
-    // 1 - 1/(2k) = (2k - 1)/(2k): exact numerator, one dd division
-    p = dd_div_d(dd_mul_d(p, 2.0 * k - 1.0), 2.0 * k);
+// One CTA: the factors go in blocks of TJ_B; the products of the blocks, their
+// running products, then each entry as its block's running product times the
+// factors of its own block up to n (at most TJ_B double-double steps per
+// thread and phase instead of n).
+constexpr int TJ_B = 32, TJ_MAXBLK = 1024;
+__device__ __forceinline__ dd tj_factors(dd p, int k0, int k1) {  // p prod_{k0 <= k <= k1} (2k - 1)/(2k)
+  for (int k = k0; k <= k1; ++k) p = dd_div_d(dd_mul_d(p, 2.0 * k - 1.0), 2.0 * k);
+  return p;
+}
+__global__ void __launch_bounds__(1024) k_threej_table(int nmax, double *__restrict__ c) {
+  __shared__ dd run[TJ_MAXBLK];  // run[b] = product of the factors 1 .. b TJ_B
+  const int nblk = nmax / TJ_B + 1;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    run[b] = b == 0 ? dd{1.0, 0.0} : tj_factors(dd{1.0, 0.0}, (b - 1) * TJ_B + 1, b * TJ_B);
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int b = 1; b < nblk; ++b) run[b] = dd_mul(run[b - 1], run[b]);
+  __syncthreads();
+  for (int n = threadIdx.x; n <= nmax; n += blockDim.x) {
+    const int b = n / TJ_B;
+    const dd p = tj_factors(run[b], b * TJ_B + 1, n);
+    c[n] = p.hi + p.lo;
   }
-  c[n] = p.hi + p.lo;
 }
 
 // ---- launchers -------------------------------------------------------------
@@ -271,7 +285,8 @@ cudaError_t launch_x_weights(int kind, int n, const double *x, double *w, cudaSt
   return cudaGetLastError();
 }
 cudaError_t launch_threej_table(int nmax, double *c, cudaStream_t st) {
-  k_threej_table<<<cdiv(nmax + 1, 128), 128, 0, st>>>(nmax, c);
+  if (nmax / TJ_B + 1 > TJ_MAXBLK) return cudaErrorInvalidValue;  // l_max beyond ~21800
+  k_threej_table<<<1, 1024, 0, st>>>(nmax, c);
   return cudaGetLastError();
 }
 

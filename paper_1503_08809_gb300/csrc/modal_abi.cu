@@ -1152,6 +1152,7 @@ int modal_project_direct(modal_handle *h, const modal_problem *p, const int32_t 
     return MODAL_OK;
   }
   if (!l_grid) return fail(h, MODAL_EINVAL, "null l_grid");
+  if (p->l_max > 21000) return fail(h, MODAL_EUNSUPPORTED, "l_max > 21000 is not supported by the direct form");
   if (h->opt_direct_tensor == 2 && tc_direct_supported(p->nb_late, p->nb_prim)) {
     // radial integrals and Gamma' update on the tensor cores
     void *scratch;

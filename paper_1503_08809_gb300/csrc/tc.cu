@@ -3608,9 +3608,25 @@ __global__ void __launch_bounds__(256) k_dtc_x(const DtcBatch *__restrict__ info
                                                double *__restrict__ Xb) {
   const int64_t tb = blockIdx.x;
   if (tb >= info->n_tri) return;
-  extern __shared__ double dx_sm[];  // [nbp][P2]
-  const double *zb = Z + tb * nbp * P2;
-  for (int i = threadIdx.x; i < nbp * P2; i += blockDim.x) dx_sm[i] = zb[i];
+  extern __shared__ __align__(16) double dx_sm[];  // [nbp][P2]
+  const int nz = nbp * P2;
+  const double *zb = Z + tb * nz;
+  if ((nz & 1) == 0) {  // the block starts on a 16-byte boundary: 16-byte loads, four in flight per thread
+    const double2 *z2 = reinterpret_cast<const double2 *>(zb);
+    double2 *s2 = reinterpret_cast<double2 *>(dx_sm);
+    const int n2 = nz / 2;
+    int i = threadIdx.x;
+    for (; i + 3 * (int)blockDim.x < n2; i += 4 * blockDim.x) {
+      const double2 v0 = z2[i], v1 = z2[i + blockDim.x], v2 = z2[i + 2 * blockDim.x], v3 = z2[i + 3 * blockDim.x];
+      s2[i] = v0;
+      s2[i + blockDim.x] = v1;
+      s2[i + 2 * blockDim.x] = v2;
+      s2[i + 3 * blockDim.x] = v3;
+    }
+    for (; i < n2; i += blockDim.x) s2[i] = z2[i];
+  } else {
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) dx_sm[i] = zb[i];
+  }
   __syncthreads();
   for (int m = threadIdx.x; m < n_prim; m += blockDim.x) {
     const int p = prim[3 * m], r = prim[3 * m + 1], s = prim[3 * m + 2];
@@ -3643,11 +3659,16 @@ constexpr int DTC_WCH = 64, DTC_WTH = 256;
 template <int NB>
 __device__ __forceinline__ void dtc_w_step(f2 (&acc)[NB], const f2 *c, double xd) {
   const f2 x = df_from_d_fast(xd);
+  const float4 *c4 = reinterpret_cast<const float4 *>(c);  // two weights per 16-byte load
 #pragma unroll
-  for (int a = 0; a < NB; ++a) dtc_df_fma(acc[a], c[a], x);
+  for (int a = 0; a < NB; a += 2) {
+    const float4 v = c4[a / 2];
+    dtc_df_fma(acc[a], f2{v.x, v.y}, x);
+    dtc_df_fma(acc[a + 1], f2{v.z, v.w}, x);
+  }
 }
 template <int NB>
-__global__ void __launch_bounds__(DTC_WTH) k_dtc_w(const DtcBatch *__restrict__ info,
+__global__ void __launch_bounds__(DTC_WTH, 2) k_dtc_w(const DtcBatch *__restrict__ info,
                                                    const int *__restrict__ pairs_nz,
                                                    const int64_t *__restrict__ tri_off,
                                                    const int64_t *__restrict__ tri_cnt, const int *__restrict__ tri,
@@ -3656,7 +3677,7 @@ __global__ void __launch_bounds__(DTC_WTH) k_dtc_w(const DtcBatch *__restrict__ 
                                                    double *__restrict__ W, int NPK, int *__restrict__ err) {
   const int s = blockIdx.x;
   if (s >= info->nslots) return;
-  __shared__ f2 cs[DTC_WCH][DTC_MAXNB];
+  __shared__ __align__(16) f2 cs[DTC_WCH][DTC_MAXNB];
   const int pair = pairs_nz[info->slot0 + s];
   const int64_t b0 = info->trip0, b1 = b0 + info->n_tri;
   const int64_t g0 = max(tri_off[pair], b0), g1 = min(tri_off[pair] + tri_cnt[pair], b1);
