@@ -85,6 +85,8 @@ def parse():
                     help="tensor-core triple product GEMM as a persistent kernel over a work queue: 1")
     ap.add_argument("--tc-overlap", type=int, default=0,
                     help="SMs left to the Y pass running beside the queue GEMM (0: no overlap)")
+    ap.add_argument("--tc-split-k", type=int, default=0,
+                    help="K splits of the tensor-core triple GEMM (0: the library's choice)")
     ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1],
                     help="tensor-core triple product GEMM on CTA pairs (2-SM MMA): 1, or single CTAs: 0")
     ap.add_argument("--direct-tensor", type=int, default=0, choices=[0, 1, 2],
@@ -256,6 +258,7 @@ def run_ours(args):
     mg.set_option(mg.OPT_TC_PAIR, args.tc_pair, handle=h)
     mg.set_option(mg.OPT_TC_QUEUE, args.tc_queue, handle=h)
     mg.set_option(mg.OPT_TC_OVERLAP, args.tc_overlap, handle=h)
+    mg.set_option(mg.OPT_TC_SPLIT_K, args.tc_split_k, handle=h)
     dp = mg.DeviceProblem.from_host(P, device=dev, handle=h)
     gamma = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream(dev)
@@ -370,7 +373,10 @@ def run_ours(args):
                        "tc_gemm": ("CTA pairs (2-SM MMA)" if args.tc_pair else
                                    f"persistent work queue on {152 - args.tc_overlap} SMs, Y pass beside it"
                                    if args.tc_overlap else
-                                   "persistent work queue" if args.tc_queue else "one CTA per tile"),
+                                   "persistent work queue" if args.tc_queue else
+                                   "one CTA per tile (or per K range of a tile)" + (f", {args.tc_split_k} K splits"
+                                                                                     if args.tc_split_k else "")),
+                       "g_layout": "blocks by the middle index, each expanded along its wider side",
                        "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)",
                        "parallelism": (f"x-sharded over {ws} ranks, FP64 all-reduce of Gamma'" if sharded
                                        else f"{ws} independent problem(s)")},

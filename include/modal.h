@@ -132,7 +132,9 @@ int modal_handle_status(modal_handle *h);
  *   2 does so with sixteen warps from a TMA-staged tile of M~ rows (bases of
  *   up to ~21 functions; larger ones use 0).  All give the same results to
  *   rounding; 0 is the fastest at the sizes measured.
- * MODAL_OPT_TC_SPLIT_K: K splits of the shared-memory variant (0 = automatic).
+ * MODAL_OPT_TC_SPLIT_K: K splits of the triple GEMM (0 = automatic): of the
+ *   shared-memory variants, and (1 .. 4) of the one-CTA-per-tile form, whose
+ *   automatic choice models the waves of tiles on the SMs.
  * MODAL_OPT_TC_PAIR: 1 runs the triple-product GEMM of MODAL_OPT_TC_TRIPLE_FUSED = 0
  *   on CTA pairs (clusters of two, 2-SM tcgen05 MMA with M = 256: each SM
  *   reads half of the B operand); 0 on single CTAs.  Same results to rounding.

@@ -97,18 +97,30 @@ __host__ __device__ __forceinline__ void pair_decode(int uv, int &u, int &v) {
 
 // ---------------------------------------------------------------------------
 // Layout of the unsymmetrised triple-product table G used by the separable
-// path.  With Y_ab{u,v}(s) = w_s (M_au M_bv + M_av M_bu) for a <= b and
-// u <= v, the 3x3 permanent of Eq. 2D expands along the row of c as
-//   perm = Y_ab{p,r} M_cs + Y_ab{p,s} M_cr + Y_ab{r,s} M_cp,
-// so Gamma' needs only G[(a,b,{u,v}), (c,t)] = sum_s Y_ab{u,v}(s) M_ct(s)
-// for a <= b <= c.  Block b holds rows (a in [0,b], uv) and columns
-// (c in [b, nb_late), t): R_b = (b+1) P2 rows, C_b = (nb_late-b) nb_prim
-// columns, row-major, blocks stored one after the other.
+// path.  With Y_xy{u,v}(s) = w_s (M_xu M_yv + M_xv M_yu) for x <= y and
+// u <= v, the 3x3 permanent of Eq. 2D for a sorted late triple a <= b <= c
+// can be expanded along the row of c or along the row of a:
+//   perm = Y_ab{p,r} M_ct + Y_ab{p,t} M_cr + Y_ab{r,t} M_cp     (row of c)
+//        = Y_bc{p,r} M_at + Y_bc{p,t} M_ar + Y_bc{r,t} M_ap     (row of a).
+// G is stored in blocks by the middle index b.  Block b < h takes the first
+// form, G[(a, uv), (c, t)] = sum_s Y_ab{u,v}(s) M_ct(s): rows (a in [0, b],
+// uv), columns (c in [b, nb_late), t); block b >= h the second, G[(c, uv),
+// (a, t)] = sum_s Y_bc{u,v}(s) M_at(s): rows (c in [b, nb_late), uv), columns
+// (a in [0, b], t).  Either way a block has (b+1)(nb_late-b) P2 nb_prim
+// entries, row-major, blocks end to end.  h = nb_late gives the first form
+// throughout; h = (nb_late + 1) / 2 (make_glayout_split) keeps every block at
+// least (nb_late + 1) / 2 column groups wide and needs the Y rows of only the
+// pairs (a, b) with b < h and (b, c) with b >= h -- about half of them.  The
+// Y operand lists the pairs a block uses block by block (y_pair), so block
+// b's rows are the Y rows [ypair0(b) P2, ...) and its columns the M rows
+// [colstart(b), colstart(b) + cols(b)).
 // ---------------------------------------------------------------------------
 struct GLayout {
-  int nbl, nbp, P2;
-  __host__ __device__ int64_t rows(int b) const { return (int64_t)(b + 1) * P2; }
-  __host__ __device__ int64_t cols(int b) const { return (int64_t)(nbl - b) * nbp; }
+  int nbl, nbp, P2, h;
+  __host__ __device__ bool first(int b) const { return b < h; }
+  __host__ __device__ int64_t rows(int b) const { return (int64_t)(first(b) ? b + 1 : nbl - b) * P2; }
+  __host__ __device__ int64_t cols(int b) const { return (int64_t)(first(b) ? nbl - b : b + 1) * nbp; }
+  __host__ __device__ int64_t colstart(int b) const { return first(b) ? (int64_t)b * nbp : 0; }
   __host__ __device__ int64_t offset(int b) const {
     // sum_{i=1..b} i (nbl - i + 1) * P2 * nbp
     int64_t B = b;
@@ -116,11 +128,33 @@ struct GLayout {
     return s * P2 * nbp;
   }
   __host__ __device__ int64_t size() const { return offset(nbl); }
+  // pairs of Y rows used by block b, the first of them in Y order, and all of them
+  __host__ __device__ int ypairs(int b) const { return first(b) ? b + 1 : nbl - b; }
+  __host__ __device__ int ypair0(int b) const {
+    const int f = b < h ? b : h;  // blocks of the first form before b: 1 + 2 + ... + f pairs
+    const int n2 = b - f;         // blocks h .. b-1 of the second form: nbl-h + ... + nbl-b+1 pairs
+    return f * (f + 1) / 2 + n2 * (2 * nbl - 2 * h - n2 + 1) / 2;
+  }
+  __host__ __device__ int ypairs_total() const { return ypair0(nbl); }
+  // the pair x <= y of Y pair j (0 <= j < ypairs_total())
+  __host__ __device__ void y_pair(int j, int &x, int &y) const {
+    int b = 0;
+    while (b + 1 < nbl && ypair0(b + 1) <= j) ++b;
+    const int i = j - ypair0(b);
+    if (first(b)) {
+      x = i;
+      y = b;
+    } else {
+      x = b;
+      y = b + i;
+    }
+  }
   __host__ __device__ int64_t index(int a, int b, int uv, int c, int t) const {
 #ifdef MODAL_DEBUG
     return checked_index(a, b, uv, c, t);
 #else
-    return offset(b) + ((int64_t)a * P2 + uv) * cols(b) + (int64_t)(c - b) * nbp + t;
+    return first(b) ? offset(b) + ((int64_t)a * P2 + uv) * cols(b) + (int64_t)(c - b) * nbp + t
+                    : offset(b) + ((int64_t)(c - b) * P2 + uv) * cols(b) + (int64_t)a * nbp + t;
 #endif
   }
   // index() with every argument checked: 0 <= a <= b <= c < nbl,
@@ -128,10 +162,14 @@ struct GLayout {
   // builds with MODAL_DEBUG defined (callers then skip a negative index).
   __host__ __device__ int64_t checked_index(int a, int b, int uv, int c, int t) const {
     if (a < 0 || a > b || b > c || c >= nbl || uv < 0 || uv >= P2 || t < 0 || t >= nbp) return -1;
-    return offset(b) + ((int64_t)a * P2 + uv) * cols(b) + (int64_t)(c - b) * nbp + t;
+    return first(b) ? offset(b) + ((int64_t)a * P2 + uv) * cols(b) + (int64_t)(c - b) * nbp + t
+                    : offset(b) + ((int64_t)(c - b) * P2 + uv) * cols(b) + (int64_t)a * nbp + t;
   }
 };
 
-static inline GLayout make_glayout(int nbl, int nbp) { return GLayout{nbl, nbp, nbp * (nbp + 1) / 2}; }
+static inline GLayout make_glayout(int nbl, int nbp) { return GLayout{nbl, nbp, nbp * (nbp + 1) / 2, nbl}; }
+static inline GLayout make_glayout_split(int nbl, int nbp) {
+  return GLayout{nbl, nbp, nbp * (nbp + 1) / 2, (nbl + 1) / 2};
+}
 
 }  // namespace modal

@@ -358,8 +358,10 @@ template cudaError_t launch_triple<float>(const SepShape &, const float *, const
 
 // ---------------------------------------------------------------------------
 // a7: Gamma'[n][n'] = scale * (G[ab{pr}, c s] + G[ab{ps}, c r] + G[ab{rs}, c p])
-// with (a,b,c) the sorted late triple, scale = 1/(48 pi) (Eq. 2D).  Mode
-// indices outside the basis give NaN (no out-of-range read).
+// with (a,b,c) the sorted late triple, scale = 1/(48 pi) (Eq. 2D); in blocks
+// of the second form (GLayout) the same three index calls give the
+// expansion along the row of a.  Mode indices outside the basis give NaN (no
+// out-of-range read).
 // ---------------------------------------------------------------------------
 __global__ void k_gather(GLayout g, const double *__restrict__ G, const int *__restrict__ late,
                          const int *__restrict__ prim, int n_late, int n_prim, double scale,
@@ -388,8 +390,9 @@ __global__ void k_gather(GLayout g, const double *__restrict__ G, const int *__r
 }
 
 cudaError_t launch_gather(const SepShape &s, const double *G, const int *late, const int *prim,
-                          int n_late, int n_prim, double scale, double *gamma, cudaStream_t st) {
-  GLayout g = make_glayout(s.nbl, s.nbp);
+                          int n_late, int n_prim, double scale, double *gamma, cudaStream_t st,
+                          const GLayout *layout) {
+  const GLayout g = layout ? *layout : make_glayout(s.nbl, s.nbp);
   int64_t n = (int64_t)n_late * n_prim;
   if (n == 0) return cudaSuccess;
   k_gather<<<(unsigned)cdiv64(n, 256), 256, 0, st>>>(g, G, late, prim, n_late, n_prim, scale, gamma);

@@ -26,8 +26,10 @@ cudaError_t launch_triple(const SepShape &s, const T *M, const double *om, const
                           int nxc, int ksplit, double *G, double *Gpart, bool accumulate,
                           int num_sms, cudaStream_t st, bool absM = false);
 int triple_ksplit(const SepShape &s, int nxc, int num_sms);
+// layout: the G layout the triple product filled (NULL: make_glayout's)
 cudaError_t launch_gather(const SepShape &s, const double *G, const int *late, const int *prim,
-                          int n_late, int n_prim, double scale, double *gamma, cudaStream_t st);
+                          int n_late, int n_prim, double scale, double *gamma, cudaStream_t st,
+                          const GLayout *layout = nullptr);
 cudaError_t launch_zero(double *p, size_t n, cudaStream_t st);
 
 // generic K-major FP64 GEMM: C[m][n] (+)= sum_k A[m*lda + k] B[n*ldb + k]; with

@@ -683,11 +683,14 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
     h->err_pending = true;
   }
   PROFN(h, "gather", st, Gabs ? 2 : 1);
+  // the tensor-core triple product's layout of G depends on its variant
+  const GLayout gl = (pl.prec == MODAL_PREC_OZAKI_BF16 && !fa) ? tc_triple_glayout(s, pl.variant)
+                                                               : make_glayout(s.nbl, s.nbp);
   CK(launch_gather(s, G, p->late_modes, p->prim_modes, p->n_late, p->n_prim, 1.0 / (48.0 * MODAL_PI), gamma,
-                   st));                                                                    // a7
+                   st, &gl));                                                               // a7
   if (Gabs)
     CK(launch_gather(s, Gabs, p->late_modes, p->prim_modes, p->n_late, p->n_prim, 1.0 / (48.0 * MODAL_PI),
-                     pl.est, st));
+                     pl.est, st, &gl));
   return MODAL_OK;
 }
 

@@ -34,6 +34,7 @@
 #include <cstring>
 #include <algorithm>
 #include <mutex>
+#include <queue>
 #include <vector>
 
 #include "common.cuh"
@@ -254,6 +255,13 @@ struct OzParams {
   const int4 *items;
   const int *item_count;
   int P2, wtile;
+  // OUT_MODE 1: each tile's K chunks split over ksplit consecutive CTAs of
+  // chunks_per_split chunks each; the first adds its partial sums into out,
+  // part k >= 1 stores them at out_part + (k - 1) part_stride (added in
+  // order afterwards, so the result does not depend on which part ends first)
+  int ksplit, chunks_per_split;
+  double *out_part;
+  int64_t part_stride;
 };
 
 
@@ -300,6 +308,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   int ntile = OZ_BN;  // MMA N of this tile (a multiple of 16)
   int ntt = 1;  // tiles of this CTA (OUT_MODE 0: row tiles of one column tile)
   bool lead = true;  // the first column tile of its row tile: it prefetches A
+  int kc0 = 0, nchk = P.nchunks;  // this CTA's exact K chunks [kc0, kc0 + nchk) of every tile
   if (OUT_MODE == 3) {
     const int nit = *P.item_count;
     if ((int)blockIdx.x >= nit) return;  // the whole CTA: no item
@@ -321,7 +330,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     R = min((int64_t)OZ_BM, P.rowsA - a_row0);
     C = min((int64_t)OZ_BN, P.rowsB - b_row0);
   } else {
-    int t = blockIdx.x, rt = 0, ct = 0;
+    const int ks = P.ksplit > 1 ? P.ksplit : 1;
+    int t = (int)blockIdx.x / ks, rt = 0, ct = 0;
+    if (ks > 1) {
+      kc0 = ((int)blockIdx.x % ks) * P.chunks_per_split;
+      nchk = min(P.chunks_per_split, P.nchunks - kc0);
+    }
+    if (nchk <= 0) return;  // the whole CTA: an empty K range
     int64_t rowoff = 0;
     for (bblk = 0; bblk < P.g.nbl; ++bblk) {
       int nrt = (int)cdiv64(P.g.rows(bblk), OZ_BM), nct = (int)cdiv64(P.g.cols(bblk), OZ_BN);
@@ -338,7 +353,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // the block's columns go to its column tiles in equal widths (multiples of 16)
     ntile = g_tile_width(P.g.cols(bblk));
     a_row0 = rowoff + (int64_t)rt * OZ_BM;
-    b_row0 = (int64_t)bblk * P.g.nbp + (int64_t)ct * ntile;
+    b_row0 = P.g.colstart(bblk) + (int64_t)ct * ntile;
     R = min((int64_t)OZ_BM, P.g.rows(bblk) - (int64_t)rt * OZ_BM);
     C = min((int64_t)ntile, P.g.cols(bblk) - (int64_t)ct * ntile);
     out_base = P.g.offset(bblk) + (int64_t)rt * OZ_BM * P.g.cols(bblk) + (int64_t)ct * ntile;
@@ -363,8 +378,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int ksteps = P.Kpad / OZ_BK;
   const int steps_per_chunk = OZ_KC / OZ_BK;
+  const int kbase = kc0 * steps_per_chunk;  // first K step of the CTA's range
+  const int ksteps = min(P.Kpad / OZ_BK, (kc0 + nchk) * steps_per_chunk) - kbase;
   const CUtensorMap *tmB = &bmaps.m[ntile / 16 - 1];
   const uint32_t stage_bytes = (uint32_t)(OZ_A_BYTES + OZ_SLICES * ntile * OZ_ROWB);
 
@@ -388,7 +404,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         // the same rows at about the same time, and their prefetches would
         // only add L2 lookups: 2.6 % of the triple GEMM's time)
         if (lead)
-          for (int i = 0; i < OZ_PREFETCH && i < ksteps; ++i) ptx::tma_prefetch_3d(&tmA, i * OZ_BK, ar, 0);
+          for (int i = 0; i < OZ_PREFETCH && i < ksteps; ++i)
+            ptx::tma_prefetch_3d(&tmA, (kbase + i) * OZ_BK, ar, 0);
         for (int i = 0; i < ksteps; ++i) {
           const int g = tt * ksteps + i;  // step count of the CTA: stage and phase
           const int s = g % OZ_STAGES;
@@ -399,9 +416,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           unsigned char *st = sm + s * OZ_STAGE_BYTES;
           ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
-          ptx::tma_load_3d(st, &tmA, &full[s], i * OZ_BK, ar, 0);
-          ptx::tma_load_3d(st + OZ_A_BYTES, tmB, &full[s], i * OZ_BK, br, 0);
-          if (lead && i + OZ_PREFETCH < ksteps) ptx::tma_prefetch_3d(&tmA, (i + OZ_PREFETCH) * OZ_BK, ar, 0);
+          ptx::tma_load_3d(st, &tmA, &full[s], (kbase + i) * OZ_BK, ar, 0);
+          ptx::tma_load_3d(st + OZ_A_BYTES, tmB, &full[s], (kbase + i) * OZ_BK, br, 0);
+          if (lead && i + OZ_PREFETCH < ksteps)
+            ptx::tma_prefetch_3d(&tmA, (kbase + i + OZ_PREFETCH) * OZ_BK, ar, 0);
           ++issued;
         }
       }
@@ -498,8 +516,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       hi[c] = 0.f;
       lo_s[(col0 + c) * OZ_BM + row] = 0.f;
     }
-    for (int ch = 0; ch < P.nchunks; ++ch) {
-      const int cg = tt * P.nchunks + ch;  // chunk count of the CTA (barrier phase)
+    for (int cl = 0; cl < nchk; ++cl) {
+      const int ch = kc0 + cl;          // exact K chunk
+      const int cg = tt * nchk + cl;    // chunk count of the CTA (barrier phase)
       // the whole warp goes on or gives up together (shuffles below)
       const bool got = ptx::mbar_wait(acc_full, (uint32_t)(cg & 1), abort_flag, P.wait_cycles);
       if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
@@ -576,8 +595,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             double *d = P.out + (ar0 + row) * P.ld_r + (b_row0 + col) * P.ld_c;
             *d = P.out_accumulate ? *d + v : v;
           } else {
-            double *d = P.out + out_base + (int64_t)row * P.g.cols(bblk) + col;
-            *d += v;
+            const int64_t o = out_base + (int64_t)row * P.g.cols(bblk) + col;
+            if (kc0 == 0) P.out[o] += v;
+            else P.out_part[(int64_t)(kc0 / P.chunks_per_split - 1) * P.part_stride + o] = v;
           }
         }
         if (OUT_MODE == 0 && ++p == P.nbp) {
@@ -651,7 +671,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OZ_THREADS, 1)
   const int64_t R = min((int64_t)OZ_BM, P.g.rows(bblk) - rt_loc * OZ_BM);  // may be <= 0 (odd tail)
   const int64_t C = min((int64_t)ntile, P.g.cols(bblk) - (int64_t)ct * ntile);
   const int64_t a_row0 = pair_row0 + (int64_t)rank * OZ_BM;
-  const int64_t b_row0 = (int64_t)bblk * P.g.nbp + (int64_t)ct * ntile;
+  const int64_t b_row0 = P.g.colstart(bblk) + (int64_t)ct * ntile;
   const int64_t out_base = P.g.offset(bblk) + rt_loc * OZ_BM * P.g.cols(bblk) + (int64_t)ct * ntile;
 
   if (threadIdx.x == 0) {
@@ -906,7 +926,7 @@ __device__ __forceinline__ QItem q_decode(const QueueParams &Q, uint32_t code) {
   q_tile(Q.o.g, Q.wmax, t, bblk, rt, ct, rowoff);
   it.ntile = g_tile_width_cap(Q.o.g.cols(bblk), Q.wmax);
   it.a_row0 = rowoff + (int64_t)rt * OZ_BM;
-  it.b_row0 = (int64_t)bblk * Q.o.g.nbp + (int64_t)ct * it.ntile;
+  it.b_row0 = Q.o.g.colstart(bblk) + (int64_t)ct * it.ntile;
   it.R = min((int64_t)OZ_BM, Q.o.g.rows(bblk) - (int64_t)rt * OZ_BM);
   it.C = min((int64_t)it.ntile, Q.o.g.cols(bblk) - (int64_t)ct * it.ntile);
   it.ldo = Q.o.g.cols(bblk);
@@ -1520,8 +1540,9 @@ __device__ __forceinline__ void y_row_decode(int64_t r, int P2, int &b, int &a, 
 
 // Per-(row, K chunk) exponents of the Y operand, from the bound
 // |Y| <= m_au m_bv + m_av m_bu (FP64, once per row and chunk), and their
-// maximum.  Rows are ordered by the pair (a <= b), then by {u, v}.
-__global__ void __launch_bounds__(256) k_tp_y_exp(int64_t rowsY, int nbp, int nblp, int P2,
+// maximum.  Rows are ordered by the layout's Y pairs (GLayout::y_pair), then
+// by {u, v}.
+__global__ void __launch_bounds__(256) k_tp_y_exp(GLayout g, int64_t rowsY, int nbp, int nblp, int P2,
                                                   const double *__restrict__ mxW, int *__restrict__ eY,
                                                   int *__restrict__ emaxY) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1529,7 +1550,8 @@ __global__ void __launch_bounds__(256) k_tp_y_exp(int64_t rowsY, int nbp, int nb
   int e = -100000;
   if (r < rowsY) {
     int a, b, u, v;
-    y_row_decode(r, P2, b, a, u, v);
+    g.y_pair((int)(r / P2), a, b);
+    pair_decode((int)(r % P2), u, v);
     const double *mw = mxW + (int64_t)ch * nblp;
     e = exp_bound(mw[a * nbp + u] * mw[b * nbp + v] + mw[a * nbp + v] * mw[b * nbp + u]);
     eY[(int64_t)ch * rowsY + r] = e;
@@ -1597,7 +1619,7 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float2 v) {
   return *reinterpret_cast<const uint32_t *>(&p);
 }
 
-__global__ void __launch_bounds__(32 * TY_WARPS) k_tp_make_y(int64_t rowsY, int64_t K, int Kpad, int nbp, int nblp,
+__global__ void __launch_bounds__(32 * TY_WARPS) k_tp_make_y(GLayout g, int64_t rowsY, int64_t K, int Kpad, int nbp, int nblp,
                                                          int P2, const f2 *__restrict__ Mdf,
                                                          const int *__restrict__ eY, __nv_bfloat16 *__restrict__ Ysl) {
   extern __shared__ __align__(16) unsigned char ty_sm[];
@@ -1606,7 +1628,7 @@ __global__ void __launch_bounds__(32 * TY_WARPS) k_tp_make_y(int64_t rowsY, int6
   // normal float, else as two exact factors; (0, 0) for an all-zero row
   float2 *Fs = reinterpret_cast<float2 *>(ty_sm + (size_t)2 * nbp * TY_LD * sizeof(float));
   int a, b;
-  pair_decode(blockIdx.x, a, b);
+  g.y_pair(blockIdx.x, a, b);  // the block's pair a <= b (Y pair blockIdx.x of the layout)
   const int64_t row0 = (int64_t)blockIdx.x * P2;
   const int64_t kb = (int64_t)blockIdx.y * TY_K;
   const int ch = (int)(kb / OZ_KC);
@@ -1753,7 +1775,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
   if (bblk >= P.g.nbl) return;
   const int64_t a_row0 = rowoff + (int64_t)rt * OZ_BM;  // global Y row of the tile start
-  const int64_t b_row0 = (int64_t)bblk * P.g.nbp + (int64_t)ct * OZ_BN;
+  const int64_t b_row0 = P.g.colstart(bblk) + (int64_t)ct * OZ_BN;
   const int64_t R = min((int64_t)OZ_BM, P.g.rows(bblk) - (int64_t)rt * OZ_BM);
   const int64_t C = min((int64_t)OZ_BN, P.g.cols(bblk) - (int64_t)ct * OZ_BN);
   const int64_t out_base = P.g.offset(bblk) + (int64_t)rt * OZ_BM * P.g.cols(bblk) + (int64_t)ct * OZ_BN;
@@ -2056,7 +2078,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
   const int ntile = g_tile_width(P.g.cols(bblk));
   const int64_t lrow0 = (int64_t)rt * OZ_BM;       // first row of the tile inside block b
   const int64_t a_row0 = rowoff + lrow0;           // ... in the full Y row order
-  const int64_t b_row0 = (int64_t)bblk * P.g.nbp + (int64_t)ct * ntile;
+  const int64_t b_row0 = P.g.colstart(bblk) + (int64_t)ct * ntile;
   const int64_t R = min((int64_t)OZ_BM, P.g.rows(bblk) - lrow0);
   const int64_t C = min((int64_t)ntile, P.g.cols(bblk) - (int64_t)ct * ntile);
   const int64_t out_base = P.g.offset(bblk) + lrow0 * P.g.cols(bblk) + (int64_t)ct * ntile;
@@ -2314,12 +2336,28 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
   }
 }
 
+static constexpr int TRIPLE_KSPLIT_MAX = 4;  // K splits of the one-CTA-per-tile triple GEMM
+
+// Y rows of every pair a <= b (the most any layout uses: scratch sizes)
 static int64_t y_rows(const SepShape &s) {
   const int64_t P2 = (int64_t)s.nbp * (s.nbp + 1) / 2;
   return P2 * s.nbl * (s.nbl + 1) / 2;
 }
 
-size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
+// Layout of G for a triple-product variant: the split expansion (every block
+// wide, Y rows of about half of the pairs) for the forms that read Y from
+// device memory; the row-of-c expansion throughout for the forms that build
+// Y inside the GEMM.
+GLayout tc_triple_glayout(const SepShape &s, int variant) {
+  const bool y_hbm = variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR || variant == TC_TRIPLE_QUEUE;
+  return y_hbm ? make_glayout_split(s.nbl, s.nbp) : make_glayout(s.nbl, s.nbp);
+}
+
+static size_t triple_bytes(const SepShape &s, int nxc, int variant, bool parts);
+size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) { return triple_bytes(s, nxc, variant, true); }
+// parts: room for the partial sums of K splits, which the forms that read Y
+// from device memory may use (the tile autotuner switches between them)
+static size_t triple_bytes(const SepShape &s, int nxc, int variant, bool parts) {
   const int64_t K = (int64_t)nxc * s.n_mu;
   const int Kpad = (int)(cdiv64(K, 64) * 64);
   const int64_t nblp = (int64_t)s.nbl * s.nbp;
@@ -2333,6 +2371,8 @@ size_t tc_triple_scratch_bytes(const SepShape &s, int nxc, int variant) {
     b += up256((size_t)nch * y_rows(s) * 4);                            // eY
   if (y_hbm)
     b += up256((size_t)OZ_SLICES * y_rows(s) * Kpad * 2);               // Y slices
+  if (y_hbm && parts)                                                    // partial sums of K splits
+    b += up256((size_t)(TRIPLE_KSPLIT_MAX - 1) * make_glayout(s.nbl, s.nbp).size() * 8);
   return b;
 }
 
@@ -2375,6 +2415,54 @@ static double plan_step_cost(const uint32_t (&plan)[1 + OZ_PLAN_MAX], int w) {
     c += N / 2.0 > 80.0 ? N / 2.0 : 80.0;
   }
   return c;
+}
+
+// K splits of the one-CTA-per-tile triple GEMM: tiles run in launch order on
+// the SMs as they free up (one CTA per SM), each costing its schedule's
+// modelled step cost per K step; a split cuts every tile into ks consecutive
+// CTAs of whole exact chunks (partial sums added in a fixed order after the
+// GEMM), which levels the last wave when the tiles are few and large.  Chooses ks = 1 .. 4 of least
+// modelled makespan (each CTA also pays half a chunk of set-up and drain).
+// G += part 0 + part 1 + ... (the K splits beyond the first, in order)
+__global__ void k_add_parts(double *__restrict__ G, const double *__restrict__ parts, int nparts, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = G[i];
+  for (int k = 0; k < nparts; ++k) v += parts[(int64_t)k * n + i];
+  G[i] = v;
+}
+static void triple_ksplit_choice(OzParams &P, int num_sms) {
+  std::vector<double> cost;
+  for (int b = 0; b < P.g.nbl; ++b) {
+    const int w = g_tile_width(P.g.cols(b));
+    const double c = plan_step_cost(P.plan[w / 16 - 1], w) * (OZ_KC / 16);  // one exact chunk
+    const int64_t n = cdiv64(P.g.rows(b), OZ_BM) * cdiv64(P.g.cols(b), OZ_BN);
+    for (int64_t i = 0; i < n; ++i) cost.push_back(c);
+  }
+  int best = 1;
+  double best_t = 0.0;
+  const int sms = num_sms > 0 ? num_sms : 1;
+  for (int ks = 1; ks <= TRIPLE_KSPLIT_MAX && ks <= P.nchunks; ++ks) {
+    const int cpk = (int)cdiv64(P.nchunks, ks);
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (int i = 0; i < sms; ++i) free_at.push(0.0);
+    double end = 0.0;
+    for (const double c : cost)
+      for (int k = 0; k < ks; ++k) {
+        const int nc = std::min(cpk, P.nchunks - k * cpk);
+        if (nc <= 0) continue;
+        const double t = free_at.top() + c * (nc + 0.5);
+        free_at.pop();
+        free_at.push(t);
+        end = std::max(end, t);
+      }
+    if (ks == 1 || end < best_t * 0.98) {  // a split must gain at least 2 %
+      best = ks;
+      best_t = end;
+    }
+  }
+  P.chunks_per_split = (int)cdiv64(P.nchunks, best);
+  P.ksplit = (int)cdiv64(P.nchunks, P.chunks_per_split);  // no part with an empty K range
 }
 
 // The persistent queue GEMM: items (tile, K range) in order of decreasing
@@ -2475,8 +2563,8 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     int *eY = (int *)((char *)Bt + up256((size_t)OZ_SLICES * nblp * Kpad * 2));
     {
       ProfScope ps(prof, "tc_y_exp", st);
-      k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(rowsY, s.nbp, nblp, P2, mxW,
-                                                                                  eY, words + 4);
+      k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(
+          make_glayout(s.nbl, s.nbp), rowsY, s.nbp, nblp, P2, mxW, eY, words + 4);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
     CUtensorMap tm;
@@ -2514,27 +2602,26 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
   if (variant == TC_TRIPLE_MATERIALISED || variant == TC_TRIPLE_PAIR || variant == TC_TRIPLE_QUEUE) {
     // Y slices through HBM, then the TMA-fed GEMM for both operands (single
     // CTAs, or CTA pairs with the 2-SM MMA)
-    const int64_t rowsY = y_rows(s);
+    const GLayout gl = tc_triple_glayout(s, variant);
+    const int64_t rowsY = (int64_t)gl.ypairs_total() * P2;
     char *wy = (char *)Bt + up256((size_t)OZ_SLICES * nblp * Kpad * 2);
     int *eY = (int *)wy;
     wy += up256((size_t)nch * rowsY * 4);
     __nv_bfloat16 *Ysl = (__nv_bfloat16 *)wy;
     {
       ProfScope ps(prof, "tc_make_Y", st, 2);  // exponents + slices
-      k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(rowsY, s.nbp, nblp, P2, mxW,
-                                                                                  eY, words + 4);
+      k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(gl, rowsY, s.nbp, nblp, P2,
+                                                                                  mxW, eY, words + 4);
       const size_t smy = ty_smem_bytes(s.nbp);
       if ((e = cudaFuncSetAttribute(k_tp_make_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) !=
           cudaSuccess)
         goto cuda_fail;
-      const int npairs = s.nbl * (s.nbl + 1) / 2;
-      k_tp_make_y<<<dim3((unsigned)npairs, (unsigned)cdiv64(Kpad, TY_K)), 32 * TY_WARPS, smy, st>>>(
-          rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, eY, Ysl);
+      k_tp_make_y<<<dim3((unsigned)gl.ypairs_total(), (unsigned)cdiv64(Kpad, TY_K)), 32 * TY_WARPS, smy, st>>>(
+          gl, rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, eY, Ysl);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
     CUtensorMap ta;
     BMaps tb;
-    const GLayout gl = make_glayout(s.nbl, s.nbp);
     unsigned used = 0;
     for (int b = 0; b < s.nbl; ++b) used |= 1u << (g_tile_width(gl.cols(b)) / 16 - 1);
     if (int r = make_slices_map(&ta, Ysl, rowsY, Kpad, OZ_BM)) return r;
@@ -2550,7 +2637,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     P.emaxB = words + 3;
     P.out = G;
     P.err = words;
-    P.g = make_glayout(s.nbl, s.nbp);
+    P.g = gl;
     P.wait_cycles = wait_cycles;
     if (variant == TC_TRIPLE_QUEUE) {
       const int wmax = tune_wmax(tune);
@@ -2578,12 +2665,26 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     fill_mma_plans(P.plan);
     int64_t tiles = 0;
     for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(P.g.rows(b), OZ_BM) * cdiv64(P.g.cols(b), OZ_BN);
+    triple_ksplit_choice(P, num_sms);
+    if (split_k > 0) {  // a caller's choice (MODAL_OPT_TC_SPLIT_K)
+      P.chunks_per_split = (int)cdiv64(P.nchunks, std::min(split_k, TRIPLE_KSPLIT_MAX));
+      P.ksplit = (int)cdiv64(P.nchunks, P.chunks_per_split);
+    }
+    P.part_stride = gl.size();
+    P.out_part = (double *)((char *)Ysl + up256((size_t)OZ_SLICES * y_rows(s) * Kpad * 2));
     if ((e = cudaFuncSetAttribute(k_ozaki_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
         cudaSuccess)
       goto cuda_fail;
-    ProfScope ps(prof, "tc_gemm_triple", st);
-    k_ozaki_gemm<1><<<(unsigned)tiles, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
-    if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+    {
+      ProfScope ps(prof, "tc_gemm_triple", st);
+      k_ozaki_gemm<1><<<(unsigned)(tiles * P.ksplit), OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+      if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+    }
+    if (P.ksplit > 1) {
+      ProfScope ps(prof, "tc_add_parts", st);
+      k_add_parts<<<(unsigned)cdiv64(gl.size(), 256), 256, 0, st>>>(G, P.out_part, P.ksplit - 1, gl.size());
+      if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+    }
     return MODAL_OK;
   }
   {
@@ -2857,7 +2958,7 @@ __global__ void k_adj_scatter_gfull(int nbl, int nbp, const double *__restrict__
 constexpr int SET_WORDS_BYTES = 256;
 
 static size_t set_bytes(const SepShape &s, int nxc_max) {
-  return SET_WORDS_BYTES + tc_triple_scratch_bytes(s, nxc_max, TC_TRIPLE_MATERIALISED);
+  return SET_WORDS_BYTES + triple_bytes(s, nxc_max, TC_TRIPLE_MATERIALISED, false);
 }
 
 size_t tc_ovl_scratch_bytes(const SepShape &s, int nxl, int nxc) {
@@ -2906,7 +3007,8 @@ int tc_triple_prep(const SepShape &s, const double *M, const double *om, const d
   const int nblp = s.nbl * s.nbp;
   const int nch = (int)cdiv64(K, OZ_KC);
   const int P2 = s.nbp * (s.nbp + 1) / 2;
-  const int64_t rowsY = y_rows(s);
+  const GLayout gl = tc_triple_glayout(s, TC_TRIPLE_QUEUE);
+  const int64_t rowsY = (int64_t)gl.ypairs_total() * P2;
   cudaError_t e;
   {
     ProfScope ps(prof, "tc_prep_M", st, 3);
@@ -2920,15 +3022,14 @@ int tc_triple_prep(const SepShape &s, const double *M, const double *om, const d
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   {
     ProfScope ps(prof, "tc_make_Y", st, 2);
-    k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(rowsY, s.nbp, nblp, P2, r.mxW,
-                                                                                r.eY, r.sw + 1);
+    k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(gl, rowsY, s.nbp, nblp, P2,
+                                                                                r.mxW, r.eY, r.sw + 1);
     const size_t smy = ty_smem_bytes(s.nbp);
     if ((e = cudaFuncSetAttribute(k_tp_make_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) !=
         cudaSuccess)
       goto cuda_fail;
-    const int npairs = s.nbl * (s.nbl + 1) / 2;
-    k_tp_make_y<<<dim3((unsigned)npairs, (unsigned)cdiv64(Kpad, TY_K)), 32 * TY_WARPS, smy, st>>>(
-        rowsY, K, Kpad, s.nbp, nblp, P2, r.Mdf, r.eY, r.Ysl);
+    k_tp_make_y<<<dim3((unsigned)gl.ypairs_total(), (unsigned)cdiv64(Kpad, TY_K)), 32 * TY_WARPS, smy, st>>>(
+        gl, rowsY, K, Kpad, s.nbp, nblp, P2, r.Mdf, r.eY, r.Ysl);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   return MODAL_OK;
@@ -2946,19 +3047,18 @@ int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double 
   const int Kpad = (int)(cdiv64(K, 64) * 64);
   const int nblp = s.nbl * s.nbp;
   const int nch = (int)cdiv64(K, OZ_KC);
-  const int64_t rowsY = y_rows(s);
+  const GLayout gl = tc_triple_glayout(s, TC_TRIPLE_QUEUE);
+  const int64_t rowsY = (int64_t)gl.ypairs_total() * (s.nbp * (s.nbp + 1) / 2);
   cudaError_t e;
   if (!accumulate) {
     ProfScope ps(prof, "zero_G", st);
-    GLayout g = make_glayout(s.nbl, s.nbp);
-    if ((e = launch_zero(G, (size_t)g.size(), st)) != cudaSuccess) {
+    if ((e = launch_zero(G, (size_t)gl.size(), st)) != cudaSuccess) {
       snprintf(g_tc_err, sizeof g_tc_err, "triple product: %s", cudaGetErrorString(e));
       return MODAL_ECUDA;
     }
   }
   CUtensorMap ta;
   BMaps tb;
-  const GLayout gl = make_glayout(s.nbl, s.nbp);
   const int wmax = tune_wmax(tune);
   unsigned used = 0;
   for (int b = 0; b < s.nbl; ++b) used |= 1u << (g_tile_width_cap(gl.cols(b), wmax) / 16 - 1);

@@ -69,6 +69,8 @@ bool tc_direct_supported(int nb_late, int nb_prim);
 size_t tc_direct_scratch_bytes(const modal_problem *p, int ng);
 int tc_project_direct(const modal_problem *p, const int *grid, const double *dw, int ng, int mode, double *gamma,
                       void *scratch, int num_sms, long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
+// Layout of G that the triple product of a variant fills (the gather reads it)
+GLayout tc_triple_glayout(const SepShape &s, int variant);
 // device status word of the tensor-core scratch (bit 0: a bounded wait gave up,
 // bit 1: a value outside the FP32 exponent range of the split operands)
 int *tc_error_word(void *scratch);

@@ -16,6 +16,12 @@ import synthetic as syn
 pytestmark = pytest.mark.gpu
 
 TOL_MIXED = 1e-8
+# Two tensor-core forms (one CTA per tile with or without K splits, the
+# queue with split tiles, the Y pass beside the GEMM) add the same exact chunk
+# products in different groupings, so they agree to the rounding of the
+# double-FP32 running sums and FP64 partial sums (~1e-14 of the G entries,
+# amplified by the cancellation in the gather), not bit for bit.
+TOL_FORMS = 1e-11
 
 
 def normwise(a, ref):
@@ -59,7 +65,7 @@ def test_queue_matches_one_cta_per_tile(mg):
     g1 = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, handle=h1)
     mg.handle_status(handle=h0)
     mg.handle_status(handle=h1)
-    assert normwise(g1, g0) < 1e-12
+    assert normwise(g1, g0) < TOL_FORMS
     assert normwise(g1, oracle.separable(P)) < TOL_MIXED
     h0.close()
     h1.close()
@@ -108,7 +114,7 @@ def test_queue_planck_sampled(mg):
     mg.set_option(mg.OPT_TC_QUEUE, 0, handle=h)
     g0 = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, handle=h).cpu().numpy()
     mg.handle_status(handle=h)
-    assert normwise(g, g0) < 1e-12
+    assert normwise(g, g0) < TOL_FORMS
     h.close()
 
 
@@ -128,11 +134,11 @@ def test_batched_tile_autotuner(mg):
     gs2 = mg.project_separable_batched(dps, precision=mg.PREC_OZAKI_BF16, handle=h)
     mg.handle_status(handle=h)
     for g, g2 in zip(gs, gs2):
-        assert normwise(g2, g.cpu().numpy()) < 1e-12
+        assert normwise(g2, g.cpu().numpy()) < TOL_FORMS
     for dp, g in zip(dps, gs):
         single = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, handle=h)
         mg.handle_status(handle=h)
-        assert normwise(single, g.cpu().numpy()) < 1e-12
+        assert normwise(single, g.cpu().numpy()) < TOL_FORMS
     h.close()
 
 
@@ -153,7 +159,7 @@ def test_overlap_separable(mg, shape, x_chunk):
     mg.set_option(mg.OPT_TC_OVERLAP, 0, handle=h)
     g0 = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, x_chunk=x_chunk, handle=h).cpu().numpy()
     mg.handle_status(handle=h)
-    assert normwise(g, g0) < 1e-12
+    assert normwise(g, g0) < TOL_FORMS
     h.close()
 
 
@@ -166,7 +172,7 @@ def test_overlap_planck(mg):
     mg.set_option(mg.OPT_TC_OVERLAP, 32, handle=h)
     g = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, handle=h)
     mg.handle_status(handle=h)
-    assert normwise(g, g0) < 1e-12
+    assert normwise(g, g0) < TOL_FORMS
     late_pick = np.array([i for i, m in enumerate(P.late_modes) if set(m) <= {2, 9, 16}])
     prim_pick = np.array([i for i, m in enumerate(P.prim_modes) if set(m) <= {4, 13, 18}])
     ref = oracle.separable(P, late=P.late_modes[late_pick], prim=P.prim_modes[prim_pick])
