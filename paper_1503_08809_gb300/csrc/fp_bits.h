@@ -96,6 +96,10 @@ FPB_HD f2 df_from_d(double x) {
   return {h, (float)(x - (double)h)};
 }
 
+// out of line, so that the rare inputs' FP64 route is a branch taken only by
+// them rather than work every caller does
+FPB_HD_NOINLINE f2 df_from_d_slow(double x) { return df_from_d(x); }
+
 // The same split with integer operations: hi is x rounded to 24 significant
 // bits (to nearest, ties to even), and x - hi, an integer of at most 29 bits
 // times 2^(e - 52), goes to FP32 through the rounding integer-to-float
@@ -105,7 +109,7 @@ FPB_HD f2 df_from_d(double x) {
 FPB_HD f2 df_from_d_fast(double x) {
   const uint64_t u = d_bits(x);
   const int ex = (int)((u >> 52) & 0x7ffu);
-  if (ex < 950 || ex > 1149) return df_from_d(x);
+  if (ex < 950 || ex > 1149) return df_from_d_slow(x);
   const uint32_t sign = (uint32_t)(u >> 63) << 31;
   const uint64_t mant = (u & 0xfffffffffffffull) | (1ull << 52);
   uint32_t m24 = (uint32_t)(mant >> 29);

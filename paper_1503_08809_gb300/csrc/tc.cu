@@ -2795,10 +2795,15 @@ __global__ void k_split_op(int64_t rows, int64_t K, int Kpad, Op op, __nv_bfloat
   const int64_t r = w / nch;
   const int ch = (int)(w % nch);
   const int64_t k0 = (int64_t)ch * OZ_KC, k1 = min(K, k0 + OZ_KC);
-  float m = 0.f;
-  for (int64_t k = k0 + lane; k < k1; k += 32) m = fmaxf(m, fabsf(__double2float_rn(op.val(r, k))));
+  // max |x| on the bits (non-negative doubles order as their bit patterns; a
+  // NaN sorts above infinity), rounded to FP32 once: the same value as the
+  // maximum of the rounded magnitudes, without a conversion per element
+  unsigned long long mb = 0ull;
+  for (int64_t k = k0 + lane; k < k1; k += 32)
+    mb = max(mb, (unsigned long long)fpb::d_bits(op.val(r, k)) & 0x7fffffffffffffffull);
 #pragma unroll
-  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  float m = __double2float_rn(fpb::d_from(mb));
   if (!(m < 1e37f)) {
     if (lane == 0) atomicOr(err, ERR_RANGE);
     m = 0.f;
