@@ -44,8 +44,8 @@ TC_SLICE_PRODUCTS = 15       # BF16 slice products per useful MAC in the tensor-
 # capture (n_x = 8 gives one launch with the same K as every launch of the
 # 500-point step), keyed by the kernel's form.  A form that changed since its
 # capture is left out (its traffic is then reported as null).
-NCU_TRAFFIC = {("tc_gemm_triple", "single"): 11.328e9 + 49.2e6, ("tc_make_Y", "single"): 88.4e6 + 10.551e9,
-               ("tc_make_Y", "pair"): 88.4e6 + 10.551e9, ("tc_make_Y", "queue"): 88.4e6 + 10.551e9}
+NCU_TRAFFIC = {("tc_gemm_triple", "single"): 7.136e9 + 92.5e6, ("tc_make_Y", "single"): 80.6e6 + 5.497e9,
+               ("tc_make_Y", "pair"): 80.6e6 + 5.497e9, ("tc_make_Y", "queue"): 80.6e6 + 5.497e9}
 # kernels inside one profiler scope (the library counts kernels; a roofline
 # divides the scope's time by its scope count)
 SCOPE_KERNELS = {"tc_make_Y": 2, "tc_prep_M": 2}
