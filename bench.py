@@ -45,7 +45,8 @@ TC_SLICE_PRODUCTS = 15       # BF16 slice products per useful MAC in the tensor-
 # 500-point step), keyed by the kernel's form.  A form that changed since its
 # capture is left out (its traffic is then reported as null).
 NCU_TRAFFIC = {("tc_gemm_triple", "single"): 7.136e9 + 92.5e6, ("tc_make_Y", "single"): 80.6e6 + 5.497e9,
-               ("tc_make_Y", "pair"): 80.6e6 + 5.497e9, ("tc_make_Y", "queue"): 80.6e6 + 5.497e9}
+               ("tc_make_Y", "pair"): 80.6e6 + 5.497e9, ("tc_make_Y", "queue"): 80.6e6 + 5.497e9,
+               ("tc_make_Y", "tail"): 80.6e6 + 5.497e9}
 # kernels inside one profiler scope (the library counts kernels; a roofline
 # divides the scope's time by its scope count)
 SCOPE_KERNELS = {"tc_make_Y": 2, "tc_prep_M": 2}
@@ -85,6 +86,8 @@ def parse():
                     help="tensor-core triple product GEMM as a persistent kernel over a work queue: 1")
     ap.add_argument("--tc-overlap", type=int, default=0,
                     help="SMs left to the Y pass running beside the queue GEMM (0: no overlap)")
+    ap.add_argument("--tc-tail", type=int, default=1, choices=[0, 1],
+                    help="operand and Y passes beside the previous chunk's GEMM on a second stream: 1 (default)")
     ap.add_argument("--tc-split-k", type=int, default=0,
                     help="K splits of the tensor-core triple GEMM (0: the library's choice)")
     ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1],
@@ -259,6 +262,7 @@ def run_ours(args):
     mg.set_option(mg.OPT_TC_QUEUE, args.tc_queue, handle=h)
     mg.set_option(mg.OPT_TC_OVERLAP, args.tc_overlap, handle=h)
     mg.set_option(mg.OPT_TC_SPLIT_K, args.tc_split_k, handle=h)
+    mg.set_option(mg.OPT_TC_OVERLAP_TAIL, args.tc_tail, handle=h)
     dp = mg.DeviceProblem.from_host(P, device=dev, handle=h)
     gamma = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream(dev)
@@ -308,13 +312,37 @@ def run_ours(args):
     # ---- rooflines: the dominant kernel, and every tensor / HBM kernel ------
     peaks, src = measured_peaks()
     launches_per_step = {k: max(1, v[0] // args.steps) for k, v in prof.items()}
-    form = "pair" if args.tc_pair else "queue" if (args.tc_queue or args.tc_overlap) else "single"
+    form = ("pair" if args.tc_pair else "queue" if (args.tc_queue or args.tc_overlap) else
+            "tail" if (args.tc_tail and prec_name == "ozaki" and not sharded) else "single")
     rooflines = {k: kernel_roofline(k, prof[k], launches_per_step[k], P, prec_name, peaks, src, args.steps, ms,
                                     form) for k in prof}
     rooflines = {k: v for k, v in rooflines.items() if v is not None}
     dom = max(prof, key=lambda k: prof[k][1]) if prof else None
     roof = rooflines.get(dom)
     gpu_launches = sum(v[0] for v in prof.values())
+    step_tensor = None
+    if prec_name == "ozaki":
+        # the whole step's issued tensor work (triple product and l contraction)
+        # over the step time: the path's own fraction of the tensor peak
+        g2 = P.nb_prim * (P.nb_prim + 1) // 2
+        macs = g2 * P.nb_prim * P.n_late + P.nb_late * P.nb_prim * P.L
+        tf = TC_SLICE_PRODUCTS * 2.0 * macs * P.slices / (ms * 1e-3) / 1e12
+        step_tensor = {"issued_tflops": tf, "peak": peaks["bf16_tflops"], "frac": tf / peaks["bf16_tflops"],
+                       "peak_source": f"bf16 {src}"}
+    if form == "tail" and roof is not None and dom == "tc_gemm_triple":
+        # under the tail overlap the GEMM's launches share the SMs with the next
+        # chunk's operand passes, so its launch time is not the kernel's own:
+        # two more steps with one stream give that figure
+        mg.set_option(mg.OPT_TC_OVERLAP_TAIL, 0, handle=h)
+        p2 = profiled(h, lambda: [step() for _ in range(2)], dev)
+        mg.set_option(mg.OPT_TC_OVERLAP_TAIL, 1, handle=h)
+        if "tc_gemm_triple" in p2:
+            alone = kernel_roofline("tc_gemm_triple", p2["tc_gemm_triple"],
+                                    max(1, p2["tc_gemm_triple"][0] // 2), P, prec_name, peaks, src, 2, ms,
+                                    "single")
+            roof["alone"] = {k: alone[k] for k in ("achieved", "frac", "kernel_ms_avg", "traffic")}
+            roof["note"] = ("launch time includes the next chunk's operand and Y passes sharing the SMs "
+                            "(MODAL_OPT_TC_OVERLAP_TAIL); 'alone': the same kernel with one stream")
 
     # ---- end to end through host buffers -----------------------------------
     e2e = None
@@ -375,13 +403,15 @@ def run_ours(args):
                                    if args.tc_overlap else
                                    "persistent work queue" if args.tc_queue else
                                    "one CTA per tile (or per K range of a tile)" + (f", {args.tc_split_k} K splits"
-                                                                                     if args.tc_split_k else "")),
+                                                                                     if args.tc_split_k else "") +
+                                   (", operand and Y passes beside the previous chunk's GEMM" if args.tc_tail
+                                    else "")),
                        "g_layout": "blocks by the middle index, each expanded along its wider side",
                        "l2": "inputs larger than L2 (q~ 160 MB; M chunks of up to 2 GiB)",
                        "parallelism": (f"x-sharded over {ws} ranks, FP64 all-reduce of Gamma'" if sharded
                                        else f"{ws} independent problem(s)")},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "fp64_gpu": fp64, "error": err, "kernel_rooflines": rooflines,
+            "fp64_gpu": fp64, "error": err, "kernel_rooflines": rooflines, "step_tensor": step_tensor,
             "clocks": clk, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
 
@@ -423,7 +453,10 @@ def kernel_roofline(name, rec, per_step, P, prec_name, peaks, src, steps, ms, fo
         extra = {"flops_counted": f"issued tensor flops ({nprod} product(s) per useful MAC)",
                  "useful_achieved": 2.0 * macs * k_launch / avg_s / 1e12}
     elif name == "tc_make_Y":
-        rows = g2 * P.nb_late * (P.nb_late + 1) // 2
+        # Y rows of the pairs the G layout of the Y-in-HBM forms uses: (a, b)
+        # for b < h and (b, c) for b >= h, h = ceil(nb / 2)
+        hh = (P.nb_late + 1) // 2
+        rows = g2 * (hh * (hh + 1) // 2 + (P.nb_late - hh) * (P.nb_late - hh + 1) // 2)
         work = 10.0 * rows * kpad + 8.0 * P.nb_late * P.nb_prim * kpad   # Y slices out, M~ in
         unit, bound, peak, note = "GB/s", "hbm", peaks["hbm_gbs"], f"hbm copy {src}"
     else:

@@ -155,6 +155,12 @@ int modal_handle_status(modal_handle *h);
  *   second stream beside the previous chunk's GEMM, which then runs as the
  *   queue form on all but n SMs (two scratch sets; single-problem calls
  *   without error_estimate; implies MODAL_OPT_TC_QUEUE).  0 (default): off.
+ * MODAL_OPT_TC_OVERLAP_TAIL: 1 (default) runs the operand and Y passes of
+ *   each radial chunk on a second stream beside the previous chunk's GEMM,
+ *   which runs one CTA per tile (or K range of one) on a high-priority
+ *   stream: the passes take the SMs that the GEMM's last wave leaves idle
+ *   (two scratch sets; single-problem calls without error_estimate and
+ *   with the default GEMM form).  0: one stream.  Same results to rounding.
  * MODAL_OPT_DIRECT_TENSOR: 1 runs the Gamma' update of modal_project_direct
  *   (Gamma' += Y^T diag(z) X over each batch of triples, the reduction of
  *   Eq. 3D) on the tensor cores with exponent-aligned BF16 slices (errors of
@@ -178,6 +184,7 @@ int modal_handle_status(modal_handle *h);
 #define MODAL_OPT_TC_AUTOTUNE 6
 #define MODAL_OPT_TC_OVERLAP 7
 #define MODAL_OPT_DIRECT_TENSOR 8
+#define MODAL_OPT_TC_OVERLAP_TAIL 9
 int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value);
 
 /* Bound (in SM clock cycles) of those device-side waits for later calls on

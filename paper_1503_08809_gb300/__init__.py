@@ -8,7 +8,7 @@ fails loudly if it has not been built.
 """
 from __future__ import annotations
 
-from ._lib import (OPT_BATCH_STREAMS, OPT_DIRECT_TENSOR, OPT_TC_AUTOTUNE, OPT_TC_OVERLAP, OPT_TC_PAIR, OPT_TC_QUEUE, OPT_TC_SPLIT_K, OPT_TC_TRIPLE_FUSED, ModalError, PREC_FP32, PREC_FP64,
+from ._lib import (OPT_BATCH_STREAMS, OPT_DIRECT_TENSOR, OPT_TC_AUTOTUNE, OPT_TC_OVERLAP, OPT_TC_OVERLAP_TAIL, OPT_TC_PAIR, OPT_TC_QUEUE, OPT_TC_SPLIT_K, OPT_TC_TRIPLE_FUSED, ModalError, PREC_FP32, PREC_FP64,
                    PREC_BF16X3, PREC_OZAKI_BF16, PREC_TF32, W_EXACT_3J, W_SMOOTH_GOSPER, XW_HERMITE, XW_TRAPEZOID, lib,
                    lib_path)
 from .api import (DeviceProblem, Handle, contract_l, default_handle, gl_nodes, gram, gram_solve,

@@ -12,6 +12,7 @@ PREC_FP64, PREC_FP32, PREC_OZAKI_BF16, PREC_TF32, PREC_BF16X3 = 0, 1, 2, 3, 4
 XW_TRAPEZOID, XW_HERMITE = 0, 1
 OPT_TC_TRIPLE_FUSED, OPT_TC_SPLIT_K, OPT_BATCH_STREAMS, OPT_TC_PAIR, OPT_TC_QUEUE, OPT_TC_AUTOTUNE, OPT_TC_OVERLAP = 1, 2, 3, 4, 5, 6, 7
 OPT_DIRECT_TENSOR = 8
+OPT_TC_OVERLAP_TAIL = 9
 W_EXACT_3J, W_SMOOTH_GOSPER = 0, 1
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}

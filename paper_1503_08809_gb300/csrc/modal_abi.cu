@@ -45,7 +45,9 @@ struct modal_handle {
   int opt_autotune = 1;           // batched calls time the triple GEMM's tile shapes per bucket
   int opt_overlap = 0;            // SMs left to the Y pass beside the queue GEMM (0: no overlap)
   int opt_direct_tensor = 0;      // the direct form's Gamma update on the tensor cores
+  int opt_overlap_tail = 1;       // operand and Y passes beside the previous chunk's GEMM (its last wave)
   cudaStream_t ovl_stream = nullptr;
+  cudaStream_t ovl_hi = nullptr;  // high-priority stream of the GEMMs in the tail-overlap form
   cudaEvent_t ovl_ev[6] = {};     // fork, l contraction done, side done, prep[2] / gemm[2] (below)
   cudaEvent_t ovl_prep[2] = {}, ovl_gemm[2] = {};
   // tile shape chosen per problem bucket (tile_bucket): 0 = one CTA per tile,
@@ -216,6 +218,7 @@ int modal_handle_destroy(modal_handle *h) {
   }
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->ovl_stream) cudaStreamDestroy(h->ovl_stream);
+  if (h->ovl_hi) cudaStreamDestroy(h->ovl_hi);
   for (int i = 0; i < 6; ++i)
     if (h->ovl_ev[i]) cudaEventDestroy(h->ovl_ev[i]);
   for (int i = 0; i < 2; ++i) {
@@ -306,6 +309,10 @@ int modal_handle_set_option(modal_handle *h, int32_t option, int64_t value) {
       if (value < 0 || value > h->num_sms / 2)
         return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_OVERLAP takes 0 .. %d", h->num_sms / 2);
       h->opt_overlap = (int)value;
+      return MODAL_OK;
+    case MODAL_OPT_TC_OVERLAP_TAIL:
+      if (value < 0 || value > 1) return fail(h, MODAL_EINVAL, "MODAL_OPT_TC_OVERLAP_TAIL takes 0 or 1");
+      h->opt_overlap_tail = (int)value;
       return MODAL_OK;
     case MODAL_OPT_DIRECT_TENSOR:
       if (value < 0 || value > 2) return fail(h, MODAL_EINVAL, "MODAL_OPT_DIRECT_TENSOR takes 0, 1 or 2");
@@ -417,6 +424,7 @@ struct SepPlan {
   int variant;  // tensor-core triple-product variant
   int tune = 0; // tile shape of the queue variant (tc.cuh tune_wmax / tune_split)
   int overlap = 0;  // > 0: Y pass beside the queue GEMM, which keeps num_sms - overlap SMs
+  bool tail = false;  // operand and Y passes on a low-priority stream beside the one-CTA-per-tile GEMM
   int nxl;      // radial points per l-contraction chunk (tensor-core form; = nxc otherwise)
   int nxc;      // radial points per chunk
   int ksplit;   // K split of the SIMT triple product
@@ -498,17 +506,20 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   pl.ksplit = triple_ksplit(pl.s, pl.nxc, num_sms);
   const int nchunks = p->n_x > 0 ? (p->n_x + pl.nxc - 1) / pl.nxc : 0;
   const bool need_part = pl.ksplit > 1 || nchunks > 1;
+  pl.overlap = (prec == MODAL_PREC_OZAKI_BF16 && pl.variant == TC_TRIPLE_QUEUE && h && h->opt_overlap > 0 &&
+                !pl.est) ? h->opt_overlap : 0;
+  pl.tail = prec == MODAL_PREC_OZAKI_BF16 && pl.variant == TC_TRIPLE_MATERIALISED && h && h->opt_overlap_tail &&
+            !pl.est && !pl.overlap;
   size_t b = 0;
   b += 2 * align256(sizeof(double) * n_mu);                      // mu, om
   b += align256(sizeof(double) * (size_t)n_mu * pl.s.L);          // A
-  b += align256(pl.elem * (size_t)pl.nxl * n_mu * nblp);          // M chunk
+  b += align256(pl.elem * (size_t)pl.nxl * n_mu * nblp) * (pl.tail ? 2 : 1);  // M chunk(s)
   b += align256(sizeof(double) * (size_t)pl.Gsize);               // G
   if (pl.est) b += align256(sizeof(double) * (size_t)pl.Gsize);   // G of |M| (error scale)
   if (need_part) b += align256(sizeof(double) * (size_t)pl.Gsize * pl.ksplit);
-  pl.overlap = (prec == MODAL_PREC_OZAKI_BF16 && pl.variant == TC_TRIPLE_QUEUE && h && h->opt_overlap > 0 &&
-                !pl.est) ? h->opt_overlap : 0;
   if (prec == MODAL_PREC_OZAKI_BF16)
-    b += pl.overlap ? tc_ovl_scratch_bytes(pl.s, pl.nxl, pl.nxc) : tc_scratch_bytes(pl.s, pl.nxl, pl.nxc, pl.variant);
+    b += (pl.overlap || pl.tail) ? tc_ovl_scratch_bytes(pl.s, pl.nxl, pl.nxc)
+                                 : tc_scratch_bytes(pl.s, pl.nxl, pl.nxc, pl.variant);
   if (prec == MODAL_PREC_TF32 || prec == MODAL_PREC_BF16X3) b += fa_scratch_bytes(pl.s, pl.nxc);
   pl.bytes = b + 1024;
   return MODAL_OK;
@@ -523,11 +534,16 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
 //   side: prep(c) after the l contraction of its l-chunk and after GEMM(c - 2)
 //   main waits for the side's last prep of l-chunk L before l contraction L + 1.
 static int run_tc_overlap(modal_handle *h, int num_sms, const modal_problem *p, const SepPlan &pl, void *tcs,
-                          double *M, const double *om, const double *A, double *G, cudaStream_t st,
+                          double *M, double *M2, const double *om, const double *A, double *G, cudaStream_t st,
                           bool first_in_call) {
   const SepShape &s = pl.s;
   if (!h->ovl_stream) CK(cudaStreamCreateWithFlags(&h->ovl_stream, cudaStreamNonBlocking));
-  for (int i = 0; i < 3; ++i)
+  if (pl.tail && !h->ovl_hi) {
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&h->ovl_hi, cudaStreamNonBlocking, greatest));
+  }
+  for (int i = 0; i < 5; ++i)
     if (!h->ovl_ev[i]) CK(cudaEventCreateWithFlags(&h->ovl_ev[i], cudaEventDisableTiming));
   for (int i = 0; i < 2; ++i) {
     if (!h->ovl_prep[i]) CK(cudaEventCreateWithFlags(&h->ovl_prep[i], cudaEventDisableTiming));
@@ -537,32 +553,68 @@ static int run_tc_overlap(modal_handle *h, int num_sms, const modal_problem *p, 
   Profiler *prof = h->prof.on ? &h->prof : nullptr;
   const long long wc = h->wait_cycles;
   const int grid_sms = num_sms - pl.overlap;
+  // the tail form runs the l contraction and the GEMMs on a high-priority
+  // stream, so that the side stream's blocks take only the SMs that the
+  // GEMM's last wave leaves idle; the call's stream waits for both at the end
+  cudaStream_t user = st;
+  if (pl.tail) {
+    CK(cudaEventRecord(h->ovl_ev[3], user));
+    CK(cudaStreamWaitEvent(h->ovl_hi, h->ovl_ev[3], 0));
+    st = h->ovl_hi;
+  }
   if (int r = tc_prepare_l(s, A, p->q, tcs, pl.nxl, st, prof, first_in_call))
     return fail(h, r, "tensor-core operand split failed: %s", tc_last_error());
-  int gc = 0;  // chunk count
-  for (int x0 = 0; x0 < p->n_x; x0 += pl.nxl) {
-    const int nl = (p->n_x - x0) < pl.nxl ? (p->n_x - x0) : pl.nxl;
-    if (x0 > 0) CK(cudaStreamWaitEvent(st, h->ovl_ev[2], 0));  // the side has read the previous M
-    if (int r = tc_contract_l(s, p->qt, x0, nl, pl.nxl, M, tcs, wc, st, prof))
+  // l-chunk L's M: one buffer, or (tail form) two used in turn, so that the
+  // next l contraction can run before the last GEMM of the current l-chunk
+  // and the side stream prepares the next chunk's operands during that GEMM
+  auto mbuf = [&](int L) { return (pl.tail && M2 && (L & 1)) ? M2 : M; };
+  auto lcontract = [&](int L) -> int {
+    const int x0 = L * pl.nxl, nl = (p->n_x - x0) < pl.nxl ? (p->n_x - x0) : pl.nxl;
+    if (int r = tc_contract_l(s, p->qt, x0, nl, pl.nxl, mbuf(L), tcs, wc, st, prof))
       return fail(h, r, "tensor-core l contraction failed: %s", tc_last_error());
-    CK(cudaEventRecord(h->ovl_ev[1], st));
-    CK(cudaStreamWaitEvent(side, h->ovl_ev[1], 0));
+    return cudaEventRecord(h->ovl_ev[1], st) == cudaSuccess ? MODAL_OK
+                                                              : fail(h, MODAL_ECUDA, "event record failed");
+  };
+  const int nL = (p->n_x + pl.nxl - 1) / pl.nxl;
+  const bool ahead = pl.tail && M2;  // the next l contraction is issued before the last GEMM of an l-chunk
+  int gc = 0;  // chunk count
+  if (ahead && nL > 0)
+    if (int r = lcontract(0)) return r;
+  for (int L = 0; L < nL; ++L) {
+    const int x0 = L * pl.nxl, nl = (p->n_x - x0) < pl.nxl ? (p->n_x - x0) : pl.nxl;
+    if (!ahead) {
+      if (L > 0) CK(cudaStreamWaitEvent(st, h->ovl_ev[2], 0));  // the side has read the previous M
+      if (int r = lcontract(L)) return r;
+    }
+    CK(cudaStreamWaitEvent(side, h->ovl_ev[1], 0));  // l-chunk L's M is ready
+    const double *Mc = mbuf(L);
     for (int xs = x0; xs < x0 + nl; xs += pl.nxc, ++gc) {
       const int ns = (x0 + nl - xs) < pl.nxc ? (x0 + nl - xs) : pl.nxc;
       const int set = gc & 1;
-      const double *Ms = M + (size_t)(xs - x0) * s.n_mu * s.nbl * s.nbp;
+      const double *Ms = Mc + (size_t)(xs - x0) * s.n_mu * s.nbl * s.nbp;
       if (gc >= 2) CK(cudaStreamWaitEvent(side, h->ovl_gemm[set], 0));  // GEMM(gc - 2) used this set
       if (int r = tc_triple_prep(s, Ms, om, p->x_w, xs, ns, pl.nxl, pl.nxc, tcs, set, side, prof))
         return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
       CK(cudaEventRecord(h->ovl_prep[set], side));
+      if (ahead && xs + pl.nxc >= x0 + nl && L + 1 < nL) {
+        // before this l-chunk's last GEMM: the next l contraction, into the
+        // other M buffer once the side has read it (l-chunk L - 1)
+        if (L > 0) CK(cudaStreamWaitEvent(st, h->ovl_ev[2], 0));
+        if (int r = lcontract(L + 1)) return r;
+      }
       CK(cudaStreamWaitEvent(st, h->ovl_prep[set], 0));
-      if (int r = tc_triple_gemm(s, ns, pl.nxl, pl.nxc, G, gc > 0, tcs, set, wc, grid_sms, pl.tune, st, prof))
+      if (int r = tc_triple_gemm(s, ns, pl.nxl, pl.nxc, G, gc > 0, tcs, set, wc, grid_sms, pl.tune, pl.tail,
+                                 h->opt_split_k, st, prof))
         return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
       CK(cudaEventRecord(h->ovl_gemm[set], st));
     }
     CK(cudaEventRecord(h->ovl_ev[2], side));
   }
   CK(cudaStreamWaitEvent(st, h->ovl_ev[2], 0));  // nothing of the side stream outlives the call
+  if (pl.tail) {  // back on the call's stream
+    CK(cudaEventRecord(h->ovl_ev[4], st));
+    CK(cudaStreamWaitEvent(user, h->ovl_ev[4], 0));
+  }
   return MODAL_OK;
 }
 
@@ -576,12 +628,13 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
   const bool fa = pl.prec == MODAL_PREC_TF32 || pl.prec == MODAL_PREC_BF16X3;
   const int fa_kind = pl.prec == MODAL_PREC_TF32 ? TC_FORM_TF32 : TC_FORM_BF16X3;
   void *tcs = (pl.prec == MODAL_PREC_OZAKI_BF16)
-                  ? bp.take<char>(pl.overlap ? tc_ovl_scratch_bytes(s, pl.nxl, pl.nxc)
-                                             : tc_scratch_bytes(s, pl.nxl, pl.nxc, pl.variant))
+                  ? bp.take<char>((pl.overlap || pl.tail) ? tc_ovl_scratch_bytes(s, pl.nxl, pl.nxc)
+                                                          : tc_scratch_bytes(s, pl.nxl, pl.nxc, pl.variant))
                   : fa ? bp.take<char>(fa_scratch_bytes(s, pl.nxc)) : nullptr;
   double *mu = bp.take<double>(s.n_mu), *om = bp.take<double>(s.n_mu);
   double *A = bp.take<double>((size_t)s.n_mu * s.L);
   void *M = bp.take<char>(pl.elem * (size_t)pl.nxl * s.n_mu * s.nbl * s.nbp);
+  void *M2 = pl.tail ? bp.take<char>(pl.elem * (size_t)pl.nxl * s.n_mu * s.nbl * s.nbp) : nullptr;
   double *G = bp.take<double>((size_t)pl.Gsize);
   double *Gabs = pl.est ? bp.take<double>((size_t)pl.Gsize) : nullptr;
   const int nchunks = (p->n_x + pl.nxc - 1) / pl.nxc;
@@ -646,8 +699,10 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
     } else {
       // tensor-core form: the l contraction over an l-chunk of nxl points,
       // then the triple product over its chunks of nxc points
-      if (pl.overlap && h && !capturing) {  // every chunk, Y pass beside the GEMM
-        if (int r = run_tc_overlap(h, num_sms, p, pl, tcs, (double *)M, om, A, G, st, first_in_call)) return r;
+      if ((pl.overlap || pl.tail) && h && !capturing) {  // every chunk, Y pass beside the GEMM
+        if (int r = run_tc_overlap(h, num_sms, p, pl, tcs, (double *)M, (double *)M2, om, A, G, st,
+                                   first_in_call))
+          return r;
         break;
       }
       if (x0 % pl.nxl != 0) continue;
@@ -877,6 +932,7 @@ static int tune_tiles(modal_handle *h, const modal_problem *p, const modal_opts 
     if ((rr = plan_separable(h, &sub, o, q, h->num_sms)) != MODAL_OK) break;
     q.variant = c == 0 ? TC_TRIPLE_MATERIALISED : TC_TRIPLE_QUEUE;
     q.tune = c == 0 ? 0 : c - 1;
+    q.tail = false;  // the GEMM's own time, as the batched graph runs it
     void *scr;
     if ((rr = ws_get(h, 0, q.bytes, &scr)) != MODAL_OK) break;
     if ((rr = run_separable(h, h->num_sms, &sub, q, gamma, st, scr)) != MODAL_OK) break;

@@ -2966,9 +2966,14 @@ static size_t set_bytes(const SepShape &s, int nxc_max) {
   return SET_WORDS_BYTES + triple_bytes(s, nxc_max, TC_TRIPLE_MATERIALISED, false);
 }
 
+// two scratch sets, then the K-split partial sums of the one-CTA-per-tile
+// GEMM (one copy: the GEMMs of the chunks run one after the other)
+static size_t ovl_parts_bytes(const SepShape &s) {
+  return up256((size_t)(TRIPLE_KSPLIT_MAX - 1) * make_glayout(s.nbl, s.nbp).size() * 8);
+}
 size_t tc_ovl_scratch_bytes(const SepShape &s, int nxl, int nxc) {
   LScratch r = l_scratch(nullptr, s, nxl);
-  return (size_t)(r.end - (char *)nullptr) + 2 * set_bytes(s, nxc) + 1024;
+  return (size_t)(r.end - (char *)nullptr) + 2 * set_bytes(s, nxc) + ovl_parts_bytes(s) + 1024;
 }
 
 __global__ void k_init_set_words(int *w) {
@@ -3044,8 +3049,8 @@ cuda_fail:
 }
 
 int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double *G, bool accumulate,
-                   void *scratch, int set, long long wait_cycles, int grid_sms, int tune, cudaStream_t st,
-                   Profiler *prof) {
+                   void *scratch, int set, long long wait_cycles, int grid_sms, int tune, bool single,
+                   int split_k, cudaStream_t st, Profiler *prof) {
   LScratch ls = l_scratch(scratch, s, nxl_max);
   SetScratch r = set_scratch(scratch, s, nxl_max, nxc_max, set, nxc);
   const int64_t K = (int64_t)nxc * s.n_mu;
@@ -3082,19 +3087,40 @@ int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double 
   P.err = ls.words;
   P.g = gl;
   P.wait_cycles = wait_cycles;
-  const int rq = launch_queue_gemm(P, ta, tb, s.nbl, grid_sms, wmax, tune_split(tune), r.sw + 3, st, prof);
-  if (rq != MODAL_EUNSUPPORTED) return rq;
-  // more items than the queue table holds: one CTA per tile
+  if (!single) {
+    const int rq = launch_queue_gemm(P, ta, tb, s.nbl, grid_sms, wmax, tune_split(tune), r.sw + 3, st, prof);
+    if (rq != MODAL_EUNSUPPORTED) return rq;
+  }
+  // one CTA per tile, or per K range of one (single), or the queue's
+  // fallback when it has more items than its table holds
   unsigned used1 = 0;
   for (int b = 0; b < s.nbl; ++b) used1 |= 1u << (g_tile_width(gl.cols(b)) / 16 - 1);
   if (int rr = make_bmaps(&tb, r.Bt, nblp, Kpad, used1)) return rr;
   fill_mma_plans(P.plan);
   int64_t tiles = 0;
   for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(gl.rows(b), OZ_BM) * cdiv64(gl.cols(b), OZ_BN);
+  if (single) {
+    // no K splits by default: here the operand passes of the next chunk
+    // fill the SMs that the last wave of whole tiles leaves idle
+    P.ksplit = 1;
+    P.chunks_per_split = P.nchunks;
+    if (split_k > 0) {  // a caller's choice (MODAL_OPT_TC_SPLIT_K)
+      P.chunks_per_split = (int)cdiv64(P.nchunks, std::min(split_k, TRIPLE_KSPLIT_MAX));
+      P.ksplit = (int)cdiv64(P.nchunks, P.chunks_per_split);
+    }
+    P.part_stride = gl.size();
+    P.out_part = (double *)(ls.end + 2 * set_bytes(s, nxc_max));
+  }
   if ((e = cudaFuncSetAttribute(k_ozaki_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) ==
       cudaSuccess) {
     ProfScope ps(prof, "tc_gemm_triple", st);
-    k_ozaki_gemm<1><<<(unsigned)tiles, OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    const int ks = P.ksplit > 1 ? P.ksplit : 1;
+    k_ozaki_gemm<1><<<(unsigned)(tiles * ks), OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && P.ksplit > 1) {
+    ProfScope ps(prof, "tc_add_parts", st);
+    k_add_parts<<<(unsigned)cdiv64(gl.size(), 256), 256, 0, st>>>(G, P.out_part, P.ksplit - 1, gl.size());
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

@@ -52,7 +52,11 @@ def test_batched_uneven_models(mg, precision, tol):
 def test_batched_streams(mg, streams):
     """The batch spread over concurrent streams (MODAL_OPT_BATCH_STREAMS; 0 =
     chosen by timing on the first call): each result equals the single-problem
-    entry point on the same inputs, and the replayed graph reads new data."""
+    entry point on the same inputs -- to the rounding of the FP64 sums of the
+    exact chunk products, since a single-problem call overlaps its operand
+    passes with the previous chunk's GEMM and may group the K chunks
+    differently from the graph's one-stream form -- and the replayed graph
+    reads new data."""
     probs = syn.batched_models(n=7, scale=0.03, base_seed=2000)
     h = mg.Handle()
     mg.set_option(mg.OPT_BATCH_STREAMS, streams, handle=h)
@@ -62,13 +66,13 @@ def test_batched_streams(mg, streams):
     singles = [mg.project_separable(dp, precision=2, handle=h).cpu().numpy() for dp in dps]
     mg.handle_status(handle=h)
     for g, ref in zip(gs, singles):
-        assert normwise(g, ref) < 1e-12
+        assert normwise(g, ref) < 1e-11
     for dp in dps:
         dp.qt.mul_(2.0)
     gs2 = mg.project_separable_batched(dps, precision=2, outs=gs, handle=h)
     mg.handle_status(handle=h)
     for g, ref in zip(gs2, singles):   # cubic in q~: factor 8
-        assert normwise(g, 8.0 * ref) < 1e-12
+        assert normwise(g, 8.0 * ref) < 1e-11
     h.close()
 
 

@@ -45,6 +45,10 @@ def test_error_estimate_and_conditioned_check(mg, shape, precision, tol_est, tol
 
 
 def test_estimate_leaves_the_projection_unchanged(mg):
+    """FP64: bit for bit.  Tensor-core form: a call with an error estimate runs
+    its passes on one stream (the plain call overlaps the operand passes with
+    the previous chunk's GEMM and may group the K chunks differently), so the
+    two agree to the rounding of the FP64 sums of the exact chunk products."""
     P = syn.cpu_size()
     dp = mg.DeviceProblem.from_host(P)
     for precision in (0, 2):
@@ -52,7 +56,10 @@ def test_estimate_leaves_the_projection_unchanged(mg):
         est = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device=dp.device)
         g = mg.project_separable(dp, precision=precision, error_estimate=est).cpu().numpy()
         mg.handle_status()
-        assert np.array_equal(g, plain)
+        if precision == 0:
+            assert np.array_equal(g, plain)
+        else:
+            assert np.abs(g - plain).max() <= 1e-11 * np.abs(plain).max()
 
 
 def test_negative_radial_weights(mg):

@@ -179,3 +179,24 @@ def test_overlap_planck(mg):
     got = g.cpu().numpy()[np.ix_(late_pick, prim_pick)]
     assert np.abs(got - ref).max() / np.abs(ref).max() < TOL_MIXED
     h.close()
+
+
+@pytest.mark.parametrize("shape,x_chunk", [((300, 8, 8, 100), 8), ((200, 6, 6, 150), 16), ((120, 5, 5, 7), 0)])
+def test_tail_overlap_separable(mg, shape, x_chunk):
+    """The operand and Y passes on a second stream beside the previous
+    chunk's GEMM (MODAL_OPT_TC_OVERLAP_TAIL, on by default), the next l
+    contraction issued before an l-chunk's last GEMM into the other M buffer:
+    several l-chunks (64 radial points each) and ragged last chunks, against
+    the oracle and against the one-stream form."""
+    lmax, nbl, nbp, nx = shape
+    P = syn.make_problem(lmax, nbl, nx, seed=95, nb_prim=nbp)
+    h = mg.Handle()
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    g = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, x_chunk=x_chunk, handle=h)
+    mg.handle_status(handle=h)
+    assert normwise(g, oracle.separable(P)) < TOL_MIXED
+    mg.set_option(mg.OPT_TC_OVERLAP_TAIL, 0, handle=h)
+    g0 = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, x_chunk=x_chunk, handle=h).cpu().numpy()
+    mg.handle_status(handle=h)
+    assert normwise(g, g0) < TOL_FORMS
+    h.close()
