@@ -242,7 +242,11 @@ int modal_contract_l(modal_handle *h, const modal_problem *prob, int32_t n_mu,
  * the Modal2D listing.  gamma: device [n_late][n_prim] FP64 (overwritten).
  * Exact (up to rounding) when n_mu >= (3 l_max + 1)/2; smaller n_mu is
  * rejected with MODAL_EINVAL unless opts->allow_inexact_gl. opts may be NULL
- * (FP64, automatic n_mu).  Stream-ordered, no host synchronisation. */
+ * (FP64, automatic n_mu).  Stream-ordered, no host synchronisation; a call
+ * that runs passes on the handle's own streams (MODAL_OPT_TC_OVERLAP_TAIL)
+ * forks from and joins the caller's stream with events, so the call can be
+ * captured in a CUDA graph once the handle has served a call of the same
+ * sizes (its scratch is then allocated). */
 int modal_project_separable(modal_handle *h, const modal_problem *prob,
                             const modal_opts *opts, double *gamma, modal_stream_t stream);
 

@@ -200,3 +200,33 @@ def test_tail_overlap_separable(mg, shape, x_chunk):
     mg.handle_status(handle=h)
     assert normwise(g, g0) < TOL_FORMS
     h.close()
+
+
+def test_tail_overlap_graph_capture(mg):
+    """A single-problem call with its passes on the handle's second and
+    high-priority streams forks from and joins the caller's stream with
+    events, so it can be captured into a CUDA graph (after one call has sized
+    the scratch); replays match the oracle, also after new tables are copied
+    into the same device buffers."""
+    P = syn.make_problem(200, 6, 70, seed=97)
+    h = mg.Handle()
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    out = torch.empty(P.n_late, P.n_prim, dtype=torch.float64, device="cuda")
+    mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, out=out, x_chunk=8, handle=h)
+    mg.handle_status(handle=h)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
+        mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, out=out, x_chunk=8, handle=h)
+    out.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert normwise(out, oracle.separable(P)) < TOL_MIXED
+    P2 = syn.make_problem(200, 6, 70, seed=98)
+    dp.qt.copy_(torch.tensor(P2.qt))
+    dp.q.copy_(torch.tensor(P2.q))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert normwise(out, oracle.separable(P2)) < TOL_MIXED
+    h.close()
