@@ -51,11 +51,12 @@ typedef struct CUstream_st *modal_stream_t;
                                     chunk sums, FP64 accumulation */
 #define MODAL_PREC_TF32 3        /* l contraction on tcgen05 in TF32 (kind::tf32,
                                     one product, FP32 accumulation); triple
-                                    product as MODAL_PREC_FP32 (FP32 products,
-                                    compensated sums of the slices) */
+                                    product of the FP64 M as MODAL_PREC_OZAKI_BF16
+                                    (exact slicing: the error is the l
+                                    contraction's) */
 #define MODAL_PREC_BF16X3 4      /* l contraction on tcgen05 with BF16 hi/lo
                                     operands, hi hi' + hi lo' + lo hi' (FP32
-                                    accumulation); triple product as FP32 */
+                                    accumulation); triple product as for TF32 */
 
 /* radial quadrature (modal_x_weights) */
 #define MODAL_XW_TRAPEZOID 0  /* trapezium rule (Section 3.2.4), times x^2 */

@@ -460,19 +460,21 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   if (int r = resolve_opts(h, p, o, n_mu, prec, xch)) return r;
   pl.s = SepShape{p->l_min, p->l_max, p->l_max - p->l_min + 1, p->nb_late, p->nb_prim, p->n_x, n_mu};
   pl.prec = prec;
-  const bool m_f32 = prec == MODAL_PREC_FP32 || prec == MODAL_PREC_TF32 || prec == MODAL_PREC_BF16X3;
+  // the TF32 / BF16x3 l contractions hand FP64 M to the tensor-core triple product
+  const bool fa_form = prec == MODAL_PREC_TF32 || prec == MODAL_PREC_BF16X3;
+  const bool m_f32 = prec == MODAL_PREC_FP32;
   pl.elem = m_f32 ? sizeof(float) : sizeof(double);
   const int64_t nblp = (int64_t)p->nb_late * p->nb_prim;
   if (xch > 0) {
     pl.nxc = xch < p->n_x ? xch : p->n_x;
-  } else if (prec == MODAL_PREC_OZAKI_BF16) {
+  } else if (prec == MODAL_PREC_OZAKI_BF16 || fa_form) {
     // per radial point: M (FP64), its double-FP32 copy and its 5 BF16 slices,
     // the 5 slices of the q~ rows of the l contraction and, unless Y is formed
     // in shared memory, the 5 BF16 slices of Y (which then dominate)
     const int64_t L = p->l_max - p->l_min + 1;
     int64_t per_x = 26 * (int64_t)n_mu * nblp + 10 * (int64_t)p->nb_prim * L;
     int64_t budget = (int64_t)2 << 30;
-    if (y_hbm) {
+    if (y_hbm || fa_form) {
       // 11 GiB: eight radial points per chunk at Planck size, where the
       // per-launch set-up of the GEMM tiles and the Y pass amortise best
       // (measured: 4.06 M slices/s against 3.99 M with four and 3.95 M with 16)
@@ -520,7 +522,8 @@ static int plan_separable(modal_handle *h, const modal_problem *p, const modal_o
   if (prec == MODAL_PREC_OZAKI_BF16)
     b += (pl.overlap || pl.tail) ? tc_ovl_scratch_bytes(pl.s, pl.nxl, pl.nxc)
                                  : tc_scratch_bytes(pl.s, pl.nxl, pl.nxc, pl.variant);
-  if (prec == MODAL_PREC_TF32 || prec == MODAL_PREC_BF16X3) b += fa_scratch_bytes(pl.s, pl.nxc);
+  if (fa_form)  // the l contraction's scratch (status word first), then the triple product's
+    b += align256(fa_scratch_bytes(pl.s, pl.nxc)) + tc_scratch_bytes(pl.s, pl.nxc, pl.nxc, TC_TRIPLE_MATERIALISED);
   pl.bytes = b + 1024;
   return MODAL_OK;
 }
@@ -631,6 +634,8 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
                   ? bp.take<char>((pl.overlap || pl.tail) ? tc_ovl_scratch_bytes(s, pl.nxl, pl.nxc)
                                                           : tc_scratch_bytes(s, pl.nxl, pl.nxc, pl.variant))
                   : fa ? bp.take<char>(fa_scratch_bytes(s, pl.nxc)) : nullptr;
+  // TF32 / BF16x3: the tensor-core triple product's scratch after the l contraction's
+  void *fa_tc = fa ? bp.take<char>(tc_scratch_bytes(s, pl.nxc, pl.nxc, TC_TRIPLE_MATERIALISED)) : nullptr;
   double *mu = bp.take<double>(s.n_mu), *om = bp.take<double>(s.n_mu);
   double *A = bp.take<double>((size_t)s.n_mu * s.L);
   void *M = bp.take<char>(pl.elem * (size_t)pl.nxl * s.n_mu * s.nbl * s.nbp);
@@ -672,17 +677,27 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
         CK(launch_triple<double>(s, (double *)M, om, p->x_w, x0, nxc, pl.ksplit, Gabs, Gpart, c > 0,
                                  num_sms, st, true));
       }
-    } else if (pl.prec == MODAL_PREC_FP32 || fa) {
-      if (fa) {
-        // the l contraction on the tensor cores with FP32 accumulation
-        Profiler *prof = (h && h->prof.on && !capturing) ? &h->prof : nullptr;
-        if (c == 0)
-          if (int r = fa_prepare_l(fa_kind, s, A, p->q, tcs, pl.nxc, st, prof, first_in_call))
-            return fail(h, r, "tensor-core operand split failed: %s", fa_last_error());
-        const long long wc = h ? h->wait_cycles : TC_DEFAULT_WAIT_CYCLES;
-        if (int r = fa_contract_l(fa_kind, s, p->qt, x0, nxc, pl.nxc, M, false, tcs, wc, st, prof))
-          return fail(h, r, "tensor-core l contraction failed: %s", fa_last_error());
-      } else {
+    } else if (fa) {
+      // the l contraction on the tensor cores with FP32 accumulation (FP64
+      // M), then the exact-slicing triple product of the tensor-core form
+      Profiler *prof = (h && h->prof.on && !capturing) ? &h->prof : nullptr;
+      const long long wc = h ? h->wait_cycles : TC_DEFAULT_WAIT_CYCLES;
+      if (c == 0) {
+        if (int r = fa_prepare_l(fa_kind, s, A, p->q, tcs, pl.nxc, st, prof, first_in_call))
+          return fail(h, r, "tensor-core operand split failed: %s", fa_last_error());
+        CK(tc_init_words(fa_tc, s, pl.nxc, 1, st));
+      }
+      if (int r = fa_contract_l(fa_kind, s, p->qt, x0, nxc, pl.nxc, M, true, tcs, wc, st, prof))
+        return fail(h, r, "tensor-core l contraction failed: %s", fa_last_error());
+      CK(tc_init_words(fa_tc, s, pl.nxc, 0, st));
+      int r = tc_triple_chunk(s, (const double *)M, om, p->x_w, x0, nxc, pl.nxc, G, c > 0, fa_tc, wc, num_sms,
+                              TC_TRIPLE_MATERIALISED, h ? h->opt_split_k : 0, st, prof, false, 0);
+      if (!r && Gabs)
+        r = tc_triple_chunk(s, (const double *)M, om, p->x_w, x0, nxc, pl.nxc, Gabs, c > 0, fa_tc, wc, num_sms,
+                            TC_TRIPLE_MATERIALISED, h ? h->opt_split_k : 0, st, prof, true, 0);
+      if (r) return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
+    } else if (pl.prec == MODAL_PREC_FP32) {
+      {
         PROF(h, "contract_l_f32", st);
         CK(launch_contract_l<float>(s, A, p->q, p->qt, x0, nxc, (float *)M, st));
       }
@@ -729,6 +744,8 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
       }
     }
   }
+  if (fa && nchunks > 0)  // the triple product's status joins the l contraction's word
+    CK(tc_or_status(fa_error_word(tcs), fa_tc, st));
   if ((pl.prec == MODAL_PREC_OZAKI_BF16 || fa) && nchunks > 0 && !capturing && h) {
     // surface a bounded-wait give-up through modal_handle_status (no sync here)
     CK(cudaMemcpyAsync(h->pinned_err, fa ? fa_error_word(tcs) : tc_error_word(tcs), sizeof(int),
@@ -739,8 +756,8 @@ static int run_separable(modal_handle *h, int num_sms, const modal_problem *p, c
   }
   PROFN(h, "gather", st, Gabs ? 2 : 1);
   // the tensor-core triple product's layout of G depends on its variant
-  const GLayout gl = (pl.prec == MODAL_PREC_OZAKI_BF16 && !fa) ? tc_triple_glayout(s, pl.variant)
-                                                               : make_glayout(s.nbl, s.nbp);
+  const GLayout gl = pl.prec == MODAL_PREC_OZAKI_BF16 ? tc_triple_glayout(s, pl.variant)
+                     : fa ? tc_triple_glayout(s, TC_TRIPLE_MATERIALISED) : make_glayout(s.nbl, s.nbp);
   CK(launch_gather(s, G, p->late_modes, p->prim_modes, p->n_late, p->n_prim, 1.0 / (48.0 * MODAL_PI), gamma,
                    st, &gl));                                                               // a7
   if (Gabs)

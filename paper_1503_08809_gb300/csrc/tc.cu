@@ -4158,6 +4158,22 @@ int tc_project_direct(const modal_problem *p, const int *grid, const double *dw,
 }
 #undef DTC_CK
 
+// status words of a triple-product scratch used without the l contraction
+// of this form: mode 1 at the start of a call (error bits and all maxima),
+// mode 0 before each chunk (the maxima)
+cudaError_t tc_init_words(void *scratch, const SepShape &s, int nxl_max, int mode, cudaStream_t st) {
+  const LScratch r = l_scratch(scratch, s, nxl_max);
+  k_init_words<<<1, 32, 0, st>>>(r.words, mode);
+  return cudaGetLastError();
+}
+__global__ void k_or_word(int *dst, const int *src) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dst |= *src;
+}
+cudaError_t tc_or_status(int *dst, void *scratch, cudaStream_t st) {
+  k_or_word<<<1, 32, 0, st>>>(dst, (const int *)scratch);
+  return cudaGetLastError();
+}
+
 int *tc_error_word(void *scratch) { return (int *)scratch; }
 
 void tc_release(int) {}

@@ -73,6 +73,11 @@ int tc_project_direct(const modal_problem *p, const int *grid, const double *dw,
                       void *scratch, int num_sms, long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
 // Layout of G that the triple product of a variant fills (the gather reads it)
 GLayout tc_triple_glayout(const SepShape &s, int variant);
+// status words of a triple-product scratch driven without this form's l
+// contraction (mode 1: call start, 0: per chunk), and the OR of its error
+// bits into another status word
+cudaError_t tc_init_words(void *scratch, const SepShape &s, int nxl_max, int mode, cudaStream_t st);
+cudaError_t tc_or_status(int *dst, void *scratch, cudaStream_t st);
 // device status word of the tensor-core scratch (bit 0: a bounded wait gave up,
 // bit 1: a value outside the FP32 exponent range of the split operands)
 int *tc_error_word(void *scratch);

@@ -88,3 +88,24 @@ def test_fa_batched(mg):
         assert normwise(g, single) < 1e-6
         assert normwise(g, oracle.separable(P)) < TOL_GAMMA["tf32"]
     h.close()
+
+
+@pytest.mark.parametrize("form", ["tf32", "bf16x3"])
+def test_fa_bounded_wait_status(mg, form):
+    """A one-clock wait bound makes both the l contraction's and the tensor-core
+    triple product's waits give up: the call reports MODAL_ETIMEOUT through
+    its single status word, and the next call with the default bound is
+    right."""
+    P = syn.make_problem(30, 4, 5, seed=12)
+    dp = mg.DeviceProblem.from_host(P)
+    h = mg.Handle()
+    mg.set_wait_limit(1, handle=h)
+    mg.project_separable(dp, precision=prec_of(mg, form), handle=h)
+    with pytest.raises(mg.ModalError) as ei:
+        mg.handle_status(handle=h)
+    assert ei.value.code == 4        # MODAL_ETIMEOUT
+    mg.set_wait_limit(0, handle=h)
+    g = mg.project_separable(dp, precision=prec_of(mg, form), handle=h)
+    mg.handle_status(handle=h)
+    assert normwise(g, oracle.separable(P)) < TOL_GAMMA[form]
+    h.close()
