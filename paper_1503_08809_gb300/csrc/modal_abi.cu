@@ -50,6 +50,7 @@ struct modal_handle {
   cudaStream_t ovl_hi = nullptr;  // high-priority stream of the GEMMs in the tail-overlap form
   cudaEvent_t ovl_ev[6] = {};     // fork, l contraction done, side done, prep[2] / gemm[2] (below)
   cudaEvent_t ovl_prep[2] = {}, ovl_gemm[2] = {};
+  cudaEvent_t ovl_prep2[2] = {};  // tail form: the second half of a chunk's Y rows is ready
   // tile shape chosen per problem bucket (tile_bucket): 0 = one CTA per tile,
   // 1 + tune = the queue form with that tile shape
   std::unordered_map<uint64_t, int> tile_choice;
@@ -223,6 +224,7 @@ int modal_handle_destroy(modal_handle *h) {
     if (h->ovl_ev[i]) cudaEventDestroy(h->ovl_ev[i]);
   for (int i = 0; i < 2; ++i) {
     if (h->ovl_prep[i]) cudaEventDestroy(h->ovl_prep[i]);
+    if (h->ovl_prep2[i]) cudaEventDestroy(h->ovl_prep2[i]);
     if (h->ovl_gemm[i]) cudaEventDestroy(h->ovl_gemm[i]);
   }
   if (h->err_event) cudaEventDestroy(h->err_event);
@@ -550,6 +552,7 @@ static int run_tc_overlap(modal_handle *h, int num_sms, const modal_problem *p, 
     if (!h->ovl_ev[i]) CK(cudaEventCreateWithFlags(&h->ovl_ev[i], cudaEventDisableTiming));
   for (int i = 0; i < 2; ++i) {
     if (!h->ovl_prep[i]) CK(cudaEventCreateWithFlags(&h->ovl_prep[i], cudaEventDisableTiming));
+    if (!h->ovl_prep2[i]) CK(cudaEventCreateWithFlags(&h->ovl_prep2[i], cudaEventDisableTiming));
     if (!h->ovl_gemm[i]) CK(cudaEventCreateWithFlags(&h->ovl_gemm[i], cudaEventDisableTiming));
   }
   cudaStream_t side = h->ovl_stream;
@@ -596,9 +599,17 @@ static int run_tc_overlap(modal_handle *h, int num_sms, const modal_problem *p, 
       const int set = gc & 1;
       const double *Ms = Mc + (size_t)(xs - x0) * s.n_mu * s.nbl * s.nbp;
       if (gc >= 2) CK(cudaStreamWaitEvent(side, h->ovl_gemm[set], 0));  // GEMM(gc - 2) used this set
-      if (int r = tc_triple_prep(s, Ms, om, p->x_w, xs, ns, pl.nxl, pl.nxc, tcs, set, side, prof))
+      // tail form: the Y rows in two halves (the G blocks of each expansion),
+      // so that the GEMM of the first half runs while the second is formed
+      if (int r = tc_triple_prep(s, Ms, om, p->x_w, xs, ns, pl.nxl, pl.nxc, tcs, set, pl.tail ? 0 : -1, side,
+                                 prof))
         return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
       CK(cudaEventRecord(h->ovl_prep[set], side));
+      if (pl.tail) {
+        if (int r = tc_triple_prep(s, Ms, om, p->x_w, xs, ns, pl.nxl, pl.nxc, tcs, set, 1, side, prof))
+          return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
+        CK(cudaEventRecord(h->ovl_prep2[set], side));
+      }
       if (ahead && xs + pl.nxc >= x0 + nl && L + 1 < nL) {
         // before this l-chunk's last GEMM: the next l contraction, into the
         // other M buffer once the side has read it (l-chunk L - 1)
@@ -607,8 +618,14 @@ static int run_tc_overlap(modal_handle *h, int num_sms, const modal_problem *p, 
       }
       CK(cudaStreamWaitEvent(st, h->ovl_prep[set], 0));
       if (int r = tc_triple_gemm(s, ns, pl.nxl, pl.nxc, G, gc > 0, tcs, set, wc, grid_sms, pl.tune, pl.tail,
-                                 h->opt_split_k, st, prof))
+                                 h->opt_split_k, pl.tail ? 0 : -1, st, prof))
         return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
+      if (pl.tail) {
+        CK(cudaStreamWaitEvent(st, h->ovl_prep2[set], 0));
+        if (int r = tc_triple_gemm(s, ns, pl.nxl, pl.nxc, G, true, tcs, set, wc, grid_sms, pl.tune, true,
+                                   h->opt_split_k, 1, st, prof))
+          return fail(h, r, "tensor-core triple product failed: %s", tc_last_error());
+      }
       CK(cudaEventRecord(h->ovl_gemm[set], st));
     }
     CK(cudaEventRecord(h->ovl_ev[2], side));

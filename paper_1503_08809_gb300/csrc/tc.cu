@@ -262,6 +262,7 @@ struct OzParams {
   int ksplit, chunks_per_split;
   double *out_part;
   int64_t part_stride;
+  int tile0;  // OUT_MODE 1: first tile of the launch (tiles in block order)
 };
 
 
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     C = min((int64_t)OZ_BN, P.rowsB - b_row0);
   } else {
     const int ks = P.ksplit > 1 ? P.ksplit : 1;
-    int t = (int)blockIdx.x / ks, rt = 0, ct = 0;
+    int t = (int)blockIdx.x / ks + P.tile0, rt = 0, ct = 0;
     if (ks > 1) {
       kc0 = ((int)blockIdx.x % ks) * P.chunks_per_split;
       nchk = min(P.chunks_per_split, P.nchunks - kc0);
@@ -1619,7 +1620,7 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float2 v) {
   return *reinterpret_cast<const uint32_t *>(&p);
 }
 
-__global__ void __launch_bounds__(32 * TY_WARPS) k_tp_make_y(GLayout g, int64_t rowsY, int64_t K, int Kpad, int nbp, int nblp,
+__global__ void __launch_bounds__(32 * TY_WARPS) k_tp_make_y(GLayout g, int pair0, int64_t rowsY, int64_t K, int Kpad, int nbp, int nblp,
                                                          int P2, const f2 *__restrict__ Mdf,
                                                          const int *__restrict__ eY, __nv_bfloat16 *__restrict__ Ysl) {
   extern __shared__ __align__(16) unsigned char ty_sm[];
@@ -1628,8 +1629,9 @@ __global__ void __launch_bounds__(32 * TY_WARPS) k_tp_make_y(GLayout g, int64_t 
   // normal float, else as two exact factors; (0, 0) for an all-zero row
   float2 *Fs = reinterpret_cast<float2 *>(ty_sm + (size_t)2 * nbp * TY_LD * sizeof(float));
   int a, b;
-  g.y_pair(blockIdx.x, a, b);  // the block's pair a <= b (Y pair blockIdx.x of the layout)
-  const int64_t row0 = (int64_t)blockIdx.x * P2;
+  const int jp = pair0 + (int)blockIdx.x;  // the block's Y pair of the layout
+  g.y_pair(jp, a, b);
+  const int64_t row0 = (int64_t)jp * P2;
   const int64_t kb = (int64_t)blockIdx.y * TY_K;
   const int ch = (int)(kb / OZ_KC);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2424,11 +2426,12 @@ static double plan_step_cost(const uint32_t (&plan)[1 + OZ_PLAN_MAX], int w) {
 // GEMM), which levels the last wave when the tiles are few and large.  Chooses ks = 1 .. 4 of least
 // modelled makespan (each CTA also pays half a chunk of set-up and drain).
 // G += part 0 + part 1 + ... (the K splits beyond the first, in order)
-__global__ void k_add_parts(double *__restrict__ G, const double *__restrict__ parts, int nparts, int64_t n) {
+__global__ void k_add_parts(double *__restrict__ G, const double *__restrict__ parts, int nparts, int64_t n,
+                            int64_t stride) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double v = G[i];
-  for (int k = 0; k < nparts; ++k) v += parts[(int64_t)k * n + i];
+  for (int k = 0; k < nparts; ++k) v += parts[(int64_t)k * stride + i];
   G[i] = v;
 }
 static void triple_ksplit_choice(OzParams &P, int num_sms) {
@@ -2617,7 +2620,7 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
           cudaSuccess)
         goto cuda_fail;
       k_tp_make_y<<<dim3((unsigned)gl.ypairs_total(), (unsigned)cdiv64(Kpad, TY_K)), 32 * TY_WARPS, smy, st>>>(
-          gl, rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, eY, Ysl);
+          gl, 0, rowsY, K, Kpad, s.nbp, nblp, P2, Mdf, eY, Ysl);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
     CUtensorMap ta;
@@ -2682,7 +2685,8 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
     }
     if (P.ksplit > 1) {
       ProfScope ps(prof, "tc_add_parts", st);
-      k_add_parts<<<(unsigned)cdiv64(gl.size(), 256), 256, 0, st>>>(G, P.out_part, P.ksplit - 1, gl.size());
+      k_add_parts<<<(unsigned)cdiv64(gl.size(), 256), 256, 0, st>>>(G, P.out_part, P.ksplit - 1, gl.size(),
+                                                                      gl.size());
       if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
     }
     return MODAL_OK;
@@ -3009,7 +3013,7 @@ static SetScratch set_scratch(void *scratch, const SepShape &s, int nxl_max, int
 }
 
 int tc_triple_prep(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
-                   int nxl_max, int nxc_max, void *scratch, int set, cudaStream_t st, Profiler *prof) {
+                   int nxl_max, int nxc_max, void *scratch, int set, int part, cudaStream_t st, Profiler *prof) {
   LScratch ls = l_scratch(scratch, s, nxl_max);
   SetScratch r = set_scratch(scratch, s, nxl_max, nxc_max, set, nxc);
   const int64_t K = (int64_t)nxc * s.n_mu;
@@ -3019,8 +3023,12 @@ int tc_triple_prep(const SepShape &s, const double *M, const double *om, const d
   const int P2 = s.nbp * (s.nbp + 1) / 2;
   const GLayout gl = tc_triple_glayout(s, TC_TRIPLE_QUEUE);
   const int64_t rowsY = (int64_t)gl.ypairs_total() * P2;
+  // part 0: M~, B slices, Y exponents and the Y rows of the first-form
+  // blocks; part 1: the Y rows of the others; part < 0: everything
+  const int pmid = gl.ypair0(gl.h < gl.nbl ? gl.h : gl.nbl);
+  const int p0 = part == 1 ? pmid : 0, p1 = part == 0 ? pmid : gl.ypairs_total();
   cudaError_t e;
-  {
+  if (part != 1) {
     ProfScope ps(prof, "tc_prep_M", st, 3);
     k_init_set_words<<<1, 32, 0, st>>>(r.sw);
     if ((e = cudaMemsetAsync(r.colmax, 0, (size_t)nch * nblp * 8, st)) != cudaSuccess) goto cuda_fail;
@@ -3031,15 +3039,17 @@ int tc_triple_prep(const SepShape &s, const double *M, const double *om, const d
   }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   {
-    ProfScope ps(prof, "tc_make_Y", st, 2);
-    k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(gl, rowsY, s.nbp, nblp, P2,
-                                                                                r.mxW, r.eY, r.sw + 1);
+    ProfScope ps(prof, "tc_make_Y", st, part == 1 ? 1 : 2);
+    if (part != 1)
+      k_tp_y_exp<<<dim3((unsigned)cdiv64(rowsY, 256), (unsigned)nch), 256, 0, st>>>(gl, rowsY, s.nbp, nblp, P2,
+                                                                                  r.mxW, r.eY, r.sw + 1);
     const size_t smy = ty_smem_bytes(s.nbp);
     if ((e = cudaFuncSetAttribute(k_tp_make_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) !=
         cudaSuccess)
       goto cuda_fail;
-    k_tp_make_y<<<dim3((unsigned)gl.ypairs_total(), (unsigned)cdiv64(Kpad, TY_K)), 32 * TY_WARPS, smy, st>>>(
-        gl, rowsY, K, Kpad, s.nbp, nblp, P2, r.Mdf, r.eY, r.Ysl);
+    if (p1 > p0)
+      k_tp_make_y<<<dim3((unsigned)(p1 - p0), (unsigned)cdiv64(Kpad, TY_K)), 32 * TY_WARPS, smy, st>>>(
+          gl, p0, rowsY, K, Kpad, s.nbp, nblp, P2, r.Mdf, r.eY, r.Ysl);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   return MODAL_OK;
@@ -3050,7 +3060,7 @@ cuda_fail:
 
 int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double *G, bool accumulate,
                    void *scratch, int set, long long wait_cycles, int grid_sms, int tune, bool single,
-                   int split_k, cudaStream_t st, Profiler *prof) {
+                   int split_k, int part, cudaStream_t st, Profiler *prof) {
   LScratch ls = l_scratch(scratch, s, nxl_max);
   SetScratch r = set_scratch(scratch, s, nxl_max, nxc_max, set, nxc);
   const int64_t K = (int64_t)nxc * s.n_mu;
@@ -3097,8 +3107,16 @@ int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double 
   for (int b = 0; b < s.nbl; ++b) used1 |= 1u << (g_tile_width(gl.cols(b)) / 16 - 1);
   if (int rr = make_bmaps(&tb, r.Bt, nblp, Kpad, used1)) return rr;
   fill_mma_plans(P.plan);
-  int64_t tiles = 0;
-  for (int b = 0; b < s.nbl; ++b) tiles += cdiv64(gl.rows(b), OZ_BM) * cdiv64(gl.cols(b), OZ_BN);
+  // tiles of the blocks of the part (single form): first-form blocks, the
+  // others, or all
+  int64_t tiles = 0, tile0 = 0;
+  for (int b = 0; b < s.nbl; ++b) {
+    const int64_t n = cdiv64(gl.rows(b), OZ_BM) * cdiv64(gl.cols(b), OZ_BN);
+    const bool in = part < 0 || (part == 0) == gl.first(b);
+    if (in) tiles += n;
+    else if (part == 1) tile0 += n;  // the first-form blocks come first
+  }
+  P.tile0 = (int)tile0;
   if (single) {
     // no K splits by default: here the operand passes of the next chunk
     // fill the SMs that the last wave of whole tiles leaves idle
@@ -3115,12 +3133,17 @@ int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double 
       cudaSuccess) {
     ProfScope ps(prof, "tc_gemm_triple", st);
     const int ks = P.ksplit > 1 ? P.ksplit : 1;
-    k_ozaki_gemm<1><<<(unsigned)(tiles * ks), OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    if (tiles > 0) k_ozaki_gemm<1><<<(unsigned)(tiles * ks), OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess && P.ksplit > 1) {
+  if (e == cudaSuccess && P.ksplit > 1 && tiles > 0) {
+    // the part's blocks are contiguous in G: [offset(first), offset(last + 1))
+    int bl0 = 0, bl1 = s.nbl;
+    if (part == 0) bl1 = gl.h < s.nbl ? gl.h : s.nbl;
+    if (part == 1) bl0 = gl.h < s.nbl ? gl.h : s.nbl;
+    const int64_t g0 = gl.offset(bl0), n = gl.offset(bl1) - g0;
     ProfScope ps(prof, "tc_add_parts", st);
-    k_add_parts<<<(unsigned)cdiv64(gl.size(), 256), 256, 0, st>>>(G, P.out_part, P.ksplit - 1, gl.size());
+    k_add_parts<<<(unsigned)cdiv64(n, 256), 256, 0, st>>>(G + g0, P.out_part + g0, P.ksplit - 1, n, gl.size());
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

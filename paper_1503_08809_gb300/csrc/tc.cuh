@@ -41,13 +41,18 @@ int tc_triple_chunk(const SepShape &s, const double *M, const double *om, const 
 // alternating scratch sets, so that the phases of neighbouring chunks can
 // run on two streams at once.  Scratch: tc_ovl_scratch_bytes.
 size_t tc_ovl_scratch_bytes(const SepShape &s, int nxl, int nxc);
+// part 0: operands and the Y rows of the first-form G blocks (GLayout),
+// part 1: the Y rows of the others, part < 0: all
 int tc_triple_prep(const SepShape &s, const double *M, const double *om, const double *xw, int x0, int nxc,
-                   int nxl_max, int nxc_max, void *scratch, int set, cudaStream_t st, Profiler *prof = nullptr);
+                   int nxl_max, int nxc_max, void *scratch, int set, int part, cudaStream_t st,
+                   Profiler *prof = nullptr);
 // single: one CTA per tile or K range of a tile (K splits by the modelled
 // makespan on grid_sms SMs); otherwise the persistent queue on grid_sms SMs
+// part (single form only): the tiles of the first-form blocks (0), of the
+// others (1), or all (< 0)
 int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double *G, bool accumulate,
                    void *scratch, int set, long long wait_cycles, int grid_sms, int tune, bool single,
-                   int split_k, cudaStream_t st, Profiler *prof = nullptr);
+                   int split_k, int part, cudaStream_t st, Profiler *prof = nullptr);
 // The adjoint of the separable form on the tensor cores (exact slicing):
 // dL/dM by one GEMM over the Y rows per radial chunk, then dL/dq~ and dL/dq
 // by two more; nxc radial points per chunk (tc_backward_nxc).  The status

@@ -230,3 +230,22 @@ def test_tail_overlap_graph_capture(mg):
     torch.cuda.synchronize()
     assert normwise(out, oracle.separable(P2)) < TOL_MIXED
     h.close()
+
+
+@pytest.mark.parametrize("split_k", [0, 2])
+def test_tail_overlap_split_k(mg, split_k):
+    """The overlapped form with its GEMM in two halves (the G blocks of each
+    expansion) and, on request, K splits whose partial sums are added per
+    half: against the oracle and the one-stream form."""
+    P = syn.make_problem(400, 7, 40, seed=99)
+    h = mg.Handle()
+    mg.set_option(mg.OPT_TC_SPLIT_K, split_k, handle=h)
+    dp = mg.DeviceProblem.from_host(P, handle=h)
+    g = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, x_chunk=8, handle=h)
+    mg.handle_status(handle=h)
+    assert normwise(g, oracle.separable(P)) < TOL_MIXED
+    mg.set_option(mg.OPT_TC_OVERLAP_TAIL, 0, handle=h)
+    g0 = mg.project_separable(dp, precision=mg.PREC_OZAKI_BF16, x_chunk=8, handle=h).cpu().numpy()
+    mg.handle_status(handle=h)
+    assert normwise(g, g0) < TOL_FORMS
+    h.close()
