@@ -2899,18 +2899,25 @@ __global__ void __launch_bounds__(256) k_adj_split_y(int64_t S, int nbl, int nbp
     }
     const int e = exp_bound_f(bnd);
     const SplitScale sc = split_scale(e);
+    // (pair, {u,v}) of the lane's row, stepped along instead of divided out per row
+    int pr = (int)((k0 + 4 * lane) / P2), uvr = (int)((k0 + 4 * lane) % P2);
     for (int64_t r0 = k0 + 4 * lane; r0 < kend; r0 += 128) {
       float q[4][OZ_SLICES];
+      int prt = pr, uvt = uvr;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int64_t r = r0 + t;
         float h = 0.f, l = 0.f;
         if (r < rowsY) {
-          const int ab = prtab[r / P2], uv = uvtab[r % P2];
+          const int ab = prtab[prt], uv = uvtab[uvt];
           const int oa = (ab & 255) * nbp, ob = (ab >> 8) * nbp, u = uv & 255, v = uv >> 8;
           const f2 y = df_addv(df_mul(Ms[oa + u], Ms[ob + v]), df_mul(Ms[oa + v], Ms[ob + u]));
           h = sg * y.h;
           l = sg * y.l;
+        }
+        if (++uvt == P2) {
+          uvt = 0;
+          ++prt;
         }
         const float H = sc.zero ? 0.f : (h * sc.s1) * sc.s2;
         const float L = sc.zero ? 0.f : (l * sc.s1) * sc.s2;
@@ -2920,6 +2927,11 @@ __global__ void __launch_bounds__(256) k_adj_split_y(int64_t S, int nbl, int nbp
       for (int qq = 0; qq < OZ_SLICES; ++qq)
         outq[(qq * sstride + sl * KpadY + r0) / 4] =
             make_uint2(bf16x2_bits(make_float2(q[0][qq], q[1][qq])), bf16x2_bits(make_float2(q[2][qq], q[3][qq])));
+      uvr += 128;
+      while (uvr >= P2) {
+        uvr -= P2;
+        ++pr;
+      }
     }
     if (lane == 0) {
       ex[(int64_t)ch * S + sl] = e;
