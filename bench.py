@@ -46,7 +46,7 @@ TC_SLICE_PRODUCTS = 15       # BF16 slice products per useful MAC in the tensor-
 # capture is left out (its traffic is then reported as null).
 NCU_TRAFFIC = {("tc_gemm_triple", "single"): 7.136e9 + 92.5e6, ("tc_make_Y", "single"): 80.6e6 + 5.497e9,
                ("tc_make_Y", "pair"): 80.6e6 + 5.497e9, ("tc_make_Y", "queue"): 80.6e6 + 5.497e9,
-               ("tc_make_Y", "tail"): 80.6e6 + 5.497e9, ("tc_gemm_triple", "tail"): 6.831e9 + 46.0e6}
+               ("tc_gemm_triple", "tail"): 3.112e9 + 15.7e6}  # tail form: per half-chunk launch
 # kernels inside one profiler scope (the library counts kernels; a roofline
 # divides the scope's time by its scope count)
 SCOPE_KERNELS = {"tc_make_Y": 2, "tc_prep_M": 2}
