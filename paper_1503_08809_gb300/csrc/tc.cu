@@ -45,6 +45,7 @@
 #include "mma_plan.h"
 #include "fp_bits.h"
 #include "oz_split.h"
+#include "dtc_enum.h"
 
 namespace modal {
 
@@ -3473,50 +3474,8 @@ constexpr int DTC_NT = 4096;   // tiles per batch (at most)
 constexpr int DTC_NP = 1024;   // pairs per batch (at most)
 constexpr int DTC_MAXNB = 32;  // basis functions of this form (Z block of a triple in shared memory; W sums)
 
-struct DtcBatch {
-  int64_t t0, nt;          // tiles [t0, t0 + nt) (nt = 0: past the end)
-  int64_t trip0, n_tri;    // triples [trip0, trip0 + n_tri)
-  int64_t slot0, nslots;   // pairs with tiles: slots [slot0, slot0 + nslots)
-  int n_items;             // GEMM items (nt x column tiles)
-  int pad;
-};
-
-// first class row k in [lo, hi) with grid[crow[k]] >= v (hi if none)
-__device__ __forceinline__ int dtc_lower(const int *__restrict__ grid, const int *__restrict__ crow, int lo, int hi,
-                                         int v) {
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (grid[crow[mid]] < v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// the l1 of the pair (i2 <= i3): class rows [k0, k0 + n)
-struct DtcRun {
-  int k0, n;
-};
-__device__ __forceinline__ DtcRun dtc_run(int i2, int i3, const int *__restrict__ grid, const int *__restrict__ crow,
-                                          const int *__restrict__ cls, int mode) {
-  const int l2 = grid[i2], l3 = grid[i3];
-  const int c = mode == MODAL_W_EXACT_3J ? ((l2 + l3) & 1) : 0;
-  const int base = c ? cls[0] : 0, end = base + cls[c];
-  const int k0 = dtc_lower(grid, crow, base, end, l3 - l2);
-  const int k1 = dtc_lower(grid, crow, base, end, l2 + 1);
-  return {k0, k1 > k0 ? k1 - k0 : 0};
-}
-
-// last index with off[idx] <= t (entries with zero count share the next
-// entry's offset, so this is the entry whose range holds t)
-__device__ __forceinline__ int64_t dtc_find(const int64_t *__restrict__ off, int64_t n, int64_t t) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (off[mid] <= t) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo - 1;
-}
+using DtcBatch = dtc::Batch;  // index logic of this form: dtc_enum.h
+using dtc::find;
 
 // Grid points ordered by class: crow[k] = grid index of class row k; class 0
 // (even l with exact 3j weights, every point otherwise) first.  cls = sizes.
@@ -3543,7 +3502,7 @@ __global__ void k_dtc_count(int ng, const int *__restrict__ grid, const int *__r
   if (idx >= (int64_t)ng * ng) return;
   const int i2 = (int)(idx / ng), i3 = (int)(idx % ng);
   int64_t n = 0;
-  if (i3 >= i2) n = dtc_run(i2, i3, grid, crow, cls, mode).n;
+  if (i3 >= i2) n = dtc::run(i2, i3, grid, crow, cls, mode == MODAL_W_EXACT_3J).n;
   const int64_t nt = (n + cpt - 1) / cpt;
   tri_cnt[idx] = n;
   tile_cnt[idx] = nt;
@@ -3573,29 +3532,9 @@ __global__ void k_dtc_info(int nct, int cpt, int64_t npairs, const int64_t *__re
                            const int64_t *__restrict__ tri_off, const int64_t *__restrict__ slot_of,
                            const int *__restrict__ pairs_nz, int64_t *__restrict__ tot, DtcBatch *__restrict__ info) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  const int64_t ntiles = tot[1], nslots = tot[2];
-  DtcBatch r{};
-  r.t0 = tot[3];
-  if (r.t0 < ntiles) {
-    const int64_t pa = dtc_find(tile_off, npairs, r.t0);
-    r.slot0 = slot_of[pa];
-    int64_t t1 = min(r.t0 + DTC_NT, ntiles);
-    if (r.slot0 + DTC_NP < nslots) t1 = min(t1, tile_off[pairs_nz[r.slot0 + DTC_NP]]);
-    r.nt = t1 - r.t0;
-    r.trip0 = tri_off[pa] + (r.t0 - tile_off[pa]) * cpt;
-    int64_t trip1 = tot[0];
-    if (t1 < ntiles) {
-      const int64_t pb = dtc_find(tile_off, npairs, t1);
-      trip1 = tri_off[pb] + (t1 - tile_off[pb]) * cpt;
-    }
-    r.n_tri = trip1 - r.trip0;
-    r.nslots = slot_of[dtc_find(tile_off, npairs, t1 - 1)] - r.slot0 + 1;
-    r.n_items = (int)(r.nt * nct);
-    tot[3] = t1;
-  } else {
-    r.t0 = ntiles;
-  }
-  *info = r;
+  int64_t cursor = tot[3];
+  *info = dtc::next_batch(cursor, tot, nct, cpt, npairs, tile_off, tri_off, slot_of, pairs_nz, DTC_NT, DTC_NP);
+  tot[3] = cursor;
 }
 
 // (l1, l2, l3) and the weight z of each triple of the batch
@@ -3607,9 +3546,9 @@ __global__ void k_dtc_fill(const DtcBatch *__restrict__ info, const int64_t *__r
   const int64_t tb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tb >= info->n_tri) return;
   const int64_t t = info->trip0 + tb;
-  const int64_t pr = dtc_find(tri_off, npairs, t);
+  const int64_t pr = find(tri_off, npairs, t);
   const int i2 = (int)(pr / ng), i3 = (int)(pr % ng);
-  const DtcRun run = dtc_run(i2, i3, grid, crow, cls, mode);
+  const dtc::Run run = dtc::run(i2, i3, grid, crow, cls, mode == MODAL_W_EXACT_3J);
   const int i1 = crow[run.k0 + (int)(t - tri_off[pr])];
   const int l1 = grid[i1], l2 = grid[i2], l3 = grid[i3];
   tri[3 * tb] = l1;
@@ -3756,16 +3695,13 @@ __global__ void k_dtc_items(const DtcBatch *__restrict__ info, const int64_t *__
                             const int *__restrict__ cls, int mode, int cpt, int nbp, int nct, int wu, int urows,
                             int4 *__restrict__ items) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= info->nt) return;
-  const int64_t T = info->t0 + j;
-  const int64_t pr = dtc_find(tile_off, npairs, T);
-  const int tl = (int)(T - tile_off[pr]);
-  const DtcRun run = dtc_run((int)(pr / ng), (int)(pr % ng), grid, crow, cls, mode);
-  const int k = run.k0 + tl * cpt, n = min(cpt, run.n - tl * cpt);
-  const int tri0 = (int)(tri_off[pr] + (int64_t)tl * cpt - info->trip0);
-  const int slot = (int)(slot_of[pr] - info->slot0);
-  for (int h = 0; h < nct; ++h)
-    items[j * nct + h] = make_int4(k * nbp, slot * urows + h * wu, tri0, n | (h * wu) << 16);
+  const DtcBatch b = *info;
+  if (j >= b.nt) return;
+  for (int h = 0; h < nct; ++h) {
+    const dtc::Item it = dtc::item(b, j, h, tile_off, tri_off, slot_of, npairs, ng, grid, crow, cls,
+                                   mode == MODAL_W_EXACT_3J, cpt, nbp, wu, urows);
+    items[j * nct + h] = make_int4(it.a_row0, it.b_row0, it.tri0, it.packed);
+  }
 }
 
 // X[tb][m] of the batch's triples from their Z blocks (one triple per block)
