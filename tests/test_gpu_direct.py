@@ -204,3 +204,15 @@ def test_direct_tensor_update_planck_sparse_sampled(mg, level):
     got = g[np.ix_(rows, cols)]
     assert np.abs(got - ref).max() / np.abs(g64).max() < TOL_TC
     h.close()
+
+
+def test_direct_tensor_integrals_many_radial_points(mg):
+    """More radial points than one exact chunk of the slicing (1100 > 1024):
+    the q~ rows and the U rows are split in two K chunks each."""
+    P = syn.make_problem(50, 3, 1100, seed=21, nb_prim=4)
+    lg, dw = syn.sparse_l_grid(50)
+    h = _tensor_handle(mg, 2)
+    g = mg.project_direct(mg.DeviceProblem.from_host(P, handle=h), lg, dw, handle=h)
+    assert mg.handle_status(handle=h) == 0
+    assert normwise(g, oracle.direct(P, l_grid=lg, l_dw=dw)) < TOL_TC
+    h.close()
