@@ -792,7 +792,7 @@ int modal_workspace_size(const modal_problem *p, const modal_opts *o, int for_ba
   if (int r = plan_separable(nullptr, p, o, pl, sms)) return r;
   size_t b = pl.bytes;
   if (for_backward) {
-    size_t bb = pl.prec == MODAL_PREC_OZAKI_BF16 ? tc_backward_scratch_bytes(pl.s, tc_backward_nxc(pl.s))
+    size_t bb = pl.prec == MODAL_PREC_OZAKI_BF16 ? tc_backward_scratch_bytes(pl.s, tc_backward_nxc(pl.s, sms))
                                                  : backward_scratch_bytes(pl.s, pl.nxc, pl.prec);
     b = bb > b ? bb : b;
   }
@@ -1377,7 +1377,7 @@ int modal_project_backward(modal_handle *h, const modal_problem *p, const modal_
   if (int r = plan_separable(h, p, o, pl, h->num_sms)) return r;
   cudaStream_t st = (cudaStream_t)stream;
   if (pl.prec == MODAL_PREC_OZAKI_BF16) {  // the adjoint's three contractions on the tensor cores
-    int nxc = tc_backward_nxc(pl.s);
+    int nxc = tc_backward_nxc(pl.s, h->num_sms);
     if (o && o->x_chunk > 0 && o->x_chunk < nxc) nxc = o->x_chunk;  // a smaller chunk on request
     void *scratch;
     if (int r = ws_get(h, 0, tc_backward_scratch_bytes(pl.s, nxc), &scratch)) return r;

@@ -55,10 +55,11 @@ int tc_triple_gemm(const SepShape &s, int nxc, int nxl_max, int nxc_max, double 
                    int split_k, int part, cudaStream_t st, Profiler *prof = nullptr);
 // The adjoint of the separable form on the tensor cores (exact slicing):
 // dL/dM by one GEMM over the Y rows per radial chunk, then dL/dq~ and dL/dq
-// by two more; nxc radial points per chunk (tc_backward_nxc).  The status
+// by two more; nxc radial points per chunk (tc_backward_nxc: by memory and
+// the dL/dM GEMM's CTA waves on num_sms SMs).  The status
 // word is tc_error_word(scratch).
 size_t tc_backward_scratch_bytes(const SepShape &s, int nxc);
-int tc_backward_nxc(const SepShape &s);
+int tc_backward_nxc(const SepShape &s, int num_sms);
 int tc_backward(const SepShape &s, int nxc, const modal_problem *p, const double *gbar, double *dqt, double *dq,
                 void *scratch, long long wait_cycles, cudaStream_t st, Profiler *prof = nullptr);
 // C[m][n] += A B^T over one batch of T terms of the direct form (only the
