@@ -47,6 +47,13 @@ TC_SLICE_PRODUCTS = 15       # BF16 slice products per useful MAC in the tensor-
 NCU_TRAFFIC = {("tc_gemm_triple", "single"): 7.136e9 + 92.5e6, ("tc_make_Y", "single"): 80.6e6 + 5.497e9,
                ("tc_make_Y", "pair"): 80.6e6 + 5.497e9, ("tc_make_Y", "queue"): 80.6e6 + 5.497e9,
                ("tc_gemm_triple", "tail"): 3.112e9 + 15.7e6}  # tail form: per half-chunk launch
+# Tensor-pipe activity of the triple GEMM from one full ncu capture of a
+# half-chunk launch of the tail form (255 whole tiles, K = 12004): cycles with
+# the pipe busy over the SMs' active cycles and over the elapsed cycles.  It
+# does not depend on the SM clock, unlike `frac` against the measured cuBLAS
+# peak, whose clock under load differs from this kernel's.  Like
+# NCU_TRAFFIC, valid only while the kernel is unchanged since the capture.
+NCU_TENSOR = {("tc_gemm_triple", "tail"): {"of_active_cycles": 0.680, "of_elapsed_cycles": 0.554}}
 # kernels inside one profiler scope (the library counts kernels; a roofline
 # divides the scope's time by its scope count)
 SCOPE_KERNELS = {"tc_make_Y": 2, "tc_prep_M": 2}
@@ -467,6 +474,8 @@ def kernel_roofline(name, rec, per_step, P, prec_name, peaks, src, steps, ms, fo
          "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((name, form)) if P.n_x == 500 else None,
          "peak_source": note, "kernel_ms_avg": avg_s * 1e3, "launches_per_step": per_step,
          "kernel_share_of_step": tot / (ms * steps)}
+    if (name, form) in NCU_TENSOR:
+        r["ncu_tensor_active"] = NCU_TENSOR[(name, form)]
     r.update(extra)
     return r
 
