@@ -39,6 +39,7 @@
 
 #include "common.cuh"
 #include "direct.cuh"
+#include "grid_plan.h"
 #include "kernels.cuh"
 #include "ptx.cuh"
 #include "tc.cuh"
@@ -1357,8 +1358,7 @@ int tc_contract_l(const SepShape &s, const double *qt, int x0, int nxc, int nxc_
       goto cuda_fail;
     // row tiles per CTA: a few, keeping at least ~4 waves of CTAs
     const int64_t nrt = cdiv64(rowsA, OZ_BM), nct = cdiv64(rowsB, OZ_BN);
-    int rpc = (int)(nrt * nct / (4 * 152));
-    rpc = rpc < 1 ? 1 : (rpc > 4 ? 4 : rpc);
+    const int rpc = gridp::rows_per_cta(nrt, nct);
     P.rows_per_cta = rpc;
     dim3 grid((unsigned)nct, (unsigned)cdiv64(nrt, rpc));
     ProfScope ps(prof, "tc_gemm_l", st);
@@ -3224,8 +3224,7 @@ static int dense_gemm(const __nv_bfloat16 *As, const int *eA, const int *emaxA, 
   P.koff = koff;
   fill_mma_plans(P.plan);
   const int64_t nrt = cdiv64(rowsA, OZ_BM), nct = cdiv64(rowsB, OZ_BN);
-  int rpc = (int)(nrt * nct / (4 * 152));
-  rpc = rpc < 1 ? 1 : (rpc > 4 ? 4 : rpc);
+  const int rpc = gridp::rows_per_cta(nrt, nct);
   P.rows_per_cta = rpc;
   cudaError_t e = cudaFuncSetAttribute(k_ozaki_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
   if (e == cudaSuccess) {
@@ -3300,36 +3299,17 @@ size_t tc_backward_scratch_bytes(const SepShape &s, int nxc) {
   return (size_t)(adj_scratch(nullptr, s, nxc).end - (char *)nullptr) + 1024;
 }
 
-// CTA waves of the dL/dM GEMM over S slices (the grid dense_gemm launches:
-// 128-row tiles, several per CTA when there are many) on num_sms SMs
-static int64_t dm_gemm_waves(int64_t S, int64_t ncols, int num_sms) {
-  const int64_t nrt = cdiv64(S, OZ_BM), nct = cdiv64(ncols, OZ_BN);
-  int64_t rpc = nrt * nct / (4 * (int64_t)num_sms);
-  rpc = rpc < 1 ? 1 : (rpc > 4 ? 4 : rpc);
-  return rpc * cdiv64(nct * cdiv64(nrt, rpc), num_sms);
-}
-
 // radial points per chunk of the tensor-core adjoint: its per-point buffers
 // (Y^T slices, M, dM and its slices, T) within 8 GiB, 1 .. 32; given the SM
-// count, the chunk in [cmax / 2, cmax] whose dL/dM GEMM launches take the
-// fewest CTA waves over all chunks (a part-full last wave costs a whole
-// one), plus a tenth of a wave per chunk for its other launches
+// count, the chunk between half and all of that whose dL/dM GEMMs need the
+// fewest CTA waves over the call (grid_plan.h)
 int tc_backward_nxc(const SepShape &s, int num_sms) {
   const int64_t per_x = (int64_t)s.n_mu * (10 * pad32(y_rows(s)) + 26 * (int64_t)s.nbl * s.nbp) +
                         8 * (int64_t)s.nbl * s.nbp * s.L;
   int64_t c = ((int64_t)8 << 30) / (per_x > 0 ? per_x : 1);
   c = c < 1 ? 1 : (c > 32 ? 32 : c);
   if (c > s.n_x) c = s.n_x > 0 ? s.n_x : 1;
-  if (num_sms <= 0 || s.n_x <= 0) return (int)c;
-  const int64_t ncols = (int64_t)s.nbl * s.nbp;
-  int64_t best = c, best_cost = -1;
-  for (int64_t cc = c; cc >= 1 && 2 * cc >= c; --cc) {
-    const int64_t full = s.n_x / cc, rest = s.n_x % cc;
-    int64_t cost = 10 * full * dm_gemm_waves(cc * s.n_mu, ncols, num_sms) + full;
-    if (rest) cost += 10 * dm_gemm_waves(rest * s.n_mu, ncols, num_sms) + 1;
-    if (best_cost < 0 || cost < best_cost) best = cc, best_cost = cost;
-  }
-  return (int)best;
+  return gridp::chunk(s.n_x, s.n_mu, (int64_t)s.nbl * s.nbp, c, num_sms);
 }
 
 // The adjoint on the tensor cores (see the block comment above k_adj_split_y).
